@@ -1,0 +1,202 @@
+"""Serial FP64 CPU oracle for the five-equation RHS -- TEST INFRASTRUCTURE.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline
+leg (and its ``--impl reference`` arm) may import this package.  The product
+path (``paper_2409_10729_gb300``) never imports it and fails loudly when its
+own CUDA library is missing.
+
+The arithmetic lives in ``mfc5_oracle.c`` (plain C, ``-O2 -ffp-contract=off``),
+a step-by-step statement of arXiv 2409.10729 Sec. II (model, stiffened-gas
+EOS, finite-volume RHS with WENO5-JS + HLLC) plus the SSP-RK3 / CFL reading.
+This module only builds the shared library and marshals numpy arrays.
+
+Parity status: every function here is pinned by ``tests/test_oracle_*.py``
+(closed forms, exact Riemann solutions, convergence order, conservation,
+equilibrium, symmetry); none is "parity unpinned".
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "mfc5_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle_mfc5.so")
+# Test hook: the mutation test points this at a deliberately broken build.
+_LIB_OVERRIDE = os.environ.get("MFC5_ORACLE_LIB")
+
+OK, EINVAL, ENOMEM, ENONPHYSICAL = 0, -1, -2, -4
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (no fast-math, no FMA contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+               "-shared", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class OrcParams(ctypes.Structure):
+    _fields_ = [
+        ("ndim", ctypes.c_int),
+        ("n", ctypes.c_int * 3),
+        ("lo", ctypes.c_double * 3),
+        ("hi", ctypes.c_double * 3),
+        ("bc", (ctypes.c_int * 2) * 3),
+        ("gamma", ctypes.c_double * 2),
+        ("pi_inf", ctypes.c_double * 2),
+        ("weno_eps", ctypes.c_double),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(_LIB_OVERRIDE or build())
+        dp = ctypes.POINTER(ctypes.c_double)
+        pp = ctypes.POINTER(OrcParams)
+        lp = ctypes.POINTER(ctypes.c_long)
+        sig = {
+            "orc_neq": ([pp], ctypes.c_int),
+            "orc_prim_to_cons": ([pp, dp, dp], ctypes.c_int),
+            "orc_cons_to_prim": ([pp, dp, dp], ctypes.c_int),
+            "orc_rhs": ([pp, dp, dp], ctypes.c_int),
+            "orc_rhs_points": ([pp, dp, lp, ctypes.c_long, dp], ctypes.c_int),
+            "orc_max_wavespeed": ([pp, dp, dp], ctypes.c_int),
+            "orc_step_dt": ([pp, dp, ctypes.c_double], ctypes.c_int),
+            "orc_run_cfl": ([pp, dp, ctypes.c_double, ctypes.c_int, dp], ctypes.c_int),
+            "orc_weno5_cell": ([ctypes.c_double, dp, dp, dp], None),
+            "orc_hllc_face": ([pp, ctypes.c_int, dp, dp, dp, dp], ctypes.c_int),
+            "orc_sound_speed2": ([pp, dp, dp], ctypes.c_int),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(_lib, name)
+            fn.argtypes = args
+            fn.restype = res
+    return _lib
+
+
+def params(p: dict) -> OrcParams:
+    """OrcParams from the plain dict produced by the input generators."""
+    s = OrcParams()
+    s.ndim = int(p["ndim"])
+    for d in range(3):
+        s.n[d] = int(p["n"][d])
+        s.lo[d] = float(p["lo"][d])
+        s.hi[d] = float(p["hi"][d])
+        s.bc[d][0] = int(p["bc"][d][0])
+        s.bc[d][1] = int(p["bc"][d][1])
+    for i in range(2):
+        s.gamma[i] = float(p["gamma"][i])
+        s.pi_inf[i] = float(p["pi_inf"][i])
+    s.weno_eps = float(p.get("weno_eps", 1e-6))
+    return s
+
+
+def _dptr(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _check(st: int, what: str, allow_nonphysical: bool = False) -> int:
+    if st == OK or (allow_nonphysical and st == ENONPHYSICAL):
+        return st
+    raise RuntimeError(f"oracle {what} failed with status {st}")
+
+
+def neq(p: dict) -> int:
+    n = lib().orc_neq(ctypes.byref(params(p)))
+    if n < 0:
+        raise RuntimeError(f"oracle rejected params with status {n}")
+    return n
+
+
+def prim_to_cons(p: dict, w: np.ndarray) -> np.ndarray:
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    q = np.empty_like(w)
+    _check(lib().orc_prim_to_cons(ctypes.byref(params(p)), _dptr(w), _dptr(q)), "prim_to_cons")
+    return q
+
+
+def cons_to_prim(p: dict, q: np.ndarray) -> np.ndarray:
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    w = np.empty_like(q)
+    _check(lib().orc_cons_to_prim(ctypes.byref(params(p)), _dptr(q), _dptr(w)), "cons_to_prim")
+    return w
+
+
+def rhs(p: dict, q: np.ndarray, allow_nonphysical: bool = False) -> np.ndarray:
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    out = np.empty_like(q)
+    _check(lib().orc_rhs(ctypes.byref(params(p)), _dptr(q), _dptr(out)), "rhs", allow_nonphysical)
+    return out
+
+
+def rhs_points(p: dict, q: np.ndarray, cells: np.ndarray) -> np.ndarray:
+    """L(q) at flat cell indices ``cells``; returns [len(cells), neq]."""
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    cells = np.ascontiguousarray(cells, dtype=np.int64)
+    ne = int(p["ndim"]) + 4
+    out = np.empty((len(cells), ne), dtype=np.float64)
+    st = lib().orc_rhs_points(ctypes.byref(params(p)), _dptr(q),
+                              cells.ctypes.data_as(ctypes.POINTER(ctypes.c_long)),
+                              len(cells), _dptr(out))
+    _check(st, "rhs_points")
+    return out
+
+
+def max_wavespeed(p: dict, q: np.ndarray) -> float:
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    s = ctypes.c_double()
+    _check(lib().orc_max_wavespeed(ctypes.byref(params(p)), _dptr(q), ctypes.byref(s)), "wavespeed")
+    return s.value
+
+
+def step_dt(p: dict, q: np.ndarray, dt: float) -> np.ndarray:
+    """One RK3 step of size dt; returns a new array."""
+    q = np.array(q, dtype=np.float64, copy=True, order="C")
+    _check(lib().orc_step_dt(ctypes.byref(params(p)), _dptr(q), float(dt)), "step_dt")
+    return q
+
+
+def run_cfl(p: dict, q: np.ndarray, cfl: float, nsteps: int):
+    """nsteps CFL steps; returns (new state, time advanced)."""
+    q = np.array(q, dtype=np.float64, copy=True, order="C")
+    t = ctypes.c_double()
+    _check(lib().orc_run_cfl(ctypes.byref(params(p)), _dptr(q), float(cfl), int(nsteps),
+                             ctypes.byref(t)), "run_cfl")
+    return q, t.value
+
+
+def weno5_cell(v5, eps: float = 1e-6):
+    v = np.ascontiguousarray(v5, dtype=np.float64)
+    vm, vp = ctypes.c_double(), ctypes.c_double()
+    lib().orc_weno5_cell(float(eps), _dptr(v), ctypes.byref(vm), ctypes.byref(vp))
+    return vm.value, vp.value
+
+
+def hllc_face(p: dict, direction: int, wL, wR):
+    """HLLC flux between primitive face states; returns (F[neq], u_face, status)."""
+    wl = np.ascontiguousarray(wL, dtype=np.float64)
+    wr = np.ascontiguousarray(wR, dtype=np.float64)
+    F = np.empty_like(wl)
+    uf = ctypes.c_double()
+    st = lib().orc_hllc_face(ctypes.byref(params(p)), int(direction), _dptr(wl), _dptr(wr),
+                             _dptr(F), ctypes.byref(uf))
+    return F, uf.value, st
+
+
+def sound_speed2(p: dict, w) -> float:
+    wv = np.ascontiguousarray(w, dtype=np.float64)
+    c2 = ctypes.c_double()
+    _check(lib().orc_sound_speed2(ctypes.byref(params(p)), _dptr(wv), ctypes.byref(c2)), "c2")
+    return c2.value

@@ -1,0 +1,533 @@
+/*
+ * mfc5_oracle.c -- TEST INFRASTRUCTURE, not part of the product.
+ *
+ * A plain, serial, double-precision CPU statement of the right-hand side of
+ * the two-fluid five-equation (Allaire) model with the stiffened-gas equation
+ * of state, discretised with WENO5-JS face reconstruction, the HLLC Riemann
+ * solver and Shu-Osher TVD-RK3, as described in arXiv 2409.10729:
+ *   - model and EOS:               Sec. II-A (unnumbered equation block and
+ *                                  the stiffened-gas relation that follows it)
+ *   - finite-volume semi-discrete: Sec. II-B, Eq. (eqn:discretization) and the
+ *                                  cell-integrated form that follows it
+ *   - WENO + HLLC:                 Sec. II-B, last paragraph
+ * Readings of points the paper leaves open (mixture rules, sound speed, WENO
+ * epsilon, wave-speed estimates, the discrete h(q) div(u) term, the time
+ * integrator, the CFL rule, boundary ghosts) are listed in the design doc and are
+ * followed here verbatim.
+ *
+ * Only tests/, the smoke check and bench.py's CPU-baseline leg may load this
+ * file's shared library.  It shares no code with the CUDA path.
+ *
+ * Build: gcc -O2 -ffp-contract=off -fPIC -shared (no fast-math, no pow):
+ * every formula below is evaluated in the written operation order, with IEEE
+ * division and square root.
+ *
+ * Layout: conservative q[f][z][y][x] (x fastest), interior cells only.
+ *   f = 0: alpha1 rho1, 1: alpha2 rho2, 2..2+d-1: rho u_k, 2+d: rho E,
+ *   3+d: alpha1.  neq = d + 4.
+ * Primitive w has the same slots with u_k in place of rho u_k and p in place
+ * of rho E.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_OK 0
+#define ORC_EINVAL (-1)
+#define ORC_ENOMEM (-2)
+#define ORC_ENONPHYSICAL (-4)
+
+typedef struct {
+    int ndim;          /* 1, 2 or 3 */
+    int n[3];          /* cells per dimension; unused dimensions = 1 */
+    double lo[3];      /* domain lower corner */
+    double hi[3];      /* domain upper corner */
+    int bc[3][2];      /* per dimension, per side: 0 transmissive, 1 periodic */
+    double gamma[2];   /* ratio of specific heats, fluid 1 and fluid 2 */
+    double pi_inf[2];  /* stiffness, fluid 1 and fluid 2 */
+    double weno_eps;   /* WENO epsilon (absolute) */
+} orc_params;
+
+typedef struct {
+    int ndim, neq;
+    long n[3];
+    long stride[3];
+    long ncell;
+    double dx[3];
+    int periodic[3];
+    double g1, g2;     /* 1/(gamma_i - 1) */
+    double P1, P2;     /* gamma_i pi_i/(gamma_i - 1) */
+    double eps;
+} grid;
+
+#define IE(g) (2 + (g)->ndim)
+#define IA(g) (3 + (g)->ndim)
+
+static int make_grid(const orc_params* p, grid* g) {
+    if (!p || p->ndim < 1 || p->ndim > 3) return ORC_EINVAL;
+    g->ndim = p->ndim;
+    g->neq = p->ndim + 4;
+    g->ncell = 1;
+    for (int d = 0; d < 3; d++) {
+        long n = p->n[d];
+        if (d >= p->ndim) n = 1;
+        if (n < 1) return ORC_EINVAL;
+        g->n[d] = n;
+        g->stride[d] = g->ncell;
+        g->ncell *= n;
+        g->periodic[d] = 0;
+        g->dx[d] = 1.0;
+        if (d < p->ndim) {
+            if (!(p->hi[d] > p->lo[d])) return ORC_EINVAL;
+            g->dx[d] = (p->hi[d] - p->lo[d]) / (double)n;
+            int b0 = p->bc[d][0], b1 = p->bc[d][1];
+            if (b0 < 0 || b0 > 1 || b1 < 0 || b1 > 1 || b0 != b1) return ORC_EINVAL;
+            g->periodic[d] = (b0 == 1);
+        }
+    }
+    for (int i = 0; i < 2; i++)
+        if (!(p->gamma[i] > 1.0) || !(p->pi_inf[i] >= 0.0)) return ORC_EINVAL;
+    if (!(p->weno_eps > 0.0)) return ORC_EINVAL;
+    g->g1 = 1.0 / (p->gamma[0] - 1.0);
+    g->g2 = 1.0 / (p->gamma[1] - 1.0);
+    g->P1 = p->gamma[0] * p->pi_inf[0] / (p->gamma[0] - 1.0);
+    g->P2 = p->gamma[1] * p->pi_inf[1] / (p->gamma[1] - 1.0);
+    g->eps = p->weno_eps;
+    return ORC_OK;
+}
+
+/* ---- equation of state (Sec. II-A) -------------------------------------- */
+
+/* Mixture rules: Gamma = sum alpha_i/(gamma_i-1), Pi = sum alpha_i gamma_i
+ * pi_i/(gamma_i-1), with alpha2 = 1 - alpha1.  Then rho E = Gamma p + Pi +
+ * rho|u|^2/2, the stiffened-gas relation with the kinetic energy added. */
+static void mixture(const grid* g, double a1, double* G, double* Pi) {
+    double a2 = 1.0 - a1;
+    *G = a1 * g->g1 + a2 * g->g2;
+    *Pi = a1 * g->P1 + a2 * g->P2;
+}
+
+static double kinetic(const grid* g, double rho, const double* u) {
+    double s = 0.0;
+    for (int k = 0; k < g->ndim; k++) s = s + u[k] * u[k];
+    return 0.5 * rho * s;
+}
+
+static void cons_to_prim(const grid* g, const double* q, double* w) {
+    double rho = q[0] + q[1];
+    double u[3] = {0.0, 0.0, 0.0};
+    for (int k = 0; k < g->ndim; k++) u[k] = q[2 + k] / rho;
+    double ke = kinetic(g, rho, u);
+    double G, Pi;
+    mixture(g, q[IA(g)], &G, &Pi);
+    double p = (q[IE(g)] - ke - Pi) / G;
+    w[0] = q[0];
+    w[1] = q[1];
+    for (int k = 0; k < g->ndim; k++) w[2 + k] = u[k];
+    w[IE(g)] = p;
+    w[IA(g)] = q[IA(g)];
+}
+
+static void prim_to_cons(const grid* g, const double* w, double* q) {
+    double rho = w[0] + w[1];
+    double u[3] = {0.0, 0.0, 0.0};
+    for (int k = 0; k < g->ndim; k++) u[k] = w[2 + k];
+    double ke = kinetic(g, rho, u);
+    double G, Pi;
+    mixture(g, w[IA(g)], &G, &Pi);
+    q[0] = w[0];
+    q[1] = w[1];
+    for (int k = 0; k < g->ndim; k++) q[2 + k] = rho * u[k];
+    q[IE(g)] = G * w[IE(g)] + Pi + ke;
+    q[IA(g)] = w[IA(g)];
+}
+
+/* Mixture sound speed squared, c^2 = ((Gamma+1) p + Pi)/(Gamma rho). */
+static double sound2(double G, double Pi, double rho, double p) {
+    return ((G + 1.0) * p + Pi) / (G * rho);
+}
+
+/* ---- WENO5-JS (Sec. II-B, fifth-order reconstruction) -------------------- */
+
+static double sq(double x) { return x * x; }
+
+/* v[0..4] = v_{i-2} .. v_{i+2} (cell averages of one primitive).
+ * Returns the left-biased value at face i+1/2 (vm) and the right-biased value
+ * at face i-1/2 (vp); both use the same three Jiang-Shu smoothness indicators
+ * of cell i. */
+static void weno5(double eps, const double* v, double* vm, double* vp) {
+    const double c13 = 13.0 / 12.0;
+    double b0 = c13 * sq(v[0] - 2.0 * v[1] + v[2]) + 0.25 * sq(v[0] - 4.0 * v[1] + 3.0 * v[2]);
+    double b1 = c13 * sq(v[1] - 2.0 * v[2] + v[3]) + 0.25 * sq(v[1] - v[3]);
+    double b2 = c13 * sq(v[2] - 2.0 * v[3] + v[4]) + 0.25 * sq(3.0 * v[2] - 4.0 * v[3] + v[4]);
+
+    /* left-biased value at i+1/2: linear weights (0.1, 0.6, 0.3) */
+    double a0 = 0.1 / sq(eps + b0);
+    double a1 = 0.6 / sq(eps + b1);
+    double a2 = 0.3 / sq(eps + b2);
+    double s = a0 + a1 + a2;
+    double p0 = (2.0 * v[0] - 7.0 * v[1] + 11.0 * v[2]) / 6.0;
+    double p1 = (-v[1] + 5.0 * v[2] + 2.0 * v[3]) / 6.0;
+    double p2 = (2.0 * v[2] + 5.0 * v[3] - v[4]) / 6.0;
+    *vm = (a0 / s) * p0 + (a1 / s) * p1 + (a2 / s) * p2;
+
+    /* right-biased value at i-1/2: mirrored weights (0.3, 0.6, 0.1) */
+    a0 = 0.3 / sq(eps + b0);
+    a1 = 0.6 / sq(eps + b1);
+    a2 = 0.1 / sq(eps + b2);
+    s = a0 + a1 + a2;
+    p0 = (-v[0] + 5.0 * v[1] + 2.0 * v[2]) / 6.0;
+    p1 = (2.0 * v[1] + 5.0 * v[2] - v[3]) / 6.0;
+    p2 = (11.0 * v[2] - 7.0 * v[3] + 2.0 * v[4]) / 6.0;
+    *vp = (a0 / s) * p0 + (a1 / s) * p1 + (a2 / s) * p2;
+}
+
+/* ---- HLLC (Sec. II-B; Toro's three-wave approximate solver) -------------- */
+
+typedef struct {
+    double rho, u[3], p, a1, G, Pi, E, c2;
+} face_state;
+
+static void face_from_prim(const grid* g, const double* w, face_state* s) {
+    s->rho = w[0] + w[1];
+    s->u[0] = s->u[1] = s->u[2] = 0.0;
+    for (int k = 0; k < g->ndim; k++) s->u[k] = w[2 + k];
+    s->p = w[IE(g)];
+    s->a1 = w[IA(g)];
+    mixture(g, s->a1, &s->G, &s->Pi);
+    s->E = s->G * s->p + s->Pi + kinetic(g, s->rho, s->u);
+    s->c2 = sound2(s->G, s->Pi, s->rho, s->p);
+}
+
+/* Physical flux of the face state K in direction dir. */
+static void phys_flux(const grid* g, int dir, const double* w, const face_state* K, double* F) {
+    double un = K->u[dir];
+    F[0] = w[0] * un;
+    F[1] = w[1] * un;
+    for (int k = 0; k < g->ndim; k++) F[2 + k] = K->rho * K->u[k] * un;
+    F[2 + dir] = F[2 + dir] + K->p;
+    F[IE(g)] = (K->E + K->p) * un;
+    F[IA(g)] = K->a1 * un;
+}
+
+/* HLLC star-region flux F*_K = F_K + S_K (q*_K - q_K); the volume-fraction
+ * slot carries alpha1_K S* (advection with the contact velocity). */
+static void star_flux(const grid* g, int dir, const double* w, const face_state* K,
+                      double SK, double Ss, double* F) {
+    double un = K->u[dir];
+    phys_flux(g, dir, w, K, F);
+    double chi = (SK - un) / (SK - Ss);
+    F[0] = F[0] + SK * (chi * w[0] - w[0]);
+    F[1] = F[1] + SK * (chi * w[1] - w[1]);
+    for (int k = 0; k < g->ndim; k++) {
+        double mstar = (k == dir) ? chi * K->rho * Ss : chi * K->rho * K->u[k];
+        F[2 + k] = F[2 + k] + SK * (mstar - K->rho * K->u[k]);
+    }
+    double Estar = chi * (K->E + (Ss - un) * (K->rho * Ss + K->p / (SK - un)));
+    F[IE(g)] = F[IE(g)] + SK * (Estar - K->E);
+    F[IA(g)] = K->a1 * Ss;
+}
+
+/* Flux through one face from the reconstructed primitive states wL, wR.
+ * uf receives the velocity of the selected region, used by the
+ * non-conservative volume-fraction term.  Returns 0, or 1 when a face state
+ * is non-physical (rho <= 0, c^2 <= 0 or NaN). */
+static int hllc(const grid* g, int dir, const double* wL, const double* wR, double* F, double* uf) {
+    face_state L, R;
+    face_from_prim(g, wL, &L);
+    face_from_prim(g, wR, &R);
+    int bad = !(L.rho > 0.0) || !(R.rho > 0.0) || !(L.c2 > 0.0) || !(R.c2 > 0.0);
+    double cL = sqrt(L.c2), cR = sqrt(R.c2);
+    double uL = L.u[dir], uR = R.u[dir];
+    double SL = (uL - cL < uR - cR) ? uL - cL : uR - cR;   /* Davis estimates */
+    double SR = (uL + cL > uR + cR) ? uL + cL : uR + cR;
+    double num = R.p - L.p + L.rho * uL * (SL - uL) - R.rho * uR * (SR - uR);
+    double den = L.rho * (SL - uL) - R.rho * (SR - uR);
+    double Ss = num / den;
+    if (0.0 <= SL) {
+        phys_flux(g, dir, wL, &L, F);
+        *uf = uL;
+    } else if (0.0 <= Ss) {
+        star_flux(g, dir, wL, &L, SL, Ss, F);
+        *uf = Ss;
+    } else if (0.0 <= SR) {
+        star_flux(g, dir, wR, &R, SR, Ss, F);
+        *uf = Ss;
+    } else {
+        phys_flux(g, dir, wR, &R, F);
+        *uf = uR;
+    }
+    return bad;
+}
+
+/* ---- semi-discrete right-hand side (Sec. II-B, cell-integrated form) ----- */
+
+/* Ghost index map: transmissive = nearest interior cell, periodic = wrap. */
+static long bc_map(long j, long n, int periodic) {
+    if (periodic) {
+        long r = j % n;
+        return r < 0 ? r + n : r;
+    }
+    if (j < 0) return 0;
+    if (j > n - 1) return n - 1;
+    return j;
+}
+
+static void load_prim(const grid* g, const double* q, long cell, double* w) {
+    double qc[7];
+    for (int f = 0; f < g->neq; f++) qc[f] = q[(long)f * g->ncell + cell];
+    cons_to_prim(g, qc, w);
+}
+
+/* Contribution of direction d at one cell, from the primitive pencil W
+ * (7 cells, i-3..i+3).  L receives
+ *   (F_{i-1/2} - F_{i+1/2})/dx_d  for every equation, plus
+ *   alpha1_i (u_f,{i+1/2} - u_f,{i-1/2})/dx_d  on the alpha1 row. */
+static int cell_dir(const grid* g, int d, const double* W7, double* L) {
+    int neq = g->neq;
+    double vm[3][7], vp[3][7];
+    /* WENO at cells i-1, i, i+1 (pencil slots 2, 3, 4) */
+    for (int c = 0; c < 3; c++) {
+        for (int f = 0; f < neq; f++) {
+            double v[5];
+            for (int s = 0; s < 5; s++) v[s] = W7[(c + s) * neq + f];
+            weno5(g->eps, v, &vm[c][f], &vp[c][f]);
+        }
+    }
+    double Fm[7], Fp[7], ufm, ufp;
+    int bad = hllc(g, d, vm[0], vp[1], Fm, &ufm);   /* face i-1/2 */
+    bad |= hllc(g, d, vm[1], vp[2], Fp, &ufp);      /* face i+1/2 */
+    double dx = g->dx[d];
+    for (int f = 0; f < neq; f++) L[f] = (Fm[f] - Fp[f]) / dx;
+    double a1 = W7[3 * neq + IA(g)];
+    L[IA(g)] = L[IA(g)] + a1 * (ufp - ufm) / dx;
+    return bad;
+}
+
+/* Full RHS for direction d over all pencils, computing each face once. */
+static int rhs_dir(const grid* g, int d, const double* q, double* rhs, int first,
+                   double* W, double* VM, double* VP, double* FF, double* UF) {
+    int neq = g->neq;
+    long nd = g->n[d];
+    int o1 = (d + 1) % 3, o2 = (d + 2) % 3;
+    int bad = 0;
+    for (long j2 = 0; j2 < g->n[o2]; j2++) {
+        for (long j1 = 0; j1 < g->n[o1]; j1++) {
+            long base = j1 * g->stride[o1] + j2 * g->stride[o2];
+            /* primitives of cells -3 .. nd+2 (slot = j + 3) */
+            for (long j = -3; j < nd + 3; j++) {
+                long src = bc_map(j, nd, g->periodic[d]);
+                load_prim(g, q, base + src * g->stride[d], &W[(j + 3) * neq]);
+            }
+            /* WENO at cells -1 .. nd (slot = j + 1) */
+            for (long j = -1; j < nd + 1; j++) {
+                for (int f = 0; f < neq; f++) {
+                    double v[5];
+                    for (int s = 0; s < 5; s++) v[s] = W[(j + 1 + s) * neq + f];
+                    weno5(g->eps, v, &VM[(j + 1) * neq + f], &VP[(j + 1) * neq + f]);
+                }
+            }
+            /* HLLC at faces j+1/2, j = -1 .. nd-1 (face slot = j + 1) */
+            for (long j = -1; j < nd; j++) {
+                bad |= hllc(g, d, &VM[(j + 1) * neq], &VP[(j + 2) * neq], &FF[(j + 1) * neq],
+                            &UF[j + 1]);
+            }
+            double dx = g->dx[d];
+            for (long i = 0; i < nd; i++) {
+                long cell = base + i * g->stride[d];
+                double L[7];
+                for (int f = 0; f < neq; f++) L[f] = (FF[i * neq + f] - FF[(i + 1) * neq + f]) / dx;
+                double a1 = W[(i + 3) * neq + IA(g)];
+                L[IA(g)] = L[IA(g)] + a1 * (UF[i + 1] - UF[i]) / dx;
+                for (int f = 0; f < neq; f++) {
+                    double* r = &rhs[(long)f * g->ncell + cell];
+                    *r = first ? L[f] : *r + L[f];
+                }
+            }
+        }
+    }
+    return bad;
+}
+
+static int rhs_all(const grid* g, const double* q, double* rhs) {
+    long nmax = 1;
+    for (int d = 0; d < g->ndim; d++)
+        if (g->n[d] > nmax) nmax = g->n[d];
+    int neq = g->neq;
+    double* W = malloc(sizeof(double) * (nmax + 6) * neq);
+    double* VM = malloc(sizeof(double) * (nmax + 2) * neq);
+    double* VP = malloc(sizeof(double) * (nmax + 2) * neq);
+    double* FF = malloc(sizeof(double) * (nmax + 1) * neq);
+    double* UF = malloc(sizeof(double) * (nmax + 1));
+    if (!W || !VM || !VP || !FF || !UF) {
+        free(W); free(VM); free(VP); free(FF); free(UF);
+        return ORC_ENOMEM;
+    }
+    int bad = 0;
+    for (int d = 0; d < g->ndim; d++) bad |= rhs_dir(g, d, q, rhs, d == 0, W, VM, VP, FF, UF);
+    free(W); free(VM); free(VP); free(FF); free(UF);
+    for (long i = 0; i < (long)neq * g->ncell; i++)
+        if (isnan(rhs[i]) || isinf(rhs[i])) bad = 1;
+    return bad ? ORC_ENONPHYSICAL : ORC_OK;
+}
+
+/* ---- public entry points (ctypes) ---------------------------------------- */
+
+int orc_neq(const orc_params* p) {
+    grid g;
+    int st = make_grid(p, &g);
+    return st ? st : g.neq;
+}
+
+int orc_prim_to_cons(const orc_params* p, const double* w, double* q) {
+    grid g;
+    int st = make_grid(p, &g);
+    if (st) return st;
+    double wc[7], qc[7];
+    for (long c = 0; c < g.ncell; c++) {
+        for (int f = 0; f < g.neq; f++) wc[f] = w[(long)f * g.ncell + c];
+        prim_to_cons(&g, wc, qc);
+        for (int f = 0; f < g.neq; f++) q[(long)f * g.ncell + c] = qc[f];
+    }
+    return ORC_OK;
+}
+
+int orc_cons_to_prim(const orc_params* p, const double* q, double* w) {
+    grid g;
+    int st = make_grid(p, &g);
+    if (st) return st;
+    double wc[7];
+    for (long c = 0; c < g.ncell; c++) {
+        load_prim(&g, q, c, wc);
+        for (int f = 0; f < g.neq; f++) w[(long)f * g.ncell + c] = wc[f];
+    }
+    return ORC_OK;
+}
+
+/* L(q): the semi-discrete right-hand side, same layout as q. */
+int orc_rhs(const orc_params* p, const double* q, double* rhs) {
+    grid g;
+    int st = make_grid(p, &g);
+    if (st) return st;
+    return rhs_all(&g, q, rhs);
+}
+
+/* L(q) at selected cells only (flat cell indices), out[k*neq + f].  Uses the
+ * same per-face arithmetic as orc_rhs, on a 7-cell pencil per direction. */
+int orc_rhs_points(const orc_params* p, const double* q, const long* cells, long npts, double* out) {
+    grid g;
+    int st = make_grid(p, &g);
+    if (st) return st;
+    int neq = g.neq, bad = 0;
+    for (long k = 0; k < npts; k++) {
+        long cell = cells[k];
+        if (cell < 0 || cell >= g.ncell) return ORC_EINVAL;
+        long idx[3];
+        long rem = cell;
+        for (int d = 0; d < 3; d++) { idx[d] = rem % g.n[d]; rem /= g.n[d]; }
+        double acc[7];
+        for (int d = 0; d < g.ndim; d++) {
+            double W7[7 * 7], L[7];
+            long base = cell - idx[d] * g.stride[d];
+            for (int s = 0; s < 7; s++) {
+                long src = bc_map(idx[d] + s - 3, g.n[d], g.periodic[d]);
+                load_prim(&g, q, base + src * g.stride[d], &W7[s * neq]);
+            }
+            bad |= cell_dir(&g, d, W7, L);
+            for (int f = 0; f < neq; f++) acc[f] = (d == 0) ? L[f] : acc[f] + L[f];
+        }
+        for (int f = 0; f < neq; f++) {
+            out[k * neq + f] = acc[f];
+            if (isnan(acc[f]) || isinf(acc[f])) bad = 1;
+        }
+    }
+    return bad ? ORC_ENONPHYSICAL : ORC_OK;
+}
+
+/* S = max over cells of sum_d (|u_d| + c)/dx_d; the step is dt = CFL/S. */
+int orc_max_wavespeed(const orc_params* p, const double* q, double* S_out) {
+    grid g;
+    int st = make_grid(p, &g);
+    if (st) return st;
+    double S = 0.0;
+    int bad = 0;
+    double w[7];
+    for (long c = 0; c < g.ncell; c++) {
+        load_prim(&g, q, c, w);
+        double rho = w[0] + w[1];
+        double G, Pi;
+        mixture(&g, w[IA(&g)], &G, &Pi);
+        double c2 = sound2(G, Pi, rho, w[IE(&g)]);
+        if (!(rho > 0.0) || !(c2 > 0.0)) bad = 1;
+        double cs = sqrt(c2);
+        double s = 0.0;
+        for (int d = 0; d < g.ndim; d++) s = s + (fabs(w[2 + d]) + cs) / g.dx[d];
+        if (s > S) S = s;
+    }
+    *S_out = S;
+    return bad ? ORC_ENONPHYSICAL : ORC_OK;
+}
+
+/* One Shu-Osher TVD-RK3 step of size dt, in place:
+ *   q1 = qn + dt L(qn)
+ *   q2 = 3/4 qn + 1/4 (q1 + dt L(q1))
+ *   qn+1 = 1/3 qn + 2/3 (q2 + dt L(q2)) */
+int orc_step_dt(const orc_params* p, double* q, double dt) {
+    grid g;
+    int st = make_grid(p, &g);
+    if (st) return st;
+    long m = (long)g.neq * g.ncell;
+    double* L = malloc(sizeof(double) * m);
+    double* q1 = malloc(sizeof(double) * m);
+    double* q2 = malloc(sizeof(double) * m);
+    if (!L || !q1 || !q2) { free(L); free(q1); free(q2); return ORC_ENOMEM; }
+    int bad = 0;
+    bad |= rhs_all(&g, q, L) != ORC_OK;
+    for (long i = 0; i < m; i++) q1[i] = q[i] + dt * L[i];
+    bad |= rhs_all(&g, q1, L) != ORC_OK;
+    for (long i = 0; i < m; i++) q2[i] = 0.75 * q[i] + 0.25 * (q1[i] + dt * L[i]);
+    bad |= rhs_all(&g, q2, L) != ORC_OK;
+    for (long i = 0; i < m; i++) q[i] = (1.0 / 3.0) * q[i] + (2.0 / 3.0) * (q2[i] + dt * L[i]);
+    free(L); free(q1); free(q2);
+    return bad ? ORC_ENONPHYSICAL : ORC_OK;
+}
+
+/* nsteps steps with dt_n = cfl / S(q^n); t_out receives the sum of the dt_n. */
+int orc_run_cfl(const orc_params* p, double* q, double cfl, int nsteps, double* t_out) {
+    double t = 0.0;
+    int st = ORC_OK;
+    for (int n = 0; n < nsteps; n++) {
+        double S;
+        st = orc_max_wavespeed(p, q, &S);
+        if (st) break;
+        double dt = cfl / S;
+        st = orc_step_dt(p, q, dt);
+        t = t + dt;
+        if (st) break;
+    }
+    if (t_out) *t_out = t;
+    return st;
+}
+
+/* ---- element-level entry points used by the unit pins -------------------- */
+
+void orc_weno5_cell(double eps, const double* v5, double* vm, double* vp) { weno5(eps, v5, vm, vp); }
+
+int orc_hllc_face(const orc_params* p, int dir, const double* wL, const double* wR, double* F,
+                  double* uf) {
+    grid g;
+    int st = make_grid(p, &g);
+    if (st) return st;
+    if (dir < 0 || dir >= g.ndim) return ORC_EINVAL;
+    return hllc(&g, dir, wL, wR, F, uf) ? ORC_ENONPHYSICAL : ORC_OK;
+}
+
+int orc_sound_speed2(const orc_params* p, const double* w, double* c2) {
+    grid g;
+    int st = make_grid(p, &g);
+    if (st) return st;
+    double G, Pi;
+    mixture(&g, w[IA(&g)], &G, &Pi);
+    *c2 = sound2(G, Pi, w[0] + w[1], w[IE(&g)]);
+    return ORC_OK;
+}

@@ -1,0 +1,296 @@
+"""Seeded synthetic initial conditions for the five-equation solver.
+
+This module is the one piece shared by the CUDA path and the CPU oracle.  It
+holds none of the solver's arithmetic: it lays out *primitive* fields
+``w[f][z][y][x]`` (x fastest; unused dimensions have size 1) with the slots
+
+    0: alpha1 rho1   1: alpha2 rho2   2..2+d-1: u_k   2+d: p   3+d: alpha1
+
+and a plain ``dict`` of run parameters.  Each side converts ``w`` to the
+conservative state with its own equation of state.
+
+Fluid 1 is water (gamma 4.4, pi_inf 6e8 Pa), fluid 2 is air (gamma 1.4,
+pi_inf 0), as in the stiffened-gas description of Sec. II-A.  Interfaces are
+sharp, decided at cell centres; a pure phase carries the other phase at volume
+fraction 1e-6.  Shock states are the ideal-gas normal-shock (Rankine-Hugoniot)
+relations for air moving into air at rest.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+WATER = (4.4, 6.0e8)
+AIR = (1.4, 0.0)
+ALPHA_EPS = 1.0e-6
+TRANSMISSIVE, PERIODIC = 0, 1
+
+
+def make_params(ndim, n, lo, hi, bc, gamma=(WATER[0], AIR[0]), pi_inf=(WATER[1], AIR[1]),
+                weno_eps=1e-6) -> dict:
+    """Plain parameter dict; n/lo/hi padded to 3 entries, bc to 3 pairs."""
+    n = list(n) + [1] * (3 - len(n))
+    lo = list(lo) + [0.0] * (3 - len(lo))
+    hi = list(hi) + [1.0] * (3 - len(hi))
+    if isinstance(bc, int):
+        bc = [[bc, bc]] * ndim
+    bc = [list(b) for b in bc] + [[TRANSMISSIVE, TRANSMISSIVE]] * (3 - len(bc))
+    return {"ndim": int(ndim), "n": [int(v) for v in n], "lo": [float(v) for v in lo],
+            "hi": [float(v) for v in hi], "bc": bc, "gamma": [float(g) for g in gamma],
+            "pi_inf": [float(p) for p in pi_inf], "weno_eps": float(weno_eps)}
+
+
+def neq_of(p: dict) -> int:
+    return p["ndim"] + 4
+
+
+def shape_of(p: dict):
+    """Array shape [neq, nz, ny, nx] of a state for params p."""
+    n = p["n"]
+    return (neq_of(p), n[2], n[1], n[0])
+
+
+def cell_centres(p: dict):
+    """1-D coordinate arrays (x, y, z) of cell centres."""
+    out = []
+    for d in range(3):
+        n = p["n"][d]
+        h = (p["hi"][d] - p["lo"][d]) / n
+        out.append(p["lo"][d] + (np.arange(n, dtype=np.float64) + 0.5) * h)
+    return out
+
+
+def assemble(p: dict, alpha1, rho1, rho2, vel, pres) -> np.ndarray:
+    """Primitive array from broadcastable per-cell fields.
+
+    alpha1: volume fraction of fluid 1; rho1, rho2: phase densities;
+    vel: list of ndim velocity components; pres: pressure."""
+    shp = shape_of(p)
+    w = np.empty(shp, dtype=np.float64)
+    d = p["ndim"]
+    a1 = np.broadcast_to(alpha1, shp[1:])
+    w[0] = a1 * rho1
+    w[1] = (1.0 - a1) * rho2
+    for k in range(d):
+        w[2 + k] = vel[k]
+    w[2 + d] = pres
+    w[3 + d] = a1
+    return w
+
+
+def normal_shock(gamma: float, rho1: float, p1: float, mach: float):
+    """Ideal-gas shock of Mach number `mach` moving in +x into gas at rest.
+
+    Returns (rho2, u2, p2, s): post-shock density, velocity, pressure and the
+    shock speed s = mach * c1."""
+    g = gamma
+    m2 = mach * mach
+    p2 = p1 * (1.0 + 2.0 * g / (g + 1.0) * (m2 - 1.0))
+    rho2 = rho1 * (g + 1.0) * m2 / ((g - 1.0) * m2 + 2.0)
+    s = mach * math.sqrt(g * p1 / rho1)
+    u2 = s * (1.0 - rho1 / rho2)
+    return rho2, u2, p2, s
+
+
+# ---------------------------------------------------------------------------
+# one-dimensional cases
+# ---------------------------------------------------------------------------
+
+def air_water_shock_tube(n: int = 1000):
+    """Two-fluid shock tube on [0,1]: water (p 1e9) for x < 0.7, air (rho 50,
+    p 1e5) for x >= 0.7, at rest; transmissive ends."""
+    p = make_params(1, [n], [0.0], [1.0], TRANSMISSIVE)
+    x, _, _ = cell_centres(p)
+    water = x < 0.7
+    a1 = np.where(water, 1.0 - ALPHA_EPS, ALPHA_EPS)[None, None, :]
+    pres = np.where(water, 1.0e9, 1.0e5)[None, None, :]
+    return p, assemble(p, a1, 1000.0, 50.0, [0.0], pres)
+
+
+def sod(n: int):
+    """Sod's problem for one ideal gas (gamma 1.4): (rho,u,p) = (1,0,1) for
+    x < 0.5 and (0.125,0,0.1) beyond; alpha1 = 1 everywhere."""
+    p = make_params(1, [n], [0.0], [1.0], TRANSMISSIVE, gamma=(1.4, 1.4), pi_inf=(0.0, 0.0))
+    x, _, _ = cell_centres(p)
+    left = x < 0.5
+    rho = np.where(left, 1.0, 0.125)[None, None, :]
+    pres = np.where(left, 1.0, 0.1)[None, None, :]
+    return p, assemble(p, 1.0, rho, 0.0, [0.0], pres)
+
+
+def smooth_density_wave(n: int, amp: float = 0.2):
+    """Periodic density wave rho = 1 + amp sin(2 pi x) (exact cell averages),
+    u = 1, p = 1, two identical ideal gases at alpha1 = 1/2."""
+    p = make_params(1, [n], [0.0], [1.0], PERIODIC, gamma=(1.4, 1.4), pi_inf=(0.0, 0.0))
+    x, _, _ = cell_centres(p)
+    h = 1.0 / n
+    rho = 1.0 + amp * np.sin(2.0 * math.pi * x) * (math.sin(math.pi * h) / (math.pi * h))
+    rho = rho[None, None, :]
+    return p, assemble(p, 0.5, rho, rho, [1.0], 1.0)
+
+
+def air_shock_1d(n: int, mach: float = 2.0, x_shock: float = 0.25):
+    """A single Mach-`mach` shock in air (rho 1.2, p 1e5) at x_shock moving in
+    +x; fluid 1 absent (alpha1 = 1e-6)."""
+    p = make_params(1, [n], [0.0], [1.0], TRANSMISSIVE)
+    x, _, _ = cell_centres(p)
+    rho2, u2, p2, _ = normal_shock(AIR[0], 1.2, 1.0e5, mach)
+    post = x < x_shock
+    rho = np.where(post, rho2, 1.2)[None, None, :]
+    u = np.where(post, u2, 0.0)[None, None, :]
+    pres = np.where(post, p2, 1.0e5)[None, None, :]
+    return p, assemble(p, ALPHA_EPS, 1000.0, rho, [u], pres)
+
+
+# ---------------------------------------------------------------------------
+# multi-dimensional cases
+# ---------------------------------------------------------------------------
+
+def air_water_slab(ndim: int, n: int, u0: float = 100.0, axis: int = 0):
+    """Periodic box [0,1]^ndim at uniform p = 1e5 and velocity u0 along `axis`
+    with a water slab 0.3 <= x_axis < 0.6 (rho 1000) in air (rho 1.2)."""
+    p = make_params(ndim, [n] * ndim, [0.0] * ndim, [1.0] * ndim, PERIODIC)
+    c = cell_centres(p)
+    xa = c[axis]
+    inside = (xa >= 0.3) & (xa < 0.6)
+    shp = [1, 1, 1]
+    shp[2 - axis] = len(xa)
+    a1 = np.where(inside, 1.0 - ALPHA_EPS, ALPHA_EPS).reshape(shp)
+    vel = [0.0] * ndim
+    vel[axis] = u0
+    return p, assemble(p, a1, 1000.0, 1.2, vel, 1.0e5)
+
+
+def random_periodic(ndim: int, n: int, seed: int = 0):
+    """Periodic box with smooth random fields plus a two-fluid interface: a
+    few random Fourier modes in density, velocity and pressure, and a water
+    blob of radius 0.25 (alpha1 ~ 1, tanh profile about 1.5 cells wide) in
+    air.  Used for conservation and parity checks."""
+    rng = np.random.default_rng(seed)
+    p = make_params(ndim, [n] * ndim, [0.0] * ndim, [1.0] * ndim, PERIODIC)
+    c = cell_centres(p)
+    grids = np.meshgrid(*c[:ndim][::-1], indexing="ij")[::-1]   # x, y, z broadcast [nz,ny,nx]
+    shp = shape_of(p)[1:]
+    grids = [g.reshape(shp) for g in grids]
+
+    def modes(scale):
+        f = np.zeros(shp)
+        for _ in range(3):
+            k = rng.integers(1, 3, size=ndim)
+            ph = rng.uniform(0, 2 * math.pi)
+            arg = sum(2 * math.pi * k[d] * grids[d] for d in range(ndim)) + ph
+            f = f + scale * rng.uniform(0.3, 1.0) * np.sin(arg)
+        return f
+
+    r = np.sqrt(sum((grids[d] - 0.5) ** 2 for d in range(ndim)))
+    width = 1.5 / n
+    a1 = np.clip(0.5 * (1.0 + np.tanh((0.25 - r) / width)), ALPHA_EPS, 1.0 - ALPHA_EPS)
+    rho1 = 1000.0 * (1.0 + 0.01 * modes(1.0))
+    rho2 = 1.2 * (1.0 + 0.2 * modes(1.0))
+    vel = [20.0 * modes(1.0) for _ in range(ndim)]
+    pres = 1.0e7 * (1.0 + 0.2 * modes(1.0))
+    return p, assemble(p, a1, rho1, rho2, vel, pres)
+
+
+def shock_water_column(nx: int = 1024, ny: int = 512, seed: int = 2409, mach: float = 1.47,
+                       gap: float = 0.03):
+    """Mach-1.47 shock in air (rho 1.2, p 1e5) approaching a water column of
+    radius 0.1 centred at (0.5, 0.5) on [0,2]x[0,1] (transmissive sides).
+
+    The interface radius is r(theta) = 0.1 [1 + 0.01 sum_{k=2..9} a_k
+    cos(k theta + phi_k)] with a_k ~ U[-1,1] scaled to sum |a_k| = 1 and
+    phi_k ~ U[0, 2 pi) from `seed`.  The shock starts `gap` upstream of the
+    column's leftmost point so that it reaches the column within the run."""
+    rng = np.random.default_rng(seed)
+    a = rng.uniform(-1.0, 1.0, size=8)
+    a = a / np.abs(a).sum()
+    phi = rng.uniform(0.0, 2.0 * math.pi, size=8)
+    ks = np.arange(2, 10)
+    p = make_params(2, [nx, ny], [0.0, 0.0], [2.0, 1.0], TRANSMISSIVE)
+    x, y, _ = cell_centres(p)
+    X = x[None, :]
+    Y = y[:, None]
+    cx, cy, r0 = 0.5, 0.5, 0.1
+    th = np.arctan2(Y - cy, X - cx)
+    pert = np.zeros_like(th)
+    for k, ak, pk in zip(ks, a, phi):
+        pert = pert + ak * np.cos(k * th + pk)
+    rad = r0 * (1.0 + 0.01 * pert)
+    water = ((X - cx) ** 2 + (Y - cy) ** 2) < rad ** 2
+    tt = np.linspace(0.0, 2.0 * math.pi, 4096)
+    rmax = r0 * (1.0 + 0.01 * np.max(np.sum(a[:, None] * np.cos(ks[:, None] * tt + phi[:, None]), 0)))
+    xs = cx - rmax - gap
+    rho2, u2, p2, _ = normal_shock(AIR[0], 1.2, 1.0e5, mach)
+    post = np.broadcast_to(X < xs, water.shape)
+    a1 = np.where(water, 1.0 - ALPHA_EPS, ALPHA_EPS)[None]
+    rho_air = np.where(post, rho2, 1.2)[None]
+    u = np.where(post, u2, 0.0)[None]
+    pres = np.where(post, p2, 1.0e5)[None]
+    return p, assemble(p, a1, 1000.0, rho_air, [u, 0.0], pres)
+
+
+def droplet_layout(seed: int = 2409, count: int = 8, gap: float = 0.01):
+    """Non-overlapping droplets: radii U[0.05, 0.1], centres uniform over
+    [0.3,0.9] x [0.15,0.85]^2, rejection-sampled so that centre distances
+    exceed r_i + r_j + gap.  Returns an array [count, 4] of (cx, cy, cz, r)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    while len(out) < count:
+        r = rng.uniform(0.05, 0.1)
+        c = np.array([rng.uniform(0.3, 0.9), rng.uniform(0.15, 0.85), rng.uniform(0.15, 0.85)])
+        if all(np.linalg.norm(c - o[:3]) >= r + o[3] + gap for o in out):
+            out.append(np.array([c[0], c[1], c[2], r]))
+    return np.stack(out)
+
+
+def shock_droplets(n: int = 256, seed: int = 2409, mach: float = 2.0, gap: float = 0.01,
+                   count: int = 8):
+    """Mach-2 shock in air (rho 1.2, p 1e5) over `count` water droplets on
+    [0,1]^3 (transmissive sides).  Droplets from `droplet_layout(seed)`; the
+    shock starts `gap` upstream of the leftmost droplet surface."""
+    drops = droplet_layout(seed, count)
+    p = make_params(3, [n, n, n], [0.0] * 3, [1.0] * 3, TRANSMISSIVE)
+    x, y, z = cell_centres(p)
+    water = np.zeros((n, n, n), dtype=bool)
+    for cx, cy, cz, r in drops:
+        d2 = (x[None, None, :] - cx) ** 2 + (y[None, :, None] - cy) ** 2
+        d2 = d2 + (z[:, None, None] - cz) ** 2
+        water |= d2 < r * r
+    xs = float(np.min(drops[:, 0] - drops[:, 3])) - gap
+    rho2, u2, p2, _ = normal_shock(AIR[0], 1.2, 1.0e5, mach)
+    post = (x < xs)[None, None, :]
+    a1 = np.where(water, 1.0 - ALPHA_EPS, ALPHA_EPS)
+    rho_air = np.where(post, rho2, 1.2)
+    u = np.where(post, u2, 0.0)
+    pres = np.where(post, p2, 1.0e5)
+    return p, assemble(p, a1, 1000.0, rho_air, [u, 0.0, 0.0], pres)
+
+
+def embed_1d(p1d: dict, w1d: np.ndarray, axis: int, m: int = 4):
+    """Lay a 1-D case along `axis` of a 3-D box with m cells in the other two
+    directions (transmissive there).  Velocity goes to component `axis`."""
+    n = p1d["n"][0]
+    ns = [m, m, m]
+    ns[axis] = n
+    lo = [0.0] * 3
+    hi = [1.0] * 3
+    lo[axis] = p1d["lo"][0]
+    hi[axis] = p1d["hi"][0]
+    bc = [[TRANSMISSIVE, TRANSMISSIVE] for _ in range(3)]
+    bc[axis] = list(p1d["bc"][0])
+    p = make_params(3, ns, lo, hi, bc, p1d["gamma"], p1d["pi_inf"], p1d["weno_eps"])
+    shp = [1, 1, 1]
+    shp[2 - axis] = n
+    line = {k: w1d[k, 0, 0, :].reshape(shp) for k in range(5)}
+    vel = [0.0, 0.0, 0.0]
+    vel[axis] = line[2]
+    a1 = line[4]
+    w = np.empty(shape_of(p))
+    w[0] = line[0]
+    w[1] = line[1]
+    for k in range(3):
+        w[2 + k] = vel[k]
+    w[5] = line[3]
+    w[6] = a1
+    return p, w

@@ -1,0 +1,66 @@
+"""The oracle's pins are strong enough to catch plausible mistakes.
+
+Each case plants one mistake in a temporary copy of the oracle's C source (a
+dropped term, a wrong sign, coefficient or index, a swapped operand), builds
+it, and runs the oracle pin suites against that build in a subprocess: at
+least one pin must fail.  Nothing here touches the real oracle build.
+"""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "mfc5_oracle.c")
+
+MUTATIONS = {
+    "drop_alpha_source": ("L[IA(g)] = L[IA(g)] + a1 * (UF[i + 1] - UF[i]) / dx;", "L[IA(g)] = L[IA(g)];"),
+    "source_sign": ("L[IA(g)] = L[IA(g)] + a1 * (UF[i + 1] - UF[i]) / dx;",
+                    "L[IA(g)] = L[IA(g)] - a1 * (UF[i + 1] - UF[i]) / dx;"),
+    "alpha_flux_uK": ("F[IA(g)] = K->a1 * Ss;", "F[IA(g)] = K->a1 * un;"),
+    "beta0_coefficient": ("0.25 * sq(v[0] - 4.0 * v[1] + 3.0 * v[2])", "0.25 * sq(v[0] - 4.0 * v[1] + 2.0 * v[2])"),
+    "linear_weight": ("double a0 = 0.1 / sq(eps + b0);", "double a0 = 0.3 / sq(eps + b0);"),
+    "candidate_index": ("double p1 = (-v[1] + 5.0 * v[2] + 2.0 * v[3]) / 6.0;",
+                        "double p1 = (-v[1] + 5.0 * v[2] + 2.0 * v[4]) / 6.0;"),
+    "eps_power": ("double a1 = 0.6 / sq(eps + b1);", "double a1 = 0.6 / (eps + b1);"),
+    "face_states_swapped": ("hllc(g, d, &VM[(j + 1) * neq], &VP[(j + 2) * neq]",
+                            "hllc(g, d, &VP[(j + 1) * neq], &VM[(j + 2) * neq]"),
+    "star_energy_sign": ("(Ss - un) * (K->rho * Ss + K->p / (SK - un))",
+                         "(Ss - un) * (K->rho * Ss - K->p / (SK - un))"),
+    "star_tangential": ("chi * K->rho * K->u[k];", "K->rho * K->u[k];"),
+    "chi_shifted": ("double chi = (SK - un) / (SK - Ss);", "double chi = (SK - un) / (SK - Ss + 1e-3);"),
+    "sstar_sign": ("double num = R.p - L.p + L.rho", "double num = L.p - R.p + L.rho"),
+    "davis_right": ("double SR = (uL + cL > uR + cR) ? uL + cL : uR + cR;", "double SR = uR + cR;"),
+    "face_velocity": ("        star_flux(g, dir, wL, &L, SL, Ss, F);\n        *uf = Ss;",
+                      "        star_flux(g, dir, wL, &L, SL, Ss, F);\n        *uf = uL;"),
+    "momentum_pressure": ("F[2 + dir] = F[2 + dir] + K->p;", "F[2 + dir] = F[2 + dir];"),
+    "energy_flux": ("F[IE(g)] = (K->E + K->p) * un;", "F[IE(g)] = (K->E) * un;"),
+    "sound_speed": ("return ((G + 1.0) * p + Pi) / (G * rho);", "return ((G + 1.0) * p + Pi) / (rho);"),
+    "mixture_Pi": ("*Pi = a1 * g->P1 + a2 * g->P2;", "*Pi = a1 * g->P1 + a1 * g->P2;"),
+    "mixture_Gamma": ("*G = a1 * g->g1 + a2 * g->g2;", "*G = a1 * g->g1 + a2 * g->g1;"),
+    "kinetic_half": ("return 0.5 * rho * s;", "return rho * s;"),
+    "rk_stage2": ("0.75 * q[i] + 0.25 * (q1[i] + dt * L[i])", "0.75 * q[i] + 0.25 * (q1[i] + 0.5 * dt * L[i])"),
+    "rk_stage3": ("(2.0 / 3.0) * (q2[i] + dt * L[i])", "(2.0 / 3.0) * (q2[i] + dt * L[i] * 0.99)"),
+    "periodic_ghosts": ("if (periodic) {", "if (0) {"),
+    "wavespeed_dx": ("s = s + (fabs(w[2 + d]) + cs) / g.dx[d];", "s = s + (fabs(w[2 + d]) + cs);"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_planted_mistake_is_caught(name, tmp_path):
+    before, after = MUTATIONS[name]
+    src = open(SRC).read()
+    assert src.count(before) >= 1, "mutation anchor no longer in the oracle source"
+    csrc = tmp_path / "mutant.c"
+    csrc.write_text(src.replace(before, after))
+    so = tmp_path / "libmutant.so"
+    subprocess.run(["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o",
+                    str(so), str(csrc), "-lm"], check=True)
+    env = dict(os.environ, MFC5_ORACLE_LIB=str(so))
+    suites = [os.path.join(ROOT, "tests", f) for f in
+              ("test_oracle_elements.py", "test_oracle_physics.py")]
+    r = subprocess.run([sys.executable, "-m", "pytest", *suites, "-x", "-q", "-p", "no:cacheprovider",
+                        "-m", "not gpu"], cwd=ROOT, env=env, capture_output=True, text=True,
+                       timeout=600)
+    assert r.returncode != 0, f"mutation {name} passed every pin:\n{r.stdout[-2000:]}"
