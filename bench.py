@@ -1,0 +1,383 @@
+#!/usr/bin/env python
+"""Benchmark of the five-equation RHS hot path (WENO5-JS + HLLC + SSP-RK3).
+
+Metric: grind time, ns per (cell x equation x RHS evaluation), lower is better,
+and the fraction of the HBM roofline it reaches, for the FP64 and mixed forms.
+
+Workload (per GPU): the 3-D shock / droplet array, 256^3 cells, 7 equations,
+FP64, SSP-RK3 at CFL 0.4 (the timed "step" is one RK3 step = 3 RHS
+evaluations).  The mixed form runs the same setup at 512^3.  Inputs are
+seeded synthetic states generated by paper_2409_10729_gb300.inputs.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank runs its own replica (weak scaling, no collective in
+the data path); rank 0 prints one JSON line.  `--impl reference` times the
+serial CPU oracle on the host cores (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "grind time ns/(cell·eq·RHS) & % HBM roofline: FP64 vs mixed vs MLP-gated"
+UNIT = "ns/(cell*eq*RHS)"
+CFL = 0.4
+
+# Algorithmic work per cell and direction of one sweep, counted from the
+# oracle's formulas (every +, -, *, /, sqrt counts 1):
+# cons->prim 22, WENO5-JS 107 per field, HLLC 122 per face, divergence 18.
+FLOPS_CELL_DIR_3D = 22 + 107 * 7 + 122 + 18          # 911
+FLOPS_RK_CELL = 28                                     # stage update, mean over the 3 stages
+FLOPS_WAVESPEED_CELL = 45                              # once per step, in the last stage
+# Algorithmic bytes per cell, equation and RHS: stage 1 reads q^n and writes
+# q^(1); stages 2-3 read q^(k) and q^n and write q^(k+1): 8/3 state arrays.
+ALG_BYTES = {"fp64": 8.0 / 3.0 * 8.0, "mixed": (12.0 + 16.0 + 20.0) / 3.0}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.proc = None
+        self.out_path = os.path.join("/tmp", f"mfc5_clocks_{os.getpid()}.csv")
+        try:
+            self.fh = open(self.out_path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(device_index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.out_path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 7:
+                    continue
+                try:
+                    sm.append(float(parts[0]))
+                    smax.append(float(parts[1]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[3:7]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.out_path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def read_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
+    was taken on the current kernel source (else None)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    src = b""
+    for f in ("sweep.cuh", "physics.cuh"):
+        with open(os.path.join(ROOT, "paper_2409_10729_gb300", "csrc", f), "rb") as fh:
+            src += fh.read()
+    sha = hashlib.sha256(src).hexdigest()[:16]
+    try:
+        with open(path) as fh:
+            for line in fh:
+                parts = line.split()
+                if len(parts) >= 3 and parts[0] == kernel and parts[2] == sha:
+                    return float(parts[1])
+    except OSError:
+        pass
+    return None
+
+
+def time_form(form, p, w, steps, warmup, device_index, rank, world):
+    """Run `warmup` + `steps` RK3 steps of one form; returns a result dict."""
+    import torch
+    from paper_2409_10729_gb300 import mfc
+    s = mfc.Solver(p, form)
+    s.set_state_prim(w)
+    s.step_rk3(CFL, warmup)
+    s.set_timing(True)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    sampler = ClockSampler(device_index)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream()
+    ev0.record(stream)
+    t_adv = s.step_rk3(CFL, steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+        torch.distributed.barrier()
+    kt = s.kernel_times()
+    launches = s.launches_per_step() * steps
+    s.set_timing(False)
+    ncell = p["n"][0] * p["n"][1] * p["n"][2]
+    neq = p["ndim"] + 4
+    grind = ms * 1e6 / (steps * 3 * ncell * neq * world)
+    s.close()
+    del s
+    torch.cuda.empty_cache()
+    return {"ms": ms, "grind": grind, "kernels": kt, "launches": launches, "clocks": clocks,
+            "t_advanced": t_adv, "ncell": ncell, "neq": neq}
+
+
+def roofline_for(form, res, peak_alu, alu_src, hbm_peak, hbm_src):
+    """Roofline object for the dominant kernel of one form."""
+    kt = res["kernels"]
+    name = max((k for k in kt if kt[k][1] > 0), key=lambda k: kt[k][0])
+    total_ms, count = kt[name]
+    avg_s = total_ms / count * 1e-3
+    ncell = res["ncell"]
+    flops = FLOPS_CELL_DIR_3D
+    if name == "sweep_y":
+        flops += 7
+    if name == "sweep_z":
+        flops += 7 + FLOPS_RK_CELL + FLOPS_WAVESPEED_CELL / 3.0
+    achieved = flops * ncell / avg_s / 1e12
+    share = total_ms / sum(v[0] for v in kt.values())
+    return {"bound": "alu", "kernel": name, "achieved": round(achieved, 4), "peak": round(peak_alu, 3),
+            "unit": "TFLOP/s", "frac": round(achieved / peak_alu, 4), "peak_source": alu_src,
+            "traffic": read_traffic(f"{form}:{name}"), "share_of_step": round(share, 3),
+            "avg_launch_ms": round(total_ms / count, 4),
+            "algorithmic_flops_per_cell": flops,
+            "hbm": {"achieved_gbs": round(ALG_BYTES[form] / res["grind"], 1), "peak": hbm_peak,
+                    "frac": round(ALG_BYTES[form] / res["grind"] / hbm_peak, 4), "peak_source": hbm_src}}
+
+
+def cpu_baseline(target_s=15.0):
+    """The oracle, as it stands, on a z-slab of the 256^3 shock-droplet state:
+    one RHS evaluation per sample, sized to about target_s seconds."""
+    import numpy as np
+    import oracle as O
+    from paper_2409_10729_gb300 import inputs as I
+    p, w = I.shock_droplets(256)
+    z0 = 96
+    q_all = None
+
+    def sample(k):
+        ps = dict(p)
+        ps["n"] = [256, 256, k]
+        ps["lo"] = [0.0, 0.0, z0 / 256.0]
+        ps["hi"] = [1.0, 1.0, (z0 + k) / 256.0]
+        ws = np.ascontiguousarray(w[:, z0:z0 + k])
+        q = O.prim_to_cons(ps, ws)
+        t0 = time.perf_counter()
+        O.rhs(ps, q)
+        return time.perf_counter() - t0, ps
+
+    t1, _ = sample(2)
+    k = max(2, min(160, int(target_s / max(t1 / 2, 1e-6))))
+    t, ps = sample(k)
+    ncell = 256 * 256 * k
+    grind = t * 1e9 / (ncell * 7)
+    return {"value": round(grind, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one oracle RHS on a 256x256x{k} z-slab (z from {z0}) of the 256^3 shock-droplet "
+                      f"initial state, {t:.1f} s"}, t, k
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    import oracle as O
+    O.build()
+    # size each step so the whole run stays within ~3 minutes
+    per_step = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    base, t, k = cpu_baseline(per_step)
+    import numpy as np
+    from paper_2409_10729_gb300 import inputs as I
+    p, w = I.shock_droplets(256)
+    z0 = 96
+    ps = dict(p)
+    ps["n"] = [256, 256, k]
+    ps["lo"] = [0.0, 0.0, z0 / 256.0]
+    ps["hi"] = [1.0, 1.0, (z0 + k) / 256.0]
+    q = O.prim_to_cons(ps, np.ascontiguousarray(w[:, z0:z0 + k]))
+    for _ in range(args.warmup):
+        O.rhs(ps, q)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.rhs(ps, q)
+    el = time.perf_counter() - t0
+    grind = el * 1e9 / (args.steps * 256 * 256 * k * 7)
+    line = {"metric": METRIC, "value": round(grind, 4), "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(el * 1e3 / args.steps, 2),
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": "3-D shock-droplet array 256^3 (7 eq), FP64 RHS; oracle on a "
+                                   f"256x256x{k} z-slab sample per step", "cells_per_step": 256 * 256 * k,
+                       "neq": 7},
+            "cpu_baseline": {"value": round(grind, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"one oracle RHS per step on a 256x256x{k} z-slab of the 256^3 "
+                                       "shock-droplet initial state"},
+            "e2e": {"value": round(grind, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2409_10729_gb300 import build as B
+    if rank == 0:
+        B.build()
+    if world > 1:
+        torch.distributed.barrier()
+    from paper_2409_10729_gb300 import inputs as I
+    from paper_2409_10729_gb300 import mfc
+
+    hbm_peak, hbm_src = measured_peaks()
+    fp64_peak = mfc.alu_peak(True)
+    fp32_peak = mfc.alu_peak(False)
+
+    p, w = I.shock_droplets(256)
+    res = time_form("fp64", p, w, args.steps, args.warmup, local, rank, world)
+    forms = {"fp64": res}
+    if not args.no_mixed:
+        pm, wm = I.shock_droplets(512)
+        forms["mixed"] = time_form("mixed", pm, wm, max(2, args.steps // 2), args.warmup, local, rank, world)
+        del wm
+
+    # end to end through the C ABI with pinned host buffers: per step, copy
+    # q^n in, one RK3 step, copy q^{n+1} out
+    s = mfc.Solver(p, "fp64")
+    s.set_state_prim(w)
+    q_host = torch.empty(s.shape, dtype=torch.float64).pin_memory().numpy()
+    q_out = torch.empty(s.shape, dtype=torch.float64).pin_memory().numpy()
+    s.get_state(q_host)
+    e2e_steps = max(2, min(args.steps, 5))
+    s.set_state(q_host)
+    s.step_rk3(CFL, 1)
+    s.get_state(q_out)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        s.set_state(q_host)
+        s.step_rk3(CFL, 1)
+        s.get_state(q_out)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    ncell, neq = res["ncell"], res["neq"]
+    e2e_grind = e2e_s * 1e9 / (e2e_steps * 3 * ncell * neq * world)
+    s.close()
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.barrier()
+            torch.distributed.destroy_process_group()
+        return
+    base = None
+    if world == 1 and not args.no_cpu_baseline:
+        base, _, _ = cpu_baseline()
+
+    roof = roofline_for("fp64", res, fp64_peak, "measured (FP64 FMA-chain probe)", hbm_peak, hbm_src)
+    out_forms = {}
+    for name, r in forms.items():
+        peak = fp64_peak if name == "fp64" else fp32_peak
+        rf = roofline_for(name, r, peak, "measured FMA-chain probe", hbm_peak, hbm_src)
+        out_forms[name] = {"grind": round(r["grind"], 5), "unit": UNIT, "ms_per_step": round(r["ms"] / (
+            args.steps if name == "fp64" else max(2, args.steps // 2)), 3), "cells": r["ncell"],
+            "hbm_frac": rf["hbm"]["frac"], "hbm_gbs_algorithmic": rf["hbm"]["achieved_gbs"],
+            "alu_frac": rf["frac"], "dominant_kernel": rf["kernel"],
+            "kernel_ms": {k: round(v[0] / max(1, v[1]), 4) for k, v in r["kernels"].items() if v[1]},
+            "clocks": r["clocks"]}
+    line = {
+        "metric": METRIC, "value": round(res["grind"], 5), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(res["ms"] / args.steps, 3),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "3-D shock-droplet array, 256^3 cells, 7 equations, FP64, SSP-RK3 at CFL 0.4 "
+                               "(step = one RK3 step = 3 RHS evaluations)",
+                   "cells": ncell, "neq": neq, "precision": "fp64", "parallelism": f"replicas x{world}",
+                   "l2": "no flush: each state array is 0.94 GB (7 fields x 256^3 x 8 B) > 129 MB L2"},
+        "roofline": roof,
+        "forms": out_forms,
+        "e2e": {"value": round(e2e_grind, 5), "unit": UNIT, "h2d_bytes_per_step": ncell * neq * 8,
+                "d2h_bytes_per_step": ncell * neq * 8, "steps": e2e_steps},
+        "gpu_launches": res["launches"],
+        "clocks": res["clocks"],
+        "cpu_baseline": base,
+        "alu_peaks_tflops": {"fp64": round(fp64_peak, 3), "fp32": round(fp32_peak, 2)},
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision form")
+    ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle timing")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

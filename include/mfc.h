@@ -1,0 +1,139 @@
+/*
+ * mfc.h -- C ABI of the GB300 five-equation solver library (libmfc5.so).
+ *
+ * The library evaluates and advances the semi-discrete two-fluid
+ * five-equation (Allaire) model with the stiffened-gas equation of state
+ * (arXiv 2409.10729, Sec. II-A), discretised by finite volumes on a uniform
+ * Cartesian grid with WENO5-JS reconstruction of primitive variables and HLLC
+ * fluxes (Sec. II-B, Eq. (eqn:discretization) and its cell-integrated form),
+ * advanced in time by Shu-Osher SSP-RK3.  All compute runs in the library's
+ * own CUDA kernels on one GPU; there is no CPU fallback.
+ *
+ * Conventions shared by every entry point
+ *   - State layout: conservative q[f][z][y][x], x fastest, interior cells
+ *     only, FP64.  f = 0: alpha1*rho1, 1: alpha2*rho2, 2..2+d-1: rho*u_k,
+ *     2+d: rho*E, 3+d: alpha1, with d = ndim and neq = d + 4 fields.  The
+ *     primitive layout w has u_k in place of rho*u_k and p in place of rho*E.
+ *   - Pointers flagged on_device = 1 are device pointers on the device the
+ *     context was created on; on_device = 0 means host memory.  Copies are
+ *     ordered on the context's stream; calls that return host data
+ *     synchronise that stream before returning.
+ *   - The context owns all device memory it allocates; the caller owns every
+ *     pointer it passes in and keeps it valid until the call returns.
+ *   - Every call returns an mfc_status.  Nothing aborts, traps or prints.
+ *   - One context must not be used from two threads at once.
+ */
+#ifndef MFC5_H
+#define MFC5_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mfc_ctx mfc_ctx;
+
+typedef enum {
+    MFC_OK = 0,
+    MFC_EINVAL = -1,        /* bad argument or parameter */
+    MFC_ENOMEM = -2,        /* device or pinned-host allocation failed */
+    MFC_ECUDA = -3,         /* a CUDA runtime call failed (see mfc_last_cuda_error) */
+    MFC_ENONPHYSICAL = -4,  /* a face or cell state had rho<=0, c^2<=0 or NaN */
+    MFC_ESTATE = -5         /* call out of order (e.g. stepping before a state is set) */
+} mfc_status;
+
+typedef enum {
+    MFC_FP64 = 0,   /* every step in FP64 */
+    MFC_MIXED = 1,  /* FP32 state/stencils/Riemann; FP64 pressure recovery and RK update */
+    MFC_GATED = 2   /* MFC_MIXED plus an MLP gate choosing linear-weight WENO in smooth cells */
+} mfc_precision;
+
+typedef enum { MFC_BC_TRANSMISSIVE = 0, MFC_BC_PERIODIC = 1 } mfc_bc;
+
+/* Problem statement (Sec. II-A/B): a uniform grid, two stiffened gases, BCs. */
+typedef struct {
+    int ndim;          /* 1, 2 or 3 */
+    int n[3];          /* cells per dimension; entries beyond ndim are ignored (treated as 1) */
+    double lo[3];      /* lower corner; dx_d = (hi[d] - lo[d]) / n[d] */
+    double hi[3];      /* upper corner */
+    int bc[3][2];      /* mfc_bc per dimension and side; periodic must be set on both sides */
+    double gamma[2];   /* ratio of specific heats of fluid 1 and fluid 2 (> 1) */
+    double pi_inf[2];  /* stiffness pi_inf of fluid 1 and fluid 2 (>= 0), in pressure units */
+    double weno_eps;   /* WENO5-JS epsilon, absolute (1e-6 is the usual choice) */
+    int precision;     /* mfc_precision */
+} mfc_params;
+
+/* Creates a context: validates params (MFC_EINVAL), allocates the state,
+ * stage and accumulator buffers on the current CUDA device (MFC_ENOMEM) and
+ * binds the CUDA stream `cuda_stream` (a cudaStream_t; NULL = legacy default
+ * stream).  *out receives the context, or NULL on failure. */
+int mfc_create(const mfc_params* params, void* cuda_stream, mfc_ctx** out);
+
+/* Frees every resource of the context after synchronising its stream.
+ * NULL is accepted and ignored. */
+int mfc_destroy(mfc_ctx* ctx);
+
+/* Sets the current state q^n from conservative FP64 values, layout above,
+ * neq * ncells doubles.  Also computes the CFL wave speed of that state. */
+int mfc_set_state(mfc_ctx* ctx, const double* q, int on_device);
+
+/* Same as mfc_set_state, from primitive FP64 values w (alpha1 rho1, alpha2
+ * rho2, u_k, p, alpha1); the conversion to conservative variables uses the
+ * mixture EOS of Sec. II-A and runs on the GPU. */
+int mfc_set_state_prim(mfc_ctx* ctx, const double* w, int on_device);
+
+/* Copies the current state q^n (always FP64, conservative) to q. */
+int mfc_get_state(mfc_ctx* ctx, double* q, int on_device);
+
+/* Evaluates the semi-discrete right-hand side L(q^n) of the cell-integrated
+ * form of Eq. (eqn:discretization) -- flux differences of all directions plus
+ * the alpha1 term alpha1 * div(u) -- and writes it to rhs (FP64, state
+ * layout).  Returns MFC_ENONPHYSICAL if a reconstructed face state was
+ * non-physical; rhs is written either way. */
+int mfc_rhs(mfc_ctx* ctx, double* rhs, int on_device);
+
+/* S = max over cells of sum_d (|u_d| + c)/dx_d for the current state
+ * [1/time units]; the CFL step is dt = cfl / S. */
+int mfc_max_wavespeed(mfc_ctx* ctx, double* s);
+
+/* Advances nsteps SSP-RK3 steps.  Each step uses dt_n = cfl / S(q^n), with S
+ * computed on the GPU at the end of the previous step (no host round trip).
+ * *t_advanced (may be NULL) receives the sum of the dt_n.  Returns
+ * MFC_ENONPHYSICAL after the last step if any state during the run was
+ * non-physical; the state is left as computed. */
+int mfc_step_rk3(mfc_ctx* ctx, double cfl, int nsteps, double* t_advanced);
+
+/* Advances nsteps SSP-RK3 steps of fixed size dt > 0. */
+int mfc_step_rk3_dt(mfc_ctx* ctx, double dt, int nsteps);
+
+/* Number of kernel launches one call of mfc_step_rk3 with nsteps = 1 makes
+ * (a step is replayed from a captured CUDA graph of these launches). */
+int mfc_launches_per_step(mfc_ctx* ctx, int* launches);
+
+/* Per-kernel timing.  While enabled, mfc_step_rk3/mfc_step_rk3_dt launch
+ * kernels directly (no graph) and bracket each launch with CUDA events on the
+ * context's stream; the accumulated device time per kernel kind can be read
+ * with mfc_kernel_time.  Enabling or disabling resets the accumulators. */
+int mfc_set_timing(mfc_ctx* ctx, int enable);
+
+/* Kernel kind `index` (0-based): its name, the summed device time in ms and
+ * the number of launches since timing was enabled.  Returns MFC_EINVAL when
+ * index is out of range. */
+int mfc_kernel_time(mfc_ctx* ctx, int index, const char** name, double* ms, long long* launches);
+
+/* Instrumentation, no counterpart in the paper: measures the sustained FMA
+ * throughput of the current device with independent FMA chains, FP64
+ * (fp64 != 0) or FP32, in TFLOP/s (2 flops per FMA).  Used as the ALU
+ * roofline denominator.  Allocates and frees 16 bytes of device memory and
+ * synchronises the legacy default stream. */
+int mfc_alu_peak(int fp64, double* tflops);
+
+/* Message for a status code (static storage). */
+const char* mfc_strerror(int status);
+
+/* The last CUDA error code the library saw in this context (0 if none). */
+int mfc_last_cuda_error(mfc_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MFC5_H */

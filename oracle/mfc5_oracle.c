@@ -273,10 +273,13 @@ static long bc_map(long j, long n, int periodic) {
     return j;
 }
 
-static void load_prim(const grid* g, const double* q, long cell, double* w) {
+/* Primitives of one cell; returns 1 when the cell's mixture density is not
+ * positive (or NaN). */
+static int load_prim(const grid* g, const double* q, long cell, double* w) {
     double qc[7];
     for (int f = 0; f < g->neq; f++) qc[f] = q[(long)f * g->ncell + cell];
     cons_to_prim(g, qc, w);
+    return !(qc[0] + qc[1] > 0.0);
 }
 
 /* Contribution of direction d at one cell, from the primitive pencil W
@@ -304,7 +307,9 @@ static int cell_dir(const grid* g, int d, const double* W7, double* L) {
     return bad;
 }
 
-/* Full RHS for direction d over all pencils, computing each face once. */
+/* Full RHS for direction d over all pencils, computing each face once.
+ * Returns 1 when a cell (rho <= 0) or a face state (rho <= 0, c^2 <= 0) of
+ * the stencils was non-physical. */
 static int rhs_dir(const grid* g, int d, const double* q, double* rhs, int first,
                    double* W, double* VM, double* VP, double* FF, double* UF) {
     int neq = g->neq;
@@ -317,7 +322,7 @@ static int rhs_dir(const grid* g, int d, const double* q, double* rhs, int first
             /* primitives of cells -3 .. nd+2 (slot = j + 3) */
             for (long j = -3; j < nd + 3; j++) {
                 long src = bc_map(j, nd, g->periodic[d]);
-                load_prim(g, q, base + src * g->stride[d], &W[(j + 3) * neq]);
+                bad |= load_prim(g, q, base + src * g->stride[d], &W[(j + 3) * neq]);
             }
             /* WENO at cells -1 .. nd (slot = j + 1) */
             for (long j = -1; j < nd + 1; j++) {
@@ -431,7 +436,7 @@ int orc_rhs_points(const orc_params* p, const double* q, const long* cells, long
             long base = cell - idx[d] * g.stride[d];
             for (int s = 0; s < 7; s++) {
                 long src = bc_map(idx[d] + s - 3, g.n[d], g.periodic[d]);
-                load_prim(&g, q, base + src * g.stride[d], &W7[s * neq]);
+                bad |= load_prim(&g, q, base + src * g.stride[d], &W7[s * neq]);
             }
             bad |= cell_dir(&g, d, W7, L);
             for (int f = 0; f < neq; f++) acc[f] = (d == 0) ? L[f] : acc[f] + L[f];
@@ -453,7 +458,7 @@ int orc_max_wavespeed(const orc_params* p, const double* q, double* S_out) {
     int bad = 0;
     double w[7];
     for (long c = 0; c < g.ncell; c++) {
-        load_prim(&g, q, c, w);
+        bad |= load_prim(&g, q, c, w);
         double rho = w[0] + w[1];
         double G, Pi;
         mixture(&g, w[IA(&g)], &G, &Pi);

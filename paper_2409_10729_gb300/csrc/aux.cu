@@ -1,0 +1,196 @@
+// aux.cu -- small kernels around the sweeps: primitive -> conservative
+// conversion, the FP32 working copy of the mixed form, the standalone CFL
+// wave-speed reduction, and the per-step control kernel.
+#include "sweep.cuh"
+
+namespace mfc5 {
+
+constexpr int kAuxThreads = 256;
+
+static unsigned aux_blocks(long long n) {
+    long long b = (n + kAuxThreads - 1) / kAuxThreads;
+    if (b < 1) b = 1;
+    if (b > 152LL * 64) b = 152LL * 64;  // grid-stride beyond this
+    return (unsigned)b;
+}
+
+// Primitive (alpha1 rho1, alpha2 rho2, u_k, p, alpha1) -> conservative, in
+// place (Sec. II-A: rho E = Gamma p + Pi + rho |u|^2 / 2).
+template <int NDIM>
+__global__ void prim_to_cons_kernel(double* q, long long nc, Eos e) {
+    using FL = Fields<NDIM>;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < nc;
+         c += (long long)gridDim.x * blockDim.x) {
+        double rho = q[c] + q[nc + c];
+        double ke2 = 0.0;
+#pragma unroll
+        for (int k = 0; k < NDIM; ++k) {
+            double u = q[(2 + k) * nc + c];
+            ke2 += u * u;
+            q[(2 + k) * nc + c] = rho * u;
+        }
+        double a1 = q[FL::IA * nc + c];
+        double G, Pi;
+        mixture(e, a1, G, Pi);
+        q[FL::IE * nc + c] = G * q[FL::IE * nc + c] + Pi + 0.5 * rho * ke2;
+    }
+}
+
+// FP32 working copy (conservatives + pressure) of an FP64 state, mixed form.
+template <int NDIM>
+__global__ void make_mixed_state_kernel(const double* __restrict__ qn, float* __restrict__ s0,
+                                        long long nc, Eos e) {
+    using FL = Fields<NDIM>;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < nc;
+         c += (long long)gridDim.x * blockDim.x) {
+        double q[FL::NEQ];
+#pragma unroll
+        for (int f = 0; f < FL::NEQ; ++f) {
+            q[f] = qn[f * nc + c];
+            s0[f * nc + c] = float(q[f]);
+        }
+        s0[FL::NEQ * nc + c] = mixed_pressure<NDIM>(e, q);
+    }
+}
+
+// S = max over cells of sum_d (|u_d| + c)/dx_d of an FP64 state.
+template <int NDIM>
+__global__ void wavespeed_kernel(const double* __restrict__ q, long long nc, Eos e, double idx0,
+                                 double idx1, double idx2, DevCtrl* ctrl) {
+    using FL = Fields<NDIM>;
+    const double inv_dx[3] = {idx0, idx1, idx2};
+    double smax = 0.0;
+    bool bad = false;
+    long long stride = (long long)gridDim.x * blockDim.x;
+    long long start = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    // every thread of a warp runs the same number of iterations so that the
+    // warp reduction below sees all 32 lanes
+    long long iters = (nc + stride - 1) / stride;
+    for (long long it = 0; it < iters; ++it) {
+        long long c = start + it * stride;
+        if (c < nc) {
+            double w[FL::NEQ];
+            load_prim<NDIM>(q, c, nc, e, w);
+            double s = cell_wavespeed<NDIM, double>(e, w, inv_dx, bad);
+            smax = s > smax ? s : smax;
+        }
+    }
+    double m = warp_max(smax);
+    if ((threadIdx.x & 31) == 0 && m > 0.0)
+        atomicMax(&ctrl->S_bits, (unsigned long long)__double_as_longlong(m));
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(&ctrl->status, 1u);
+}
+
+// Start of a step: take S of the current state, set dt, advance t, and clear
+// the accumulator that the step's last sweep fills with S of the new state.
+__global__ void step_begin_kernel(DevCtrl* ctrl) {
+    double S = __longlong_as_double((long long)ctrl->S_bits);
+    double dt = ctrl->dt_fixed > 0.0 ? ctrl->dt_fixed : ctrl->cfl / S;
+    if (!(dt > 0.0) || !(dt < INFINITY)) ctrl->status |= 2u;
+    ctrl->S = S;
+    ctrl->dt = dt;
+    ctrl->t += dt;
+    ctrl->S_bits = 0ULL;
+}
+
+__global__ void f32_to_f64_kernel(const float* __restrict__ src, double* __restrict__ dst, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        dst[i] = double(src[i]);
+}
+
+cudaError_t launch_prim_to_cons(int ndim, double* q, long long nc, const Eos& e, cudaStream_t s) {
+    unsigned g = aux_blocks(nc);
+    if (ndim == 1) prim_to_cons_kernel<1><<<g, kAuxThreads, 0, s>>>(q, nc, e);
+    else if (ndim == 2) prim_to_cons_kernel<2><<<g, kAuxThreads, 0, s>>>(q, nc, e);
+    else prim_to_cons_kernel<3><<<g, kAuxThreads, 0, s>>>(q, nc, e);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_make_mixed_state(int ndim, const double* qn, float* s0, long long nc, const Eos& e,
+                                    cudaStream_t s) {
+    unsigned g = aux_blocks(nc);
+    if (ndim == 1) make_mixed_state_kernel<1><<<g, kAuxThreads, 0, s>>>(qn, s0, nc, e);
+    else if (ndim == 2) make_mixed_state_kernel<2><<<g, kAuxThreads, 0, s>>>(qn, s0, nc, e);
+    else make_mixed_state_kernel<3><<<g, kAuxThreads, 0, s>>>(qn, s0, nc, e);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wavespeed(int ndim, const double* q, long long nc, const int* n, const double* inv_dx,
+                             const Eos& e, DevCtrl* ctrl, cudaStream_t s) {
+    (void)n;
+    cudaError_t err = cudaMemsetAsync(&ctrl->S_bits, 0, sizeof(unsigned long long), s);
+    if (err != cudaSuccess) return err;
+    unsigned g = aux_blocks(nc);
+    if (ndim == 1) wavespeed_kernel<1><<<g, kAuxThreads, 0, s>>>(q, nc, e, inv_dx[0], inv_dx[1], inv_dx[2], ctrl);
+    else if (ndim == 2) wavespeed_kernel<2><<<g, kAuxThreads, 0, s>>>(q, nc, e, inv_dx[0], inv_dx[1], inv_dx[2], ctrl);
+    else wavespeed_kernel<3><<<g, kAuxThreads, 0, s>>>(q, nc, e, inv_dx[0], inv_dx[1], inv_dx[2], ctrl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step_begin(DevCtrl* ctrl, cudaStream_t s) {
+    step_begin_kernel<<<1, 1, 0, s>>>(ctrl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_f32_to_f64(const float* src, double* dst, long long n, cudaStream_t s) {
+    f32_to_f64_kernel<<<aux_blocks(n), kAuxThreads, 0, s>>>(src, dst, n);
+    return cudaGetLastError();
+}
+
+}  // namespace mfc5
+
+namespace mfc5 {
+
+// ---------------------------------------------------------------------------
+// ALU peak probe: independent FMA chains (8 per thread) over a grid of 152 x 8
+// blocks; the result is stored so the chains are not removed.  Used only to
+// measure the FP64/FP32 roofline denominators.
+template <typename R>
+__global__ void fma_probe_kernel(R* sink, int iters, R a, R b) {
+    R x[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = R(threadIdx.x + k) * R(1e-3);
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) x[k] = fma(x[k], a, b);
+    }
+    R s = R(0);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += x[k];
+    if (s == R(12345.678)) sink[0] = s;  // practically never taken; keeps the chains live
+}
+
+cudaError_t run_fma_probe(int fp64, double* tflops, cudaStream_t s) {
+    const int blocks = 152 * 8, threads = 256;
+    const int iters = fp64 ? 256 : 8192;
+    void* sink = nullptr;
+    cudaError_t e = cudaMalloc(&sink, 16);
+    if (e != cudaSuccess) return e;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    for (int rep = 0; rep < 4; ++rep) {
+        cudaEventRecord(e0, s);
+        if (fp64)
+            fma_probe_kernel<double><<<blocks, threads, 0, s>>>((double*)sink, iters, 0.999999, 1e-7);
+        else
+            fma_probe_kernel<float><<<blocks, threads, 0, s>>>((float*)sink, iters, 0.9999f, 1e-5f);
+        cudaEventRecord(e1, s);
+        e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0 && ms < best) best = ms;  // first launch is warm-up
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(sink);
+    if (e != cudaSuccess) return e;
+    double flops = 2.0 * 8.0 * iters * (double)blocks * threads;
+    *tflops = flops / (best * 1e-3) / 1e12;
+    return cudaGetLastError();
+}
+
+}  // namespace mfc5

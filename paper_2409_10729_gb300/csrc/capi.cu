@@ -1,0 +1,445 @@
+// capi.cu -- host implementation of the C ABI declared in include/mfc.h.
+//
+// A context owns the device buffers of one problem and a stream.  A step of
+// SSP-RK3 is: one step_begin kernel (dt from the device-resident wave speed),
+// then for each of the three stages one fused sweep per direction; the last
+// sweep of a stage applies the stage update, and the last sweep of stage 3
+// reduces the wave speed of the new state.  The launches of one step are
+// captured once into a CUDA graph and replayed.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stddef.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "mfc.h"
+#include "mfc_internal.cuh"
+
+using namespace mfc5;
+
+namespace {
+
+enum KernelKind { K_STEP_BEGIN = 0, K_SWEEP_X, K_SWEEP_Y, K_SWEEP_Z, K_NKINDS };
+const char* kKindNames[K_NKINDS] = {"step_begin", "sweep_x", "sweep_y", "sweep_z"};
+constexpr int kMaxTimedLaunches = 16;
+
+}  // namespace
+
+struct mfc_ctx {
+    mfc_params p;
+    int ndim, neq, form;
+    int n[3];
+    long long ncell;
+    double inv_dx[3];
+    int periodic[3];
+    int seg[3];
+    Eos eos;
+    int device;
+    cudaStream_t stream;
+    cudaStream_t cap_stream;
+    double* qn;       // q^n, FP64 conservative
+    void* sa;         // stage 1 output (FP64, or FP32 cons + p)
+    void* sb;         // stage 2 output
+    float* s0;        // mixed form: FP32 copy of q^n with p
+    void* acc;        // RHS accumulator
+    double* tmp64;    // mixed form: FP64 RHS output staging (lazy)
+    DevCtrl* ctrl;    // device
+    DevCtrl* ctrl_h;  // pinned host mirror
+    bool have_state;
+    cudaGraphExec_t gexec;
+    bool graph_ok;
+    bool timing;
+    cudaEvent_t ev[kMaxTimedLaunches + 1];
+    double ktime[K_NKINDS];
+    long long kcount[K_NKINDS];
+    int last_cuda;
+};
+
+#define CK(call)                                   \
+    do {                                           \
+        cudaError_t e_ = (call);                   \
+        if (e_ != cudaSuccess) {                   \
+            ctx->last_cuda = (int)e_;              \
+            return MFC_ECUDA;                      \
+        }                                          \
+    } while (0)
+
+static int validate(const mfc_params* p) {
+    if (!p || p->ndim < 1 || p->ndim > 3) return MFC_EINVAL;
+    for (int d = 0; d < p->ndim; ++d) {
+        if (p->n[d] < 1) return MFC_EINVAL;
+        if (!(p->hi[d] > p->lo[d]) || !isfinite(p->hi[d] - p->lo[d])) return MFC_EINVAL;
+        int b0 = p->bc[d][0], b1 = p->bc[d][1];
+        if (b0 < 0 || b0 > 1 || b1 < 0 || b1 > 1 || b0 != b1) return MFC_EINVAL;
+    }
+    for (int i = 0; i < 2; ++i)
+        if (!(p->gamma[i] > 1.0) || !isfinite(p->gamma[i]) || !(p->pi_inf[i] >= 0.0) || !isfinite(p->pi_inf[i]))
+            return MFC_EINVAL;
+    if (!(p->weno_eps > 0.0) || !isfinite(p->weno_eps)) return MFC_EINVAL;
+    if (p->precision != MFC_FP64 && p->precision != MFC_MIXED) return MFC_EINVAL;
+    return MFC_OK;
+}
+
+static int pick_seg(int dir, const int* n) {
+    // longest segment (fewest duplicated halo cells) that still gives every
+    // SM a few warps
+    const long long want_threads = 152LL * 256;
+    int seg = 32;
+    while (seg > 4 && sweep_warps(dir, n, seg) * 32 < want_threads) seg >>= 1;
+    return seg;
+}
+
+static size_t state_elem(const mfc_ctx* c) { return c->form == FORM_FP64 ? sizeof(double) : sizeof(float); }
+static int state_fields(const mfc_ctx* c) { return c->form == FORM_FP64 ? c->neq : c->neq + 1; }
+
+static void free_all(mfc_ctx* c) {
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    void* bufs[] = {c->qn, c->sa, c->sb, c->s0, c->acc, c->tmp64, c->ctrl};
+    for (void* b : bufs)
+        if (b) cudaFree(b);
+    if (c->ctrl_h) cudaFreeHost(c->ctrl_h);
+    for (int i = 0; i <= kMaxTimedLaunches; ++i)
+        if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+}
+
+extern "C" int mfc_create(const mfc_params* params, void* cuda_stream, mfc_ctx** out) {
+    if (!out) return MFC_EINVAL;
+    *out = NULL;
+    int st = validate(params);
+    if (st) return st;
+    mfc_ctx* ctx = (mfc_ctx*)calloc(1, sizeof(mfc_ctx));
+    if (!ctx) return MFC_ENOMEM;
+    ctx->p = *params;
+    ctx->ndim = params->ndim;
+    ctx->neq = params->ndim + 4;
+    ctx->form = params->precision == MFC_FP64 ? FORM_FP64 : FORM_MIXED;
+    ctx->ncell = 1;
+    for (int d = 0; d < 3; ++d) {
+        ctx->n[d] = d < ctx->ndim ? params->n[d] : 1;
+        ctx->ncell *= ctx->n[d];
+        ctx->inv_dx[d] = d < ctx->ndim ? (double)ctx->n[d] / (params->hi[d] - params->lo[d]) : 0.0;
+        ctx->periodic[d] = d < ctx->ndim ? params->bc[d][0] == MFC_BC_PERIODIC : 0;
+    }
+    for (int d = 0; d < ctx->ndim; ++d) ctx->seg[d] = pick_seg(d, ctx->n);
+    double g1 = 1.0 / (params->gamma[0] - 1.0), g2 = 1.0 / (params->gamma[1] - 1.0);
+    double P1 = params->gamma[0] * params->pi_inf[0] / (params->gamma[0] - 1.0);
+    double P2 = params->gamma[1] * params->pi_inf[1] / (params->gamma[1] - 1.0);
+    ctx->eos = Eos{g1, g2, P1, P2, g1 - g2, P1 - P2};
+    ctx->stream = (cudaStream_t)cuda_stream;
+
+    cudaError_t e;
+    if ((e = cudaGetDevice(&ctx->device)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking)) != cudaSuccess) {
+        free_all(ctx);
+        free(ctx);
+        return MFC_ECUDA;
+    }
+    size_t nc = (size_t)ctx->ncell;
+    size_t sfield = state_fields(ctx), selem = state_elem(ctx);
+    bool ok = cudaMalloc((void**)&ctx->qn, nc * ctx->neq * sizeof(double)) == cudaSuccess &&
+              cudaMalloc(&ctx->sa, nc * sfield * selem) == cudaSuccess &&
+              cudaMalloc(&ctx->sb, nc * sfield * selem) == cudaSuccess &&
+              cudaMalloc(&ctx->acc, nc * ctx->neq * selem) == cudaSuccess &&
+              cudaMalloc((void**)&ctx->ctrl, sizeof(DevCtrl)) == cudaSuccess &&
+              cudaMallocHost((void**)&ctx->ctrl_h, sizeof(DevCtrl)) == cudaSuccess;
+    if (ok && ctx->form == FORM_MIXED)
+        ok = cudaMalloc((void**)&ctx->s0, nc * sfield * sizeof(float)) == cudaSuccess;
+    for (int i = 0; ok && i <= kMaxTimedLaunches; ++i) ok = cudaEventCreate(&ctx->ev[i]) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        free_all(ctx);
+        free(ctx);
+        return MFC_ENOMEM;
+    }
+    memset(ctx->ctrl_h, 0, sizeof(DevCtrl));
+    if (cudaMemcpyAsync(ctx->ctrl, ctx->ctrl_h, sizeof(DevCtrl), cudaMemcpyHostToDevice, ctx->stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+        free_all(ctx);
+        free(ctx);
+        return MFC_ECUDA;
+    }
+    *out = ctx;
+    return MFC_OK;
+}
+
+extern "C" int mfc_destroy(mfc_ctx* ctx) {
+    if (!ctx) return MFC_OK;
+    cudaStreamSynchronize(ctx->stream);
+    free_all(ctx);
+    free(ctx);
+    return MFC_OK;
+}
+
+static SweepArgs base_args(mfc_ctx* ctx) {
+    SweepArgs a;
+    memset(&a, 0, sizeof(a));
+    for (int d = 0; d < 3; ++d) {
+        a.n[d] = ctx->n[d];
+        a.inv_dx[d] = ctx->inv_dx[d];
+    }
+    a.ncell = ctx->ncell;
+    a.eos = ctx->eos;
+    a.eps = ctx->p.weno_eps;
+    a.ctrl = ctx->ctrl;
+    a.acc = ctx->acc;
+    a.qn = ctx->qn;
+    return a;
+}
+
+static cudaError_t launch_sweep(mfc_ctx* ctx, int dir, int mode, SweepArgs a, cudaStream_t s) {
+    a.periodic = ctx->periodic[dir];
+    a.seg = ctx->seg[dir];
+    return ctx->form == FORM_FP64 ? launch_sweep_fp64(ctx->ndim, dir, mode, a, s)
+                                  : launch_sweep_mixed(ctx->ndim, dir, mode, a, s);
+}
+
+// The stage input/output buffers of stage k (1..3).
+static void stage_buffers(mfc_ctx* ctx, int k, SweepArgs& a) {
+    const void* in0 = ctx->form == FORM_FP64 ? (const void*)ctx->qn : (const void*)ctx->s0;
+    a.stage = k;
+    a.qin = k == 1 ? in0 : (k == 2 ? ctx->sa : ctx->sb);
+    a.qout = k == 1 ? ctx->sa : (k == 2 ? ctx->sb : (void*)ctx->qn);
+    a.qout2 = (k == 3 && ctx->form == FORM_MIXED) ? (void*)ctx->s0 : NULL;
+}
+
+// Enqueue the launches of one step on stream s; with `timed`, bracket each
+// launch with events ev[i], ev[i+1] (recorded for later accumulation).
+static cudaError_t enqueue_step(mfc_ctx* ctx, cudaStream_t s, bool timed, int* kinds, int* nl) {
+    int L = 0;
+    cudaError_t e;
+    if (timed && (e = cudaEventRecord(ctx->ev[0], s)) != cudaSuccess) return e;
+    if ((e = launch_step_begin(ctx->ctrl, s)) != cudaSuccess) return e;
+    if (timed) {
+        kinds[L++] = K_STEP_BEGIN;
+        if ((e = cudaEventRecord(ctx->ev[L], s)) != cudaSuccess) return e;
+    }
+    for (int k = 1; k <= 3; ++k) {
+        SweepArgs a = base_args(ctx);
+        stage_buffers(ctx, k, a);
+        for (int d = 0; d < ctx->ndim; ++d) {
+            int mode = d == ctx->ndim - 1 ? SW_LAST_RK : (d == 0 ? SW_FIRST : SW_MID);
+            if ((e = launch_sweep(ctx, d, mode, a, s)) != cudaSuccess) return e;
+            if (timed) {
+                kinds[L++] = K_SWEEP_X + d;
+                if ((e = cudaEventRecord(ctx->ev[L], s)) != cudaSuccess) return e;
+            }
+        }
+    }
+    if (nl) *nl = L;
+    return cudaSuccess;
+}
+
+static int ensure_graph(mfc_ctx* ctx) {
+    if (ctx->graph_ok) return MFC_OK;
+    cudaGraph_t g = NULL;
+    CK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = enqueue_step(ctx, ctx->cap_stream, false, NULL, NULL);
+    cudaError_t e2 = cudaStreamEndCapture(ctx->cap_stream, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        ctx->last_cuda = (int)(e != cudaSuccess ? e : e2);
+        cudaGetLastError();
+        return MFC_ECUDA;
+    }
+    e = cudaGraphInstantiate(&ctx->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        ctx->last_cuda = (int)e;
+        return MFC_ECUDA;
+    }
+    ctx->graph_ok = true;
+    return MFC_OK;
+}
+
+static int after_state_change(mfc_ctx* ctx) {
+    if (ctx->form == FORM_MIXED)
+        CK(launch_make_mixed_state(ctx->ndim, ctx->qn, ctx->s0, ctx->ncell, ctx->eos, ctx->stream));
+    CK(launch_wavespeed(ctx->ndim, ctx->qn, ctx->ncell, ctx->n, ctx->inv_dx, ctx->eos, ctx->ctrl, ctx->stream));
+    ctx->have_state = true;
+    return MFC_OK;
+}
+
+static cudaMemcpyKind kind_in(int on_device) { return on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice; }
+static cudaMemcpyKind kind_out(int on_device) { return on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost; }
+
+extern "C" int mfc_set_state(mfc_ctx* ctx, const double* q, int on_device) {
+    if (!ctx || !q) return MFC_EINVAL;
+    size_t bytes = (size_t)ctx->ncell * ctx->neq * sizeof(double);
+    CK(cudaMemcpyAsync(ctx->qn, q, bytes, kind_in(on_device), ctx->stream));
+    int st = after_state_change(ctx);
+    if (st) return st;
+    if (!on_device) CK(cudaStreamSynchronize(ctx->stream));
+    return MFC_OK;
+}
+
+extern "C" int mfc_set_state_prim(mfc_ctx* ctx, const double* w, int on_device) {
+    if (!ctx || !w) return MFC_EINVAL;
+    size_t bytes = (size_t)ctx->ncell * ctx->neq * sizeof(double);
+    CK(cudaMemcpyAsync(ctx->qn, w, bytes, kind_in(on_device), ctx->stream));
+    CK(launch_prim_to_cons(ctx->ndim, ctx->qn, ctx->ncell, ctx->eos, ctx->stream));
+    int st = after_state_change(ctx);
+    if (st) return st;
+    if (!on_device) CK(cudaStreamSynchronize(ctx->stream));
+    return MFC_OK;
+}
+
+extern "C" int mfc_get_state(mfc_ctx* ctx, double* q, int on_device) {
+    if (!ctx || !q) return MFC_EINVAL;
+    if (!ctx->have_state) return MFC_ESTATE;
+    size_t bytes = (size_t)ctx->ncell * ctx->neq * sizeof(double);
+    CK(cudaMemcpyAsync(q, ctx->qn, bytes, kind_out(on_device), ctx->stream));
+    if (!on_device) CK(cudaStreamSynchronize(ctx->stream));
+    return MFC_OK;
+}
+
+static int read_ctrl(mfc_ctx* ctx) {
+    CK(cudaMemcpyAsync(ctx->ctrl_h, ctx->ctrl, sizeof(DevCtrl), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return MFC_OK;
+}
+
+// Host-set part of the control block: t, cfl, dt_fixed, status.
+static int write_ctrl_params(mfc_ctx* ctx, double cfl, double dt_fixed) {
+    ctx->ctrl_h->t = 0.0;
+    ctx->ctrl_h->cfl = cfl;
+    ctx->ctrl_h->dt_fixed = dt_fixed;
+    ctx->ctrl_h->status = 0;
+    size_t off = offsetof(DevCtrl, t);
+    CK(cudaMemcpyAsync((char*)ctx->ctrl + off, (char*)ctx->ctrl_h + off, sizeof(DevCtrl) - off,
+                       cudaMemcpyHostToDevice, ctx->stream));
+    return MFC_OK;
+}
+
+extern "C" int mfc_rhs(mfc_ctx* ctx, double* rhs, int on_device) {
+    if (!ctx || !rhs) return MFC_EINVAL;
+    if (!ctx->have_state) return MFC_ESTATE;
+    int st = write_ctrl_params(ctx, 0.0, 0.0);
+    if (st) return st;
+    double* out = on_device ? rhs : NULL;
+    if (!out) {
+        if (ctx->form == FORM_FP64) {
+            out = (double*)ctx->acc;  // the last sweep reads and writes each cell in place
+        } else {
+            if (!ctx->tmp64 && cudaMalloc((void**)&ctx->tmp64, (size_t)ctx->ncell * ctx->neq * sizeof(double)) !=
+                                   cudaSuccess) {
+                cudaGetLastError();
+                return MFC_ENOMEM;
+            }
+            out = ctx->tmp64;
+        }
+    }
+    SweepArgs a = base_args(ctx);
+    a.qin = ctx->form == FORM_FP64 ? (const void*)ctx->qn : (const void*)ctx->s0;
+    a.qout = out;
+    a.stage = 0;
+    for (int d = 0; d < ctx->ndim; ++d) {
+        int mode = d == ctx->ndim - 1 ? SW_LAST_RHS : (d == 0 ? SW_FIRST : SW_MID);
+        CK(launch_sweep(ctx, d, mode, a, ctx->stream));
+    }
+    if (!on_device)
+        CK(cudaMemcpyAsync(rhs, out, (size_t)ctx->ncell * ctx->neq * sizeof(double), cudaMemcpyDeviceToHost,
+                           ctx->stream));
+    st = read_ctrl(ctx);
+    if (st) return st;
+    return ctx->ctrl_h->status ? MFC_ENONPHYSICAL : MFC_OK;
+}
+
+extern "C" int mfc_max_wavespeed(mfc_ctx* ctx, double* s) {
+    if (!ctx || !s) return MFC_EINVAL;
+    if (!ctx->have_state) return MFC_ESTATE;
+    int st = write_ctrl_params(ctx, 0.0, 0.0);
+    if (st) return st;
+    CK(launch_wavespeed(ctx->ndim, ctx->qn, ctx->ncell, ctx->n, ctx->inv_dx, ctx->eos, ctx->ctrl, ctx->stream));
+    st = read_ctrl(ctx);
+    if (st) return st;
+    unsigned long long bits = ctx->ctrl_h->S_bits;
+    memcpy(s, &bits, sizeof(double));
+    return ctx->ctrl_h->status ? MFC_ENONPHYSICAL : MFC_OK;
+}
+
+static int run_steps(mfc_ctx* ctx, double cfl, double dt_fixed, int nsteps, double* t_out) {
+    if (!ctx->have_state) return MFC_ESTATE;
+    int st = write_ctrl_params(ctx, cfl, dt_fixed);
+    if (st) return st;
+    if (ctx->timing) {
+        for (int n = 0; n < nsteps; ++n) {
+            int kinds[kMaxTimedLaunches], nl = 0;
+            CK(enqueue_step(ctx, ctx->stream, true, kinds, &nl));
+            CK(cudaEventSynchronize(ctx->ev[nl]));
+            for (int i = 0; i < nl; ++i) {
+                float ms = 0.0f;
+                CK(cudaEventElapsedTime(&ms, ctx->ev[i], ctx->ev[i + 1]));
+                ctx->ktime[kinds[i]] += ms;
+                ctx->kcount[kinds[i]] += 1;
+            }
+        }
+    } else {
+        st = ensure_graph(ctx);
+        if (st) return st;
+        for (int n = 0; n < nsteps; ++n) CK(cudaGraphLaunch(ctx->gexec, ctx->stream));
+    }
+    st = read_ctrl(ctx);
+    if (st) return st;
+    if (t_out) *t_out = ctx->ctrl_h->t;
+    return ctx->ctrl_h->status ? MFC_ENONPHYSICAL : MFC_OK;
+}
+
+extern "C" int mfc_step_rk3(mfc_ctx* ctx, double cfl, int nsteps, double* t_advanced) {
+    if (!ctx || nsteps < 0 || !(cfl > 0.0) || !isfinite(cfl)) return MFC_EINVAL;
+    return run_steps(ctx, cfl, 0.0, nsteps, t_advanced);
+}
+
+extern "C" int mfc_step_rk3_dt(mfc_ctx* ctx, double dt, int nsteps) {
+    if (!ctx || nsteps < 0 || !(dt > 0.0) || !isfinite(dt)) return MFC_EINVAL;
+    return run_steps(ctx, 0.0, dt, nsteps, NULL);
+}
+
+extern "C" int mfc_launches_per_step(mfc_ctx* ctx, int* launches) {
+    if (!ctx || !launches) return MFC_EINVAL;
+    *launches = 1 + 3 * ctx->ndim;
+    return MFC_OK;
+}
+
+extern "C" int mfc_set_timing(mfc_ctx* ctx, int enable) {
+    if (!ctx) return MFC_EINVAL;
+    ctx->timing = enable != 0;
+    for (int k = 0; k < K_NKINDS; ++k) {
+        ctx->ktime[k] = 0.0;
+        ctx->kcount[k] = 0;
+    }
+    return MFC_OK;
+}
+
+extern "C" int mfc_kernel_time(mfc_ctx* ctx, int index, const char** name, double* ms, long long* launches) {
+    if (!ctx || index < 0 || index >= K_NKINDS) return MFC_EINVAL;
+    if (name) *name = kKindNames[index];
+    if (ms) *ms = ctx->ktime[index];
+    if (launches) *launches = ctx->kcount[index];
+    return MFC_OK;
+}
+
+extern "C" int mfc_alu_peak(int fp64, double* tflops) {
+    if (!tflops) return MFC_EINVAL;
+    cudaError_t e = run_fma_probe(fp64 != 0, tflops, (cudaStream_t)0);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return MFC_ECUDA;
+    }
+    return MFC_OK;
+}
+
+extern "C" const char* mfc_strerror(int status) {
+    switch (status) {
+        case MFC_OK: return "ok";
+        case MFC_EINVAL: return "invalid argument";
+        case MFC_ENOMEM: return "out of memory";
+        case MFC_ECUDA: return "CUDA runtime error";
+        case MFC_ENONPHYSICAL: return "non-physical state (rho<=0, c^2<=0 or NaN)";
+        case MFC_ESTATE: return "no state set";
+        default: return "unknown status";
+    }
+}
+
+extern "C" int mfc_last_cuda_error(mfc_ctx* ctx) { return ctx ? ctx->last_cuda : 0; }

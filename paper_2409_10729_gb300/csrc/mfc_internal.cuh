@@ -1,0 +1,76 @@
+// mfc_internal.cuh -- shared declarations of the CUDA library (not installed).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "physics.cuh"
+
+namespace mfc5 {
+
+// Step control block, resident in device memory so that consecutive steps
+// need no host round trip (dt of step n+1 comes from S(q^{n+1}), reduced by
+// the last sweep of step n).
+struct DevCtrl {
+    unsigned long long S_bits;  // max of the per-cell wave speed, as the bits of a positive double
+    double S;                   // wave speed the current step's dt was taken from
+    double dt;                  // current step size
+    double t;                   // time accumulated since the last reset
+    double cfl;                 // CFL number (CFL mode)
+    double dt_fixed;            // > 0 selects fixed-dt mode
+    unsigned int status;        // bit 0: non-physical face state; bit 1: bad wave speed or dt
+    unsigned int pad;
+};
+
+enum SweepMode {
+    SW_FIRST = 0,     // acc  = L_d
+    SW_MID = 1,       // acc += L_d
+    SW_LAST_RK = 2,   // L = acc + L_d; RK stage update; stage 3 also reduces S
+    SW_LAST_RHS = 3   // out = acc + L_d (FP64 output)
+};
+
+struct SweepArgs {
+    const void* qin;      // state whose stencils are read (FP64 cons, or FP32 cons+p)
+    void* acc;            // RHS accumulator (FP64 or FP32)
+    const double* qn;     // RK base state q^n (FP64)
+    void* qout;           // stage output (FP64 or FP32), or FP64 RHS output
+    void* qout2;          // mixed form, stage 3: FP32 copy of q^{n+1} with p
+    int n[3];
+    long long ncell;
+    double inv_dx[3];
+    Eos eos;
+    double eps;
+    int periodic;         // along the sweep direction
+    int seg;              // cells per thread along the sweep direction
+    int stage;            // 1, 2, 3
+    DevCtrl* ctrl;
+};
+
+// Form selectors
+enum Form { FORM_FP64 = 0, FORM_MIXED = 1 };
+
+cudaError_t launch_sweep_fp64(int ndim, int dir, int mode, const SweepArgs& a, cudaStream_t s);
+cudaError_t launch_sweep_mixed(int ndim, int dir, int mode, const SweepArgs& a, cudaStream_t s);
+
+// auxiliary kernels (aux.cu)
+cudaError_t launch_prim_to_cons(int ndim, double* q, long long ncell, const Eos& e, cudaStream_t s);
+cudaError_t launch_make_mixed_state(int ndim, const double* qn, float* s0, long long ncell,
+                                    const Eos& e, cudaStream_t s);
+cudaError_t launch_wavespeed(int ndim, const double* q, long long ncell, const int* n,
+                             const double* inv_dx, const Eos& e, DevCtrl* ctrl, cudaStream_t s);
+cudaError_t launch_step_begin(DevCtrl* ctrl, cudaStream_t s);
+cudaError_t launch_f32_to_f64(const float* src, double* dst, long long count, cudaStream_t s);
+cudaError_t run_fma_probe(int fp64, double* tflops, cudaStream_t s);
+
+// thread-block size of every sweep launch
+constexpr int kSweepThreads = 128;
+
+__host__ __device__ inline long long sweep_warps(int dir, const int* n, int seg) {
+    int na = dir == 0 ? n[1] : n[0];
+    int nb = dir == 2 ? n[1] : n[2];
+    int ns = n[dir];
+    long long nchunk = (na + 31) / 32;
+    long long nseg = (ns + seg - 1) / seg;
+    return nchunk * nseg * nb;
+}
+
+}  // namespace mfc5

@@ -1,0 +1,162 @@
+// physics.cuh -- device-side arithmetic of the five-equation RHS.
+//
+// Stiffened-gas mixture EOS (arXiv 2409.10729, Sec. II-A), WENO5-JS face
+// reconstruction and the HLLC flux (Sec. II-B, last paragraph), written for
+// the GB300 FP64 and FP32 pipes.  The formulas are the same as the serial
+// oracle's, reorganised to spend fewer divisions, which are the expensive
+// operations on this part:
+//   * WENO weights in product form: omega_k ~ d_k * prod_{j != k} (eps+beta_j)^2,
+//     so each face value costs one division instead of six (FP64), or
+//     min-normalised reciprocals that cannot overflow (FP32);
+//   * candidate stencils multiplied by 1/6 instead of divided by 6;
+//   * the HLLC star energy uses one reciprocal 1/(S_K - S*) for both chi_K
+//     and the p_K/(S_K - u_K) term.
+// Results agree with the oracle to rounding, not bit for bit.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mfc5 {
+
+// Stiffened-gas mixture constants: Gamma = g2 + alpha1 (g1 - g2),
+// Pi = P2 + alpha1 (P1 - P2), with g_i = 1/(gamma_i - 1) and
+// P_i = gamma_i pi_i / (gamma_i - 1).
+struct Eos {
+    double g1, g2, P1, P2;
+    double dg, dP;
+};
+
+template <int NDIM>
+struct Fields {
+    static constexpr int NEQ = NDIM + 4;  // alpha1 rho1, alpha2 rho2, rho u_k, rho E, alpha1
+    static constexpr int IE = 2 + NDIM;
+    static constexpr int IA = 3 + NDIM;
+};
+
+template <typename R>
+__device__ __forceinline__ R rdiv(R a, R b) { return a / b; }
+
+template <typename R>
+__device__ __forceinline__ R sqrt_pos(R x) { return sqrt(x); }
+
+// Mixture Gamma and Pi at volume fraction a1.
+template <typename R>
+__device__ __forceinline__ void mixture(const Eos& e, R a1, R& G, R& Pi) {
+    G = a1 * R(e.dg) + R(e.g2);
+    Pi = a1 * R(e.dP) + R(e.P2);
+}
+
+// ---------------------------------------------------------------- WENO5-JS
+// v0..v4 = v_{i-2}..v_{i+2}.  vm: left-biased value at i+1/2 (linear weights
+// 0.1, 0.6, 0.3); vp: right-biased value at i-1/2 (0.3, 0.6, 0.1).  The three
+// Jiang-Shu smoothness indicators of cell i serve both faces.
+template <typename R>
+__device__ __forceinline__ void weno5(R v0, R v1, R v2, R v3, R v4, R eps, R& vm, R& vp) {
+    const R c13 = R(13.0 / 12.0);
+    const R c6 = R(1.0 / 6.0);
+    R d0 = v0 - R(2) * v1 + v2, e0 = v0 - R(4) * v1 + R(3) * v2;
+    R d1 = v1 - R(2) * v2 + v3, e1 = v1 - v3;
+    R d2 = v2 - R(2) * v3 + v4, e2 = R(3) * v2 - R(4) * v3 + v4;
+    R b0 = c13 * d0 * d0 + R(0.25) * e0 * e0;
+    R b1 = c13 * d1 * d1 + R(0.25) * e1 * e1;
+    R b2 = c13 * d2 * d2 + R(0.25) * e2 * e2;
+    R s0 = eps + b0, s1 = eps + b1, s2 = eps + b2;
+    s0 = s0 * s0;
+    s1 = s1 * s1;
+    s2 = s2 * s2;
+    R m0, m1, m2;
+    if constexpr (sizeof(R) == 8) {
+        // product form: weight of stencil k is proportional to d_k * s_j * s_l
+        m0 = s1 * s2;
+        m1 = s0 * s2;
+        m2 = s0 * s1;
+    } else {
+        // FP32: weights relative to the smoothest stencil, all in (0, 1]
+        R smin = fminf(s0, fminf(s1, s2));
+        m0 = __fdividef(smin, s0);
+        m1 = __fdividef(smin, s1);
+        m2 = __fdividef(smin, s2);
+    }
+    R pm0 = (R(2) * v0 - R(7) * v1 + R(11) * v2) * c6;
+    R pm1 = (-v1 + R(5) * v2 + R(2) * v3) * c6;
+    R pm2 = (R(2) * v2 + R(5) * v3 - v4) * c6;
+    R am0 = R(0.1) * m0, am1 = R(0.6) * m1, am2 = R(0.3) * m2;
+    vm = rdiv(am0 * pm0 + am1 * pm1 + am2 * pm2, am0 + am1 + am2);
+    R pp0 = (-v0 + R(5) * v1 + R(2) * v2) * c6;
+    R pp1 = (R(2) * v1 + R(5) * v2 - v3) * c6;
+    R pp2 = (R(11) * v2 - R(7) * v3 + R(2) * v4) * c6;
+    R ap0 = R(0.3) * m0, ap1 = R(0.6) * m1, ap2 = R(0.1) * m2;
+    vp = rdiv(ap0 * pp0 + ap1 * pp1 + ap2 * pp2, ap0 + ap1 + ap2);
+}
+
+// ---------------------------------------------------------------- HLLC
+// Flux through a face normal to DIR from reconstructed primitive states
+// (alpha1 rho1, alpha2 rho2, u_k, p, alpha1).  uf receives the velocity of the
+// selected region (u_K outside the fan, S* inside), which also carries the
+// alpha1 slot: F_alpha = alpha1_K * uf.  Region choice follows
+// 0<=S_L: F_L; S_L<0<=S*: F*_L; S*<0<=S_R: F*_R; else F_R.
+// Returns true when a face state is non-physical (rho<=0, c^2<=0, NaN).
+template <int NDIM, int DIR, typename R>
+__device__ __forceinline__ bool hllc(const Eos& e, const R* wL, const R* wR, R* F, R& uf) {
+    using FL = Fields<NDIM>;
+    const int IE = FL::IE, IA = FL::IA;
+    R rhoL = wL[0] + wL[1];
+    R rhoR = wR[0] + wR[1];
+    R GL, PiL, GR, PiR;
+    mixture(e, wL[IA], GL, PiL);
+    mixture(e, wR[IA], GR, PiR);
+    R pL = wL[IE], pR = wR[IE];
+    R c2L = rdiv((GL + R(1)) * pL + PiL, GL * rhoL);
+    R c2R = rdiv((GR + R(1)) * pR + PiR, GR * rhoR);
+    bool bad = !(rhoL > R(0)) || !(rhoR > R(0)) || !(c2L > R(0)) || !(c2R > R(0));
+    R cL = sqrt_pos(c2L), cR = sqrt_pos(c2R);
+    R uL = wL[2 + DIR], uR = wR[2 + DIR];
+    R SL = (uL - cL < uR - cR) ? uL - cL : uR - cR;
+    R SR = (uL + cL > uR + cR) ? uL + cL : uR + cR;
+    R mL = rhoL * (SL - uL), mR = rhoR * (SR - uR);
+    R Ss = rdiv(pR - pL + uL * mL - uR * mR, mL - mR);
+    const bool left = (R(0) <= SL) || (R(0) <= Ss);
+    const bool star = left ? !(R(0) <= SL) : (R(0) <= SR);
+    // selected side K (element-wise select keeps both states in registers)
+    R w[FL::NEQ];
+#pragma unroll
+    for (int f = 0; f < FL::NEQ; ++f) w[f] = left ? wL[f] : wR[f];
+    R rho = left ? rhoL : rhoR;
+    R G = left ? GL : GR;
+    R Pi = left ? PiL : PiR;
+    R SK = left ? SL : SR;
+    R p = w[IE];
+    R un = w[2 + DIR];
+    R ke = R(0);
+#pragma unroll
+    for (int k = 0; k < NDIM; ++k) ke += w[2 + k] * w[2 + k];
+    ke = R(0.5) * rho * ke;
+    R E = G * p + Pi + ke;
+    F[0] = w[0] * un;
+    F[1] = w[1] * un;
+#pragma unroll
+    for (int k = 0; k < NDIM; ++k) F[2 + k] = rho * w[2 + k] * un;
+    F[2 + DIR] += p;
+    F[IE] = (E + p) * un;
+    uf = un;
+    if (star) {
+        R inv = rdiv(R(1), SK - Ss);
+        R chi = (SK - un) * inv;
+        R dchi = chi - R(1);
+        F[0] += SK * (dchi * w[0]);
+        F[1] += SK * (dchi * w[1]);
+#pragma unroll
+        for (int k = 0; k < NDIM; ++k) {
+            R ms = (k == DIR) ? chi * rho * Ss : chi * rho * w[2 + k];
+            F[2 + k] += SK * (ms - rho * w[2 + k]);
+        }
+        R dS = Ss - un;
+        R Es = chi * (E + dS * rho * Ss) + dS * p * inv;
+        F[IE] += SK * (Es - E);
+        uf = Ss;
+    }
+    F[IA] = w[IA] * uf;
+    return bad;
+}
+
+}  // namespace mfc5

@@ -1,0 +1,330 @@
+// sweep.cuh -- the fused per-direction sweep kernel.
+//
+// One launch handles one direction d of one RHS evaluation (arXiv
+// 2409.10729, Sec. II-B): for every cell it converts conservative to
+// primitive variables (Sec. II-A EOS), reconstructs both face values of every
+// primitive with WENO5-JS, solves HLLC at every face once, and forms
+//   L_d = (F_{i-1/2} - F_{i+1/2}) / dx_d  (+ alpha1_i (u_f,i+1/2 - u_f,i-1/2) / dx_d)
+// which it stores into, adds to, or finishes the RHS accumulator with.  The
+// last direction's sweep also applies the SSP-RK3 stage update and, on the
+// third stage, reduces the CFL wave speed of the new state.
+//
+// Thread mapping.  A warp owns 32 adjacent pencils along d and a segment of
+// `seg` cells of each.  For d = y, z the 32 lanes run along x, so every load
+// is one coalesced row; for d = x the lanes run along y.  Each thread slides a
+// five-cell window of primitives along its pencil in registers: per cell it
+// loads one new cell, runs WENO once (both faces), and HLLC once (the face
+// between the previous cell and this one), so no face is computed twice
+// except at the two ends of a segment.  Boundary ghosts come from index
+// clamping (transmissive) or wrapping (periodic) in the loads.
+#pragma once
+#include "mfc_internal.cuh"
+
+namespace mfc5 {
+
+__device__ __forceinline__ int bc_index(int j, int n, int periodic) {
+    if (j >= 0 && j < n) return j;
+    if (periodic) {
+        int r = j % n;
+        return r < 0 ? r + n : r;
+    }
+    return j < 0 ? 0 : n - 1;
+}
+
+// FP64 form: conservative FP64 state -> FP64 primitives (Sec. II-A EOS).
+template <int NDIM>
+__device__ __forceinline__ void load_prim(const double* __restrict__ q, long long c, long long nc,
+                                          const Eos& e, double* w) {
+    using FL = Fields<NDIM>;
+    double a1r1 = __ldg(q + c);
+    double a2r2 = __ldg(q + nc + c);
+    double r = 1.0 / (a1r1 + a2r2);
+    double ke2 = 0.0;
+    w[0] = a1r1;
+    w[1] = a2r2;
+#pragma unroll
+    for (int k = 0; k < NDIM; ++k) {
+        double m = __ldg(q + (2 + k) * nc + c);
+        double u = m * r;
+        w[2 + k] = u;
+        ke2 += m * u;
+    }
+    double E = __ldg(q + FL::IE * nc + c);
+    double a1 = __ldg(q + FL::IA * nc + c);
+    double G, Pi;
+    mixture(e, a1, G, Pi);
+    w[FL::IE] = (E - 0.5 * ke2 - Pi) / G;
+    w[FL::IA] = a1;
+}
+
+// Mixed form: FP32 state with the pressure stored as field NEQ (computed in
+// FP64 when the state was written) -> FP32 primitives.
+template <int NDIM>
+__device__ __forceinline__ void load_prim(const float* __restrict__ q, long long c, long long nc,
+                                          const Eos& e, float* w) {
+    using FL = Fields<NDIM>;
+    float a1r1 = __ldg(q + c);
+    float a2r2 = __ldg(q + nc + c);
+    float r = __fdividef(1.0f, a1r1 + a2r2);
+    w[0] = a1r1;
+    w[1] = a2r2;
+#pragma unroll
+    for (int k = 0; k < NDIM; ++k) w[2 + k] = __ldg(q + (2 + k) * nc + c) * r;
+    w[FL::IE] = __ldg(q + FL::NEQ * nc + c);
+    w[FL::IA] = __ldg(q + FL::IA * nc + c);
+}
+
+// Pressure from an FP64 conservative state, mixed form: the cancelling part
+// rho E - Pi is formed in FP64, the rest in FP32.
+template <int NDIM>
+__device__ __forceinline__ float mixed_pressure(const Eos& e, const double* q) {
+    using FL = Fields<NDIM>;
+    float rho = float(q[0] + q[1]);
+    float r = __fdividef(1.0f, rho);
+    float ke2 = 0.0f;
+#pragma unroll
+    for (int k = 0; k < NDIM; ++k) {
+        float m = float(q[2 + k]);
+        ke2 += m * (m * r);
+    }
+    double a1 = q[FL::IA];
+    double num = (q[FL::IE] - (a1 * e.dP + e.P2)) - double(0.5f * ke2);
+    float G = float(a1) * float(e.dg) + float(e.g2);
+    return __fdividef(float(num), G);
+}
+
+template <typename R>
+__device__ __forceinline__ R warp_max(R v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        R u = __shfl_xor_sync(0xffffffffu, v, o);
+        v = u > v ? u : v;
+    }
+    return v;
+}
+
+// Per-cell wave speed sum_d (|u_d| + c) / dx_d from primitives.
+template <int NDIM, typename R>
+__device__ __forceinline__ R cell_wavespeed(const Eos& e, const R* w, const double* inv_dx, bool& bad) {
+    using FL = Fields<NDIM>;
+    R rho = w[0] + w[1];
+    R G, Pi;
+    mixture(e, w[FL::IA], G, Pi);
+    R c2 = rdiv((G + R(1)) * w[FL::IE] + Pi, G * rho);
+    bad |= !(rho > R(0)) || !(c2 > R(0));
+    R c = sqrt_pos(c2);
+    R s = R(0);
+#pragma unroll
+    for (int d = 0; d < NDIM; ++d) s += (fabs(w[2 + d]) + c) * R(inv_dx[d]);
+    bad |= !(s < R(INFINITY));
+    return s;
+}
+
+template <int NDIM, int DIR, int MODE, typename R>
+__global__ void __launch_bounds__(kSweepThreads) sweep_kernel(const SweepArgs a) {
+    using FL = Fields<NDIM>;
+    constexpr int NEQ = FL::NEQ, IE = FL::IE, IA = FL::IA;
+    constexpr bool MIXED = sizeof(R) == 4;
+    const int n0 = a.n[0], n1 = a.n[1], n2 = a.n[2];
+    const int na = DIR == 0 ? n1 : n0;
+    const int nb = DIR == 2 ? n1 : n2;
+    const int ns = a.n[DIR];
+    const long long sa = DIR == 0 ? (long long)n0 : 1LL;
+    const long long sb = DIR == 2 ? (long long)n0 : (long long)n0 * n1;
+    const long long ss = DIR == 0 ? 1LL : (DIR == 1 ? (long long)n0 : (long long)n0 * n1);
+    const int seg = a.seg;
+    const long long nchunk = (na + 31) >> 5;
+    const long long nseg = (ns + seg - 1) / seg;
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= nchunk * nseg * nb) return;  // uniform over the warp
+    const int chunk = (int)(warp % nchunk);
+    const long long rest = warp / nchunk;
+    const int segi = (int)(rest % nseg);
+    const int b = (int)(rest / nseg);
+    const int ia = chunk * 32 + lane;
+    const bool active = ia < na;
+    const int s0 = segi * seg;
+    const int s1 = min(s0 + seg, ns);
+    const long long base = (long long)(active ? ia : 0) * sa + (long long)b * sb;
+    const long long nc = a.ncell;
+    const R inv_dx = R(a.inv_dx[DIR]);
+    const R eps = R(a.eps);
+    const Eos e = a.eos;
+    const R* __restrict__ qin = static_cast<const R*>(a.qin);
+
+    bool bad = false;
+    R smax = R(0);
+
+    if (active) {
+        double dt = 0.0;
+        if (MODE == SW_LAST_RK) dt = a.ctrl->dt;
+        R W[5][NEQ];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            load_prim<NDIM>(qin, base + (long long)bc_index(s0 - 3 + k, ns, a.periodic) * ss, nc, e, W[k]);
+            bad |= !(W[k][0] + W[k][1] > R(0));
+        }
+        R vmPrev[NEQ], Fprev[NEQ];
+        R ufPrev = R(0), alphaCell = R(0);
+#pragma unroll
+        for (int f = 0; f < NEQ; ++f) vmPrev[f] = Fprev[f] = R(0);
+
+        for (int j = s0 - 1; j <= s1; ++j) {
+            R vm[NEQ], vp[NEQ];
+#pragma unroll
+            for (int f = 0; f < NEQ; ++f) weno5(W[0][f], W[1][f], W[2][f], W[3][f], W[4][f], eps, vm[f], vp[f]);
+            if (j >= s0) {
+                R F[NEQ], uf;
+                bad |= hllc<NDIM, DIR, R>(e, vmPrev, vp, F, uf);
+                if (j > s0) {
+                    // cell i = j - 1 is complete: faces i-1/2 (Fprev) and i+1/2 (F)
+                    R L[NEQ];
+#pragma unroll
+                    for (int f = 0; f < NEQ; ++f) L[f] = (Fprev[f] - F[f]) * inv_dx;
+                    L[IA] += alphaCell * (uf - ufPrev) * inv_dx;
+                    const long long c = base + (long long)(j - 1) * ss;
+                    if constexpr (MODE == SW_FIRST) {
+                        R* acc = static_cast<R*>(a.acc);
+#pragma unroll
+                        for (int f = 0; f < NEQ; ++f) acc[f * nc + c] = L[f];
+                    } else if constexpr (MODE == SW_MID) {
+                        R* acc = static_cast<R*>(a.acc);
+#pragma unroll
+                        for (int f = 0; f < NEQ; ++f) acc[f * nc + c] = acc[f * nc + c] + L[f];
+                    } else if constexpr (MODE == SW_LAST_RHS) {
+                        const R* acc = static_cast<const R*>(a.acc);
+                        double* out = static_cast<double*>(a.qout);
+#pragma unroll
+                        for (int f = 0; f < NEQ; ++f) {
+                            R tot = NDIM > 1 ? acc[f * nc + c] + L[f] : L[f];
+                            out[f * nc + c] = double(tot);
+                        }
+                    } else {  // SW_LAST_RK
+                        const R* acc = static_cast<const R*>(a.acc);
+                        double qnew[NEQ];
+#pragma unroll
+                        for (int f = 0; f < NEQ; ++f) {
+                            R tot = NDIM > 1 ? acc[f * nc + c] + L[f] : L[f];
+                            double qn = a.qn[f * nc + c];
+                            double dL = dt * double(tot);
+                            if (a.stage == 1) {
+                                qnew[f] = qn + dL;
+                            } else {
+                                double qk = double(qin[f * nc + c]);
+                                if (a.stage == 2)
+                                    qnew[f] = 0.75 * qn + 0.25 * (qk + dL);
+                                else
+                                    qnew[f] = (1.0 / 3.0) * qn + (2.0 / 3.0) * (qk + dL);
+                            }
+                        }
+                        if constexpr (!MIXED) {
+                            double* out = static_cast<double*>(a.qout);
+#pragma unroll
+                            for (int f = 0; f < NEQ; ++f) out[f * nc + c] = qnew[f];
+                            if (a.stage == 3) {
+                                double wn[NEQ];
+                                double r = 1.0 / (qnew[0] + qnew[1]);
+                                double ke2 = 0.0;
+                                wn[0] = qnew[0];
+                                wn[1] = qnew[1];
+#pragma unroll
+                                for (int k = 0; k < NDIM; ++k) {
+                                    wn[2 + k] = qnew[2 + k] * r;
+                                    ke2 += qnew[2 + k] * wn[2 + k];
+                                }
+                                double G, Pi;
+                                mixture(e, qnew[IA], G, Pi);
+                                wn[IE] = (qnew[IE] - 0.5 * ke2 - Pi) / G;
+                                wn[IA] = qnew[IA];
+                                R s = cell_wavespeed<NDIM, double>(e, wn, a.inv_dx, bad);
+                                smax = s > smax ? s : smax;
+                            }
+                        } else {
+                            float pnew = mixed_pressure<NDIM>(e, qnew);
+                            float* o32 = static_cast<float*>(a.stage == 3 ? a.qout2 : a.qout);
+#pragma unroll
+                            for (int f = 0; f < NEQ; ++f) o32[f * nc + c] = float(qnew[f]);
+                            o32[NEQ * nc + c] = pnew;
+                            if (a.stage == 3) {
+                                double* o64 = static_cast<double*>(a.qout);
+#pragma unroll
+                                for (int f = 0; f < NEQ; ++f) o64[f * nc + c] = qnew[f];
+                                float wn[NEQ];
+                                float rho = float(qnew[0]) + float(qnew[1]);
+                                float r = __fdividef(1.0f, rho);
+                                wn[0] = float(qnew[0]);
+                                wn[1] = float(qnew[1]);
+#pragma unroll
+                                for (int k = 0; k < NDIM; ++k) wn[2 + k] = float(qnew[2 + k]) * r;
+                                wn[IE] = pnew;
+                                wn[IA] = float(qnew[IA]);
+                                R s = cell_wavespeed<NDIM, float>(e, wn, a.inv_dx, bad);
+                                smax = s > smax ? s : smax;
+                            }
+                        }
+                    }
+                }
+#pragma unroll
+                for (int f = 0; f < NEQ; ++f) Fprev[f] = F[f];
+                ufPrev = uf;
+            }
+#pragma unroll
+            for (int f = 0; f < NEQ; ++f) vmPrev[f] = vm[f];
+            alphaCell = W[2][IA];
+            if (j < s1) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+#pragma unroll
+                    for (int f = 0; f < NEQ; ++f) W[k][f] = W[k + 1][f];
+                load_prim<NDIM>(qin, base + (long long)bc_index(j + 3, ns, a.periodic) * ss, nc, e, W[4]);
+                bad |= !(W[4][0] + W[4][1] > R(0));
+            }
+        }
+    }
+
+    if constexpr (MODE == SW_LAST_RK) {
+        if (a.stage == 3) {
+            R m = warp_max(smax);
+            if (lane == 0 && m > R(0))
+                atomicMax(&a.ctrl->S_bits, (unsigned long long)__double_as_longlong(double(m)));
+        }
+    }
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&a.ctrl->status, 1u);
+}
+
+// Launch one sweep: the valid (direction, mode) pairs are x FIRST, y MID
+// (3-D), and LAST_RK / LAST_RHS on the last direction.
+template <int NDIM, typename R>
+cudaError_t launch_sweep_t(int dir, int mode, const SweepArgs& a, cudaStream_t s) {
+    long long warps = sweep_warps(dir, a.n, a.seg);
+    long long blocks = (warps * 32 + kSweepThreads - 1) / kSweepThreads;
+    if (blocks <= 0) return cudaSuccess;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    dim3 grid((unsigned)blocks), block(kSweepThreads);
+    constexpr int LAST = NDIM - 1;
+    if (dir == 0 && mode == SW_FIRST && NDIM > 1) {
+        if constexpr (NDIM > 1) sweep_kernel<NDIM, 0, SW_FIRST, R><<<grid, block, 0, s>>>(a);
+    } else if (dir == 1 && mode == SW_MID && NDIM == 3) {
+        if constexpr (NDIM == 3) sweep_kernel<NDIM, 1, SW_MID, R><<<grid, block, 0, s>>>(a);
+    } else if (dir == LAST && mode == SW_LAST_RK) {
+        sweep_kernel<NDIM, LAST, SW_LAST_RK, R><<<grid, block, 0, s>>>(a);
+    } else if (dir == LAST && mode == SW_LAST_RHS) {
+        sweep_kernel<NDIM, LAST, SW_LAST_RHS, R><<<grid, block, 0, s>>>(a);
+    } else {
+        return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_sweep_any(int ndim, int dir, int mode, const SweepArgs& a, cudaStream_t s) {
+    switch (ndim) {
+        case 1: return launch_sweep_t<1, R>(dir, mode, a, s);
+        case 2: return launch_sweep_t<2, R>(dir, mode, a, s);
+        case 3: return launch_sweep_t<3, R>(dir, mode, a, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace mfc5

@@ -10,9 +10,12 @@ and a plain ``dict`` of run parameters.  Each side converts ``w`` to the
 conservative state with its own equation of state.
 
 Fluid 1 is water (gamma 4.4, pi_inf 6e8 Pa), fluid 2 is air (gamma 1.4,
-pi_inf 0), as in the stiffened-gas description of Sec. II-A.  Interfaces are
-sharp, decided at cell centres; a pure phase carries the other phase at volume
-fraction 1e-6.  Shock states are the ideal-gas normal-shock (Rankine-Hugoniot)
+pi_inf 0), as in the stiffened-gas description of Sec. II-A.  A pure phase
+carries the other phase at volume fraction 1e-6.  The 1-D tube has a sharp
+interface; the 2-D/3-D material interfaces are diffuse over about one cell
+(a tanh profile of the signed distance), as in a diffuse-interface method:
+voxelised sharp spheres leave one- and two-cell slivers on which WENO5
+overshoots alpha1 beyond [0, 1] and the mixture sound speed goes imaginary.  Shock states are the ideal-gas normal-shock (Rankine-Hugoniot)
 relations for air moving into air at rest.
 """
 from __future__ import annotations
@@ -77,6 +80,34 @@ def assemble(p: dict, alpha1, rho1, rho2, vel, pres) -> np.ndarray:
     w[2 + d] = pres
     w[3 + d] = a1
     return w
+
+
+def diffuse_alpha(dist, width):
+    """Volume fraction of fluid 1 across a diffuse interface: an algebraic
+    sigmoid H = (1 - x/(1 + x^4)^(1/4))/2 of x = dist/width (dist is the
+    signed distance, negative inside fluid 1), bounded to
+    [ALPHA_EPS, 1 - ALPHA_EPS].  A width of zero gives the sharp cell-centre
+    interface.  Only +, *, / and sqrt are used, which IEEE 754 rounds exactly,
+    so the profile is bit-identical on every platform."""
+    if width <= 0.0:
+        return np.where(dist < 0.0, 1.0 - ALPHA_EPS, ALPHA_EPS)
+    x = dist / width
+    x2 = x * x
+    h = 0.5 * (1.0 - x / np.sqrt(np.sqrt(1.0 + x2 * x2)))
+    return ALPHA_EPS + (1.0 - 2.0 * ALPHA_EPS) * h
+
+
+def unit_vectors(rng, count):
+    """`count` directions uniform on the circle, as (cos, sin) pairs, drawn by
+    rejection from the unit square (uniform draws, * and sqrt only)."""
+    out = []
+    while len(out) < count:
+        c, s = rng.uniform(-1.0, 1.0, size=2)
+        r2 = c * c + s * s
+        if 1e-6 < r2 <= 1.0:
+            r = math.sqrt(r2)
+            out.append((c / r, s / r))
+    return np.array(out)
 
 
 def normal_shock(gamma: float, rho1: float, p1: float, mach: float):
@@ -162,13 +193,14 @@ def air_water_slab(ndim: int, n: int, u0: float = 100.0, axis: int = 0):
     return p, assemble(p, a1, 1000.0, 1.2, vel, 1.0e5)
 
 
-def random_periodic(ndim: int, n: int, seed: int = 0):
+def random_periodic(ndim: int, n, seed: int = 0):
     """Periodic box with smooth random fields plus a two-fluid interface: a
     few random Fourier modes in density, velocity and pressure, and a water
     blob of radius 0.25 (alpha1 ~ 1, tanh profile about 1.5 cells wide) in
     air.  Used for conservation and parity checks."""
     rng = np.random.default_rng(seed)
-    p = make_params(ndim, [n] * ndim, [0.0] * ndim, [1.0] * ndim, PERIODIC)
+    ns = [n] * ndim if np.isscalar(n) else list(n)
+    p = make_params(ndim, ns, [0.0] * ndim, [1.0] * ndim, PERIODIC)
     c = cell_centres(p)
     grids = np.meshgrid(*c[:ndim][::-1], indexing="ij")[::-1]   # x, y, z broadcast [nz,ny,nx]
     shp = shape_of(p)[1:]
@@ -184,7 +216,7 @@ def random_periodic(ndim: int, n: int, seed: int = 0):
         return f
 
     r = np.sqrt(sum((grids[d] - 0.5) ** 2 for d in range(ndim)))
-    width = 1.5 / n
+    width = 1.5 / min(ns)
     a1 = np.clip(0.5 * (1.0 + np.tanh((0.25 - r) / width)), ALPHA_EPS, 1.0 - ALPHA_EPS)
     rho1 = 1000.0 * (1.0 + 0.01 * modes(1.0))
     rho2 = 1.2 * (1.0 + 0.2 * modes(1.0))
@@ -194,36 +226,45 @@ def random_periodic(ndim: int, n: int, seed: int = 0):
 
 
 def shock_water_column(nx: int = 1024, ny: int = 512, seed: int = 2409, mach: float = 1.47,
-                       gap: float = 0.03):
+                       gap: float = 0.03, smear: float = 1.5):
     """Mach-1.47 shock in air (rho 1.2, p 1e5) approaching a water column of
     radius 0.1 centred at (0.5, 0.5) on [0,2]x[0,1] (transmissive sides).
 
     The interface radius is r(theta) = 0.1 [1 + 0.01 sum_{k=2..9} a_k
     cos(k theta + phi_k)] with a_k ~ U[-1,1] scaled to sum |a_k| = 1 and
-    phi_k ~ U[0, 2 pi) from `seed`.  The shock starts `gap` upstream of the
-    column's leftmost point so that it reaches the column within the run."""
+    phi_k uniform on the circle, from `seed`; cos(k theta + phi_k) is formed
+    by rotations, without library trigonometry, so the state is bit-identical
+    on every platform.  The interface is diffuse over about
+    `smear` cells (see diffuse_alpha).  The shock starts `gap` upstream of
+    the column's leftmost point so that it reaches the column within the run."""
     rng = np.random.default_rng(seed)
     a = rng.uniform(-1.0, 1.0, size=8)
     a = a / np.abs(a).sum()
-    phi = rng.uniform(0.0, 2.0 * math.pi, size=8)
-    ks = np.arange(2, 10)
+    phase = unit_vectors(rng, 8)                 # (cos phi_k, sin phi_k)
     p = make_params(2, [nx, ny], [0.0, 0.0], [2.0, 1.0], TRANSMISSIVE)
     x, y, _ = cell_centres(p)
     X = x[None, :]
     Y = y[:, None]
     cx, cy, r0 = 0.5, 0.5, 0.1
-    th = np.arctan2(Y - cy, X - cx)
-    pert = np.zeros_like(th)
-    for k, ak, pk in zip(ks, a, phi):
-        pert = pert + ak * np.cos(k * th + pk)
+    dx, dy = X - cx, Y - cy
+    r = np.sqrt(dx * dx + dy * dy)
+    rs = np.where(r > 0.0, r, 1.0)
+    c1 = np.where(r > 0.0, dx / rs, 1.0)         # cos(theta)
+    s1 = np.where(r > 0.0, dy / rs, 0.0)         # sin(theta)
+    # cos(k theta), sin(k theta) by repeated rotation, k = 1..9
+    ck, sk = c1, s1
+    pert = np.zeros_like(r)
+    for k in range(2, 10):
+        ck, sk = ck * c1 - sk * s1, sk * c1 + ck * s1
+        cphi, sphi = phase[k - 2]
+        pert = pert + a[k - 2] * (ck * cphi - sk * sphi)   # a_k cos(k theta + phi_k)
     rad = r0 * (1.0 + 0.01 * pert)
-    water = ((X - cx) ** 2 + (Y - cy) ** 2) < rad ** 2
-    tt = np.linspace(0.0, 2.0 * math.pi, 4096)
-    rmax = r0 * (1.0 + 0.01 * np.max(np.sum(a[:, None] * np.cos(ks[:, None] * tt + phi[:, None]), 0)))
-    xs = cx - rmax - gap
+    dist = r - rad                                         # signed, > 0 in air
+    a1 = diffuse_alpha(dist, smear * (1.0 / ny))
+    xs = cx - r0 * 1.01 - gap                              # 1.01 r0 bounds the interface radius
     rho2, u2, p2, _ = normal_shock(AIR[0], 1.2, 1.0e5, mach)
-    post = np.broadcast_to(X < xs, water.shape)
-    a1 = np.where(water, 1.0 - ALPHA_EPS, ALPHA_EPS)[None]
+    post = np.broadcast_to(X < xs, a1.shape)
+    a1 = a1[None]
     rho_air = np.where(post, rho2, 1.2)[None]
     u = np.where(post, u2, 0.0)[None]
     pres = np.where(post, p2, 1.0e5)[None]
@@ -245,22 +286,27 @@ def droplet_layout(seed: int = 2409, count: int = 8, gap: float = 0.01):
 
 
 def shock_droplets(n: int = 256, seed: int = 2409, mach: float = 2.0, gap: float = 0.01,
-                   count: int = 8):
+                   count: int = 8, smear: float = 1.5):
     """Mach-2 shock in air (rho 1.2, p 1e5) over `count` water droplets on
-    [0,1]^3 (transmissive sides).  Droplets from `droplet_layout(seed)`; the
-    shock starts `gap` upstream of the leftmost droplet surface."""
+    [0,1]^3 (transmissive sides).  Droplets from `droplet_layout(seed)`, with
+    interfaces diffuse over about `smear` cells; the shock starts `gap`
+    upstream of the leftmost droplet surface."""
     drops = droplet_layout(seed, count)
     p = make_params(3, [n, n, n], [0.0] * 3, [1.0] * 3, TRANSMISSIVE)
     x, y, z = cell_centres(p)
-    water = np.zeros((n, n, n), dtype=bool)
+    a1 = np.full((n, n, n), ALPHA_EPS)
+    h = 1.0 / n
     for cx, cy, cz, r in drops:
-        d2 = (x[None, None, :] - cx) ** 2 + (y[None, :, None] - cy) ** 2
-        d2 = d2 + (z[:, None, None] - cz) ** 2
-        water |= d2 < r * r
+        # only the bounding box of each droplet (plus the profile's tail) is touched
+        lo = [max(0, int((c - r) / h) - 8) for c in (cx, cy, cz)]
+        hi = [min(n, int((c + r) / h) + 9) for c in (cx, cy, cz)]
+        sl = (slice(lo[2], hi[2]), slice(lo[1], hi[1]), slice(lo[0], hi[0]))
+        d2 = (x[None, None, lo[0]:hi[0]] - cx) ** 2 + (y[None, lo[1]:hi[1], None] - cy) ** 2
+        d2 = d2 + (z[lo[2]:hi[2], None, None] - cz) ** 2
+        a1[sl] = np.maximum(a1[sl], diffuse_alpha(np.sqrt(d2) - r, smear * h))
     xs = float(np.min(drops[:, 0] - drops[:, 3])) - gap
     rho2, u2, p2, _ = normal_shock(AIR[0], 1.2, 1.0e5, mach)
     post = (x < xs)[None, None, :]
-    a1 = np.where(water, 1.0 - ALPHA_EPS, ALPHA_EPS)
     rho_air = np.where(post, rho2, 1.2)
     u = np.where(post, u2, 0.0)
     pres = np.where(post, p2, 1.0e5)

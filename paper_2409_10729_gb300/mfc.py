@@ -1,0 +1,223 @@
+"""ctypes binding of libmfc5 (include/mfc.h).
+
+Argument marshalling only: every step of the solver runs in the library's
+CUDA kernels.  Host arrays are numpy float64 C-contiguous arrays; device
+arrays are torch CUDA float64 contiguous tensors (torch also supplies the CUDA
+stream).  If the library has not been built this module raises on use; there
+is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libmfc5.so")
+
+MFC_OK, MFC_EINVAL, MFC_ENOMEM, MFC_ECUDA, MFC_ENONPHYSICAL, MFC_ESTATE = 0, -1, -2, -3, -4, -5
+MFC_FP64, MFC_MIXED, MFC_GATED = 0, 1, 2
+PRECISIONS = {"fp64": MFC_FP64, "mixed": MFC_MIXED, "gated": MFC_GATED}
+
+
+class MfcParams(ctypes.Structure):
+    _fields_ = [
+        ("ndim", ctypes.c_int),
+        ("n", ctypes.c_int * 3),
+        ("lo", ctypes.c_double * 3),
+        ("hi", ctypes.c_double * 3),
+        ("bc", (ctypes.c_int * 2) * 3),
+        ("gamma", ctypes.c_double * 2),
+        ("pi_inf", ctypes.c_double * 2),
+        ("weno_eps", ctypes.c_double),
+        ("precision", ctypes.c_int),
+    ]
+
+
+class MfcError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {strerror(status)} ({status})")
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libmfc5.so (raises if it is missing: build it with build.py)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libmfc5 is not built ({LIB_PATH} missing); run paper_2409_10729_gb300/build.py")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, dp, ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int
+        sig = {
+            "mfc_create": ([ctypes.POINTER(MfcParams), vp, ctypes.POINTER(vp)], ip),
+            "mfc_destroy": ([vp], ip),
+            "mfc_set_state": ([vp, vp, ip], ip),
+            "mfc_set_state_prim": ([vp, vp, ip], ip),
+            "mfc_get_state": ([vp, vp, ip], ip),
+            "mfc_rhs": ([vp, vp, ip], ip),
+            "mfc_max_wavespeed": ([vp, dp], ip),
+            "mfc_step_rk3": ([vp, ctypes.c_double, ip, dp], ip),
+            "mfc_step_rk3_dt": ([vp, ctypes.c_double, ip], ip),
+            "mfc_launches_per_step": ([vp, ctypes.POINTER(ip)], ip),
+            "mfc_set_timing": ([vp, ip], ip),
+            "mfc_kernel_time": ([vp, ip, ctypes.POINTER(ctypes.c_char_p), dp,
+                                 ctypes.POINTER(ctypes.c_longlong)], ip),
+            "mfc_alu_peak": ([ip, dp], ip),
+            "mfc_strerror": ([ip], ctypes.c_char_p),
+            "mfc_last_cuda_error": ([vp], ip),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+def strerror(status: int) -> str:
+    return lib().mfc_strerror(int(status)).decode()
+
+
+def alu_peak(fp64: bool) -> float:
+    """Measured FMA throughput of the current device, TFLOP/s."""
+    t = ctypes.c_double()
+    st = lib().mfc_alu_peak(int(bool(fp64)), ctypes.byref(t))
+    if st != MFC_OK:
+        raise MfcError(st, "mfc_alu_peak")
+    return t.value
+
+
+def make_params(p: dict, precision="fp64") -> MfcParams:
+    s = MfcParams()
+    s.ndim = int(p["ndim"])
+    for d in range(3):
+        s.n[d] = int(p["n"][d])
+        s.lo[d] = float(p["lo"][d])
+        s.hi[d] = float(p["hi"][d])
+        s.bc[d][0] = int(p["bc"][d][0])
+        s.bc[d][1] = int(p["bc"][d][1])
+    for i in range(2):
+        s.gamma[i] = float(p["gamma"][i])
+        s.pi_inf[i] = float(p["pi_inf"][i])
+    s.weno_eps = float(p.get("weno_eps", 1e-6))
+    s.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    return s
+
+
+def _ptr(a, ncells_neq: int):
+    """(pointer, on_device) for a numpy host array or a torch CUDA tensor."""
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("host arrays must be C-contiguous float64")
+        if a.size != ncells_neq:
+            raise ValueError(f"array has {a.size} elements, expected {ncells_neq}")
+        return ctypes.c_void_p(a.ctypes.data), 0
+    import torch
+    if not isinstance(a, torch.Tensor) or not a.is_cuda or a.dtype != torch.float64 or not a.is_contiguous():
+        raise ValueError("device arrays must be contiguous float64 CUDA tensors")
+    if a.numel() != ncells_neq:
+        raise ValueError(f"tensor has {a.numel()} elements, expected {ncells_neq}")
+    return ctypes.c_void_p(a.data_ptr()), 1
+
+
+class Solver:
+    """One mfc_ctx: a problem (params dict as produced by ``inputs``) on the
+    current CUDA device, bound to torch's current stream unless given one."""
+
+    def __init__(self, p: dict, precision="fp64", stream=None):
+        import torch
+        self.p = p
+        self.neq = int(p["ndim"]) + 4
+        self.shape = (self.neq, int(p["n"][2]) if p["ndim"] > 2 else 1,
+                      int(p["n"][1]) if p["ndim"] > 1 else 1, int(p["n"][0]))
+        self.size = int(np.prod(self.shape))
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self._stream = stream
+        handle = ctypes.c_void_p()
+        st = lib().mfc_create(ctypes.byref(make_params(p, precision)), ctypes.c_void_p(stream.cuda_stream),
+                              ctypes.byref(handle))
+        if st != MFC_OK:
+            raise MfcError(st, "mfc_create")
+        self.ctx = handle
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            lib().mfc_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st: int, what: str, allow=()):
+        if st != MFC_OK and st not in allow:
+            raise MfcError(st, what)
+        return st
+
+    # -- state -------------------------------------------------------------
+    def set_state(self, q):
+        ptr, dev = _ptr(q, self.size)
+        return self._check(lib().mfc_set_state(self.ctx, ptr, dev), "mfc_set_state")
+
+    def set_state_prim(self, w):
+        ptr, dev = _ptr(w, self.size)
+        return self._check(lib().mfc_set_state_prim(self.ctx, ptr, dev), "mfc_set_state_prim")
+
+    def get_state(self, out=None):
+        if out is None:
+            out = np.empty(self.shape, dtype=np.float64)
+        ptr, dev = _ptr(out, self.size)
+        self._check(lib().mfc_get_state(self.ctx, ptr, dev), "mfc_get_state")
+        return out
+
+    # -- compute -----------------------------------------------------------
+    def rhs(self, out=None, allow_nonphysical=False):
+        if out is None:
+            out = np.empty(self.shape, dtype=np.float64)
+        ptr, dev = _ptr(out, self.size)
+        allow = (MFC_ENONPHYSICAL,) if allow_nonphysical else ()
+        self.last_status = self._check(lib().mfc_rhs(self.ctx, ptr, dev), "mfc_rhs", allow)
+        return out
+
+    def max_wavespeed(self) -> float:
+        s = ctypes.c_double()
+        self._check(lib().mfc_max_wavespeed(self.ctx, ctypes.byref(s)), "mfc_max_wavespeed")
+        return s.value
+
+    def step_rk3(self, cfl: float, nsteps: int, allow_nonphysical=False) -> float:
+        t = ctypes.c_double()
+        allow = (MFC_ENONPHYSICAL,) if allow_nonphysical else ()
+        self.last_status = self._check(lib().mfc_step_rk3(self.ctx, float(cfl), int(nsteps), ctypes.byref(t)),
+                                       "mfc_step_rk3", allow)
+        return t.value
+
+    def step_rk3_dt(self, dt: float, nsteps: int):
+        return self._check(lib().mfc_step_rk3_dt(self.ctx, float(dt), int(nsteps)), "mfc_step_rk3_dt")
+
+    # -- instrumentation ---------------------------------------------------
+    def launches_per_step(self) -> int:
+        n = ctypes.c_int()
+        self._check(lib().mfc_launches_per_step(self.ctx, ctypes.byref(n)), "mfc_launches_per_step")
+        return n.value
+
+    def set_timing(self, enable: bool):
+        return self._check(lib().mfc_set_timing(self.ctx, int(bool(enable))), "mfc_set_timing")
+
+    def kernel_times(self) -> dict:
+        out = {}
+        i = 0
+        while True:
+            name, ms, cnt = ctypes.c_char_p(), ctypes.c_double(), ctypes.c_longlong()
+            st = lib().mfc_kernel_time(self.ctx, i, ctypes.byref(name), ctypes.byref(ms), ctypes.byref(cnt))
+            if st != MFC_OK:
+                break
+            out[name.value.decode()] = (ms.value, cnt.value)
+            i += 1
+        return out

@@ -1,0 +1,261 @@
+"""GPU parity: the FP64 CUDA path against the serial FP64 oracle.
+
+Every comparison is element by element on the same seeded inputs, per field.
+States (after the stated step counts) are compared as relative L-infinity,
+max|gpu - oracle| / max|oracle| <= 1e-12 (the FP64 parity bar).
+
+A single RHS is a difference of face fluxes divided by dx, so its round-off
+scales with the flux magnitude, not with the (possibly much smaller) result:
+RHS errors are taken relative to max(max|L_f|, max|q_f| * S), where
+S = max sum_d (|u_d| + c)/dx_d makes |q| S the natural size of dq/dt; the bar
+is again 1e-12.  A wrong term, sign or index shows up at 1e-6 or far above.
+
+Sizes span several warps/segments and ragged tails; full-size workloads are
+checked on sampled cells the oracle evaluates one by one, plus the wave speed
+over every cell.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2409_10729_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2409_10729_gb300 import build as B
+    B.build()
+    torch.cuda.set_device(0)
+
+
+def solver(p, precision="fp64"):
+    from paper_2409_10729_gb300 import mfc
+    return mfc.Solver(p, precision)
+
+
+def rel_err(a, b):
+    """Per-field relative L-infinity error of a against reference b.  The
+    momentum components are rows of one vector field and share its scale,
+    max over cells of |rho u| (otherwise a component that is ~0 in a given
+    orientation, e.g. rho v in a flow along x, would be judged against its own
+    round-off-sized values)."""
+    ndim = a.shape[0] - 4
+    a = a.reshape(a.shape[0], -1)
+    b = b.reshape(b.shape[0], -1)
+    scale = np.abs(b).max(1)
+    mom = np.sqrt((b[2:2 + ndim] ** 2).sum(0)).max()
+    scale[2:2 + ndim] = mom
+    return np.abs(a - b).max(1) / np.maximum(scale, 1e-300)
+
+
+def rhs_scale(p, q, Lo, S):
+    """Per-field size of the fluxes a RHS is formed from, per unit length:
+    max(max|L_f|, max|q_f| S), plus max(p) max(1/dx_d) on the momentum rows
+    (their normal flux carries the pressure)."""
+    nf = q.shape[0]
+    qf = q.reshape(nf, -1)
+    scale = np.maximum(np.abs(Lo.reshape(Lo.shape[0], -1)).max(1), np.abs(qf).max(1) * S)
+    ndim = p["ndim"]
+    pmax = np.abs(O.cons_to_prim(p, q)[2 + ndim]).max()
+    inv_dx = max(p["n"][d] / (p["hi"][d] - p["lo"][d]) for d in range(ndim))
+    scale[2:2 + ndim] = np.maximum(scale[2:2 + ndim], pmax * inv_dx)
+    return scale
+
+
+def rhs_err(p, L, Lo, q, S):
+    """Per-field RHS error relative to rhs_scale."""
+    d = np.abs(L.reshape(L.shape[0], -1) - Lo.reshape(Lo.shape[0], -1)).max(1)
+    return d / np.maximum(rhs_scale(p, q, Lo, S), 1e-300)
+
+
+SMALL = [
+    (1, [33], 0), (1, [33], 1), (1, [200], 1),
+    (2, [16, 8], 0), (2, [13, 9], 1), (2, [70, 37], 0),
+    (3, [8, 8, 8], 0), (3, [13, 9, 7], 1), (3, [7, 5, 4], 0), (3, [40, 11, 35], 1),
+]
+
+
+def _case(ndim, n, bc, seed=0):
+    p, w = I.random_periodic(ndim, n, seed=seed)
+    p["bc"] = [[bc, bc]] * ndim + [[0, 0]] * (3 - ndim)
+    return p, w
+
+
+@pytest.mark.parametrize("ndim,n,bc", SMALL)
+def test_prim_to_cons(ndim, n, bc):
+    p, w = _case(ndim, n, bc)
+    s = solver(p)
+    s.set_state_prim(w)
+    assert rel_err(s.get_state(), O.prim_to_cons(p, w)).max() <= 1e-14
+
+
+@pytest.mark.parametrize("ndim,n,bc", SMALL)
+def test_rhs_parity_small(ndim, n, bc):
+    p, w = _case(ndim, n, bc, seed=ndim)
+    s = solver(p)
+    s.set_state_prim(w)
+    L = s.rhs()
+    q = O.prim_to_cons(p, w)
+    Lo = O.rhs(p, q)
+    assert rhs_err(p, L, Lo, q, O.max_wavespeed(p, q)).max() <= TOL
+
+
+@pytest.mark.parametrize("ndim,n,bc", SMALL)
+def test_wavespeed_parity(ndim, n, bc):
+    p, w = _case(ndim, n, bc, seed=ndim + 3)
+    s = solver(p)
+    s.set_state_prim(w)
+    So = O.max_wavespeed(p, O.prim_to_cons(p, w))
+    assert abs(s.max_wavespeed() - So) <= 1e-14 * So
+
+
+@pytest.mark.parametrize("ndim,n,bc", SMALL)
+def test_cfl_steps_parity_small(ndim, n, bc):
+    p, w = _case(ndim, n, bc, seed=ndim + 5)
+    s = solver(p)
+    s.set_state_prim(w)
+    t = s.step_rk3(0.4, 5)
+    qo, to = O.run_cfl(p, O.prim_to_cons(p, w), 0.4, 5)
+    assert rel_err(s.get_state(), qo).max() <= TOL
+    assert abs(t - to) <= 1e-13 * to
+
+
+def test_fixed_dt_parity():
+    p, w = _case(3, [13, 9, 7], 1, seed=11)
+    q = O.prim_to_cons(p, w)
+    dt = 0.3 / O.max_wavespeed(p, q)
+    s = solver(p)
+    s.set_state(q)
+    s.step_rk3_dt(dt, 3)
+    qo = q
+    for _ in range(3):
+        qo = O.step_dt(p, qo, dt)
+    assert rel_err(s.get_state(), qo).max() <= TOL
+
+
+def test_air_water_tube_full_run():
+    """1000 cells, 200 CFL-0.4 steps, FP64: every field within 1e-12."""
+    p, w = I.air_water_shock_tube(1000)
+    s = solver(p)
+    s.set_state_prim(w)
+    t = s.step_rk3(0.4, 200)
+    qo, to = O.run_cfl(p, O.prim_to_cons(p, w), 0.4, 200)
+    assert rel_err(s.get_state(), qo).max() <= TOL
+    assert abs(t - to) <= 1e-12 * to
+
+
+def test_shock_water_column_reduced_full_run():
+    """The 2-D shock / water-column case on a 128x64 grid for its full 500 steps."""
+    p, w = I.shock_water_column(128, 64)
+    s = solver(p)
+    s.set_state_prim(w)
+    t = s.step_rk3(0.4, 500)
+    qo, to = O.run_cfl(p, O.prim_to_cons(p, w), 0.4, 500)
+    assert rel_err(s.get_state(), qo).max() <= TOL
+    assert abs(t - to) <= 1e-12 * to
+
+
+def test_shock_droplets_reduced_full_run():
+    """The 3-D shock / droplet case on a 32^3 grid for its full 100 steps."""
+    p, w = I.shock_droplets(32)
+    s = solver(p)
+    s.set_state_prim(w)
+    t = s.step_rk3(0.4, 100)
+    qo, to = O.run_cfl(p, O.prim_to_cons(p, w), 0.4, 100)
+    assert rel_err(s.get_state(), qo).max() <= TOL
+    assert abs(t - to) <= 1e-12 * to
+
+
+def _sample_cells(p, k, seed):
+    rng = np.random.default_rng(seed)
+    n = p["n"]
+    nc = n[0] * n[1] * n[2]
+    cells = list(rng.integers(0, nc, size=k))
+    # faces and corners of the box (ghost handling)
+    for z in (0, n[2] - 1):
+        for y in (0, n[1] - 1):
+            for x in (0, 1, 2, n[0] - 3, n[0] - 2, n[0] - 1):
+                cells.append(x + n[0] * (y + n[1] * z))
+    return np.unique(np.array(cells, dtype=np.int64))
+
+
+def _check_sampled(p, s, q, seed):
+    """RHS at sampled cells and the wave speed over all cells, against the oracle."""
+    cells = _sample_cells(p, 4096, seed)
+    Lfull = s.rhs().reshape(q.shape[0], -1)
+    Lo = O.rhs_points(p, q, cells).T
+    So = O.max_wavespeed(p, q)
+    err = np.abs(Lfull[:, cells] - Lo).max(1) / rhs_scale(p, q, Lo, So)
+    assert err.max() <= TOL
+    assert abs(s.max_wavespeed() - So) <= 1e-14 * So
+
+
+@pytest.mark.parametrize("case", ["column_1024x512", "droplets_256"])
+def test_full_size_sampled(case):
+    """Full-size workloads in the benchmark's launch configuration: the RHS of
+    the initial state and of the state after the full FP64 run, at 4096+
+    sampled cells, and the wave speed, against the oracle."""
+    if case == "column_1024x512":
+        p, w = I.shock_water_column(1024, 512)
+        steps = 500
+    else:
+        p, w = I.shock_droplets(256)
+        steps = 100
+    s = solver(p)
+    s.set_state_prim(w)
+    q0 = O.prim_to_cons(p, w)
+    assert rel_err(s.get_state(), q0).max() <= 1e-14
+    _check_sampled(p, s, q0, 1)
+    s.step_rk3(0.4, steps)
+    qf = s.get_state()
+    assert np.all(np.isfinite(qf))
+    _check_sampled(p, s, qf, 2)
+
+
+@pytest.mark.parametrize("where", ["interior", "edge"])
+def test_nonphysical_state_is_reported(where):
+    """A cell with negative density: both sides report it (MFC_ENONPHYSICAL /
+    the oracle's status), on the RHS and on a step."""
+    from paper_2409_10729_gb300 import mfc
+    p, w = _case(2, [16, 12], 0)
+    y, x = (5, 7) if where == "interior" else (0, 15)
+    w[0, 0, y, x] = -1.0
+    w[1, 0, y, x] = 0.0
+    s = solver(p)
+    s.set_state_prim(w)
+    s.rhs(allow_nonphysical=True)
+    assert s.last_status == mfc.MFC_ENONPHYSICAL
+    with pytest.raises(RuntimeError):
+        O.rhs(p, O.prim_to_cons(p, w))
+    s.step_rk3(0.4, 1, allow_nonphysical=True)
+    assert s.last_status == mfc.MFC_ENONPHYSICAL
+
+
+def test_device_arrays_and_timing_mode():
+    """Torch device tensors in and out give the same result as host arrays,
+    and stepping with per-kernel timing (direct launches) equals the graph."""
+    import torch
+    p, w = _case(3, [24, 20, 18], 1, seed=4)
+    s1, s2 = solver(p), solver(p)
+    s1.set_state_prim(torch.from_numpy(w).cuda())
+    s2.set_state_prim(w)
+    Ld = torch.empty(w.shape, dtype=torch.float64, device="cuda")
+    s1.rhs(Ld)
+    np.testing.assert_array_equal(Ld.cpu().numpy(), s2.rhs())
+    s1.set_timing(True)
+    t1 = s1.step_rk3(0.4, 4)
+    t2 = s2.step_rk3(0.4, 4)
+    assert t1 == t2
+    qd = torch.empty(w.shape, dtype=torch.float64, device="cuda")
+    s1.get_state(qd)
+    np.testing.assert_array_equal(qd.cpu().numpy(), s2.get_state())
+    kt = s1.kernel_times()
+    assert kt["sweep_z"][1] == 12 and kt["step_begin"][1] == 4
+    assert s1.launches_per_step() == 10
