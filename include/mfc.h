@@ -38,7 +38,8 @@ typedef enum {
     MFC_ENOMEM = -2,        /* device or pinned-host allocation failed */
     MFC_ECUDA = -3,         /* a CUDA runtime call failed (see mfc_last_cuda_error) */
     MFC_ENONPHYSICAL = -4,  /* a face or cell state had rho<=0, c^2<=0 or NaN */
-    MFC_ESTATE = -5         /* call out of order (e.g. stepping before a state is set) */
+    MFC_ESTATE = -5,        /* call out of order (e.g. stepping before a state is set) */
+    MFC_ETOOBIG = -6        /* problem larger than mfc_rhs_noalloc's fixed scratch */
 } mfc_status;
 
 typedef enum {
@@ -126,6 +127,32 @@ int mfc_kernel_time(mfc_ctx* ctx, int index, const char** name, double* ms, long
  * roofline denominator.  Allocates and frees 16 bytes of device memory and
  * synchronises the legacy default stream. */
 int mfc_alu_peak(int fp64, double* tflops);
+
+/* Capacity, in doubles, of the fixed device scratch used by mfc_rhs_noalloc
+ * (16 MiB): it must hold neq * ncells doubles plus a 32-double control block. */
+#define MFC_NOALLOC_MAX_DOUBLES (2 * 1024 * 1024)
+
+/* The right-hand side L(q) of mfc_rhs, FP64 only, for callers that cannot
+ * allocate device memory when they need it -- e.g. code living inside a
+ * framework whose pool allocator owns the whole GPU, or a long-running
+ * service that must keep a fixed footprint and avoid cudaMalloc's implicit
+ * device synchronisation after start-up.  There is no counterpart in the
+ * paper; the arithmetic is that of mfc_rhs.
+ *   params       problem statement; precision must be MFC_FP64 (else MFC_EINVAL)
+ *   q            device pointer, conservative FP64 state, layout above
+ *   rhs          device pointer, receives L(q), same layout
+ *   cuda_stream  cudaStream_t the kernels run on (NULL = legacy default)
+ * No context, no allocation of any kind: the only scratch (accumulator and
+ * status word) is a fixed array in device memory that belongs to the loaded
+ * library and is held on every device that loads it until process exit.
+ * Problems with neq * ncells + 32 > MFC_NOALLOC_MAX_DOUBLES are rejected with
+ * MFC_ETOOBIG before anything is launched.  The first call on a device looks
+ * up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  Every call
+ * shares the array: calls whose kernels may overlap on the GPU race and must
+ * be serialised by the caller.  The call synchronises `cuda_stream` to read
+ * the status; returns MFC_ENONPHYSICAL as mfc_rhs does. */
+int mfc_rhs_noalloc(const mfc_params* params, const double* q, double* rhs, void* cuda_stream);
 
 /* Message for a status code (static storage). */
 const char* mfc_strerror(int status);

@@ -23,7 +23,7 @@ COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE
           "--expt-relaxed-constexpr"]
 # per-unit extra flags: the mixed form uses fast FP32 division/square root
 EXTRA = {"sweep_mixed.cu": ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"]}
-UNITS = ["capi.cu", "aux.cu", "sweep_fp64.cu", "sweep_mixed.cu"]
+UNITS = ["capi.cu", "aux.cu", "sweep_fp64.cu", "sweep_mixed.cu", "noalloc.cu"]
 
 
 def nvcc() -> str:

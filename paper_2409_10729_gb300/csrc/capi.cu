@@ -438,6 +438,7 @@ extern "C" const char* mfc_strerror(int status) {
         case MFC_ECUDA: return "CUDA runtime error";
         case MFC_ENONPHYSICAL: return "non-physical state (rho<=0, c^2<=0 or NaN)";
         case MFC_ESTATE: return "no state set";
+        case MFC_ETOOBIG: return "problem too large for the fixed no-allocation scratch";
         default: return "unknown status";
     }
 }

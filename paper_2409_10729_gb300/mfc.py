@@ -16,7 +16,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "lib", "libmfc5.so")
 
-MFC_OK, MFC_EINVAL, MFC_ENOMEM, MFC_ECUDA, MFC_ENONPHYSICAL, MFC_ESTATE = 0, -1, -2, -3, -4, -5
+MFC_OK, MFC_EINVAL, MFC_ENOMEM, MFC_ECUDA, MFC_ENONPHYSICAL, MFC_ESTATE, MFC_ETOOBIG = 0, -1, -2, -3, -4, -5, -6
+MFC_NOALLOC_MAX_DOUBLES = 2 * 1024 * 1024
 MFC_FP64, MFC_MIXED, MFC_GATED = 0, 1, 2
 PRECISIONS = {"fp64": MFC_FP64, "mixed": MFC_MIXED, "gated": MFC_GATED}
 
@@ -67,6 +68,7 @@ def lib() -> ctypes.CDLL:
             "mfc_kernel_time": ([vp, ip, ctypes.POINTER(ctypes.c_char_p), dp,
                                  ctypes.POINTER(ctypes.c_longlong)], ip),
             "mfc_alu_peak": ([ip, dp], ip),
+            "mfc_rhs_noalloc": ([ctypes.POINTER(MfcParams), vp, vp, vp], ip),
             "mfc_strerror": ([ip], ctypes.c_char_p),
             "mfc_last_cuda_error": ([vp], ip),
         }

@@ -39,6 +39,8 @@ def built():
 def test_full_size_run_matches_stored_oracle(name):
     from paper_2409_10729_gb300 import mfc
     path = os.path.join(HERE, "golden", f"{name}.json")
+    if not os.path.exists(path):
+        pytest.skip(f"stored oracle result {name}.json not generated (tests/golden/make_golden.py)")
     with open(path) as f:
         g = json.load(f)
     p, w = CASES[name]()
