@@ -2,7 +2,9 @@
 """Benchmark of the five-equation RHS hot path (WENO5-JS + HLLC + SSP-RK3).
 
 Metric: grind time, ns per (cell x equation x RHS evaluation), lower is better,
-and the fraction of the HBM roofline it reaches, for the FP64 and mixed forms.
+and the fraction of the HBM roofline it reaches, for the FP64 form (reference
+operation order, bit-identical to the oracle; the headline value), the
+reorganised FP64 form and the mixed-precision form.
 
 Workload (per GPU): the 3-D shock / droplet array, 256^3 cells, 7 equations,
 FP64, SSP-RK3 at CFL 0.4 (the timed "step" is one RK3 step = 3 RHS
@@ -41,7 +43,7 @@ FLOPS_RK_CELL = 28                                     # stage update, mean over
 FLOPS_WAVESPEED_CELL = 45                              # once per step, in the last stage
 # Algorithmic bytes per cell, equation and RHS: stage 1 reads q^n and writes
 # q^(1); stages 2-3 read q^(k) and q^n and write q^(k+1): 8/3 state arrays.
-ALG_BYTES = {"fp64": 8.0 / 3.0 * 8.0, "mixed": (12.0 + 16.0 + 20.0) / 3.0}
+ALG_BYTES = {"fp64": 8.0 / 3.0 * 8.0, "fp64_fast": 8.0 / 3.0 * 8.0, "mixed": (12.0 + 16.0 + 20.0) / 3.0}
 
 
 def dist_env():
@@ -284,6 +286,7 @@ def run_ours(args):
     p, w = I.shock_droplets(256)
     res = time_form("fp64", p, w, args.steps, args.warmup, local, rank, world)
     forms = {"fp64": res}
+    forms["fp64_fast"] = time_form("fp64_fast", p, w, args.steps, args.warmup, local, rank, world)
     if not args.no_mixed:
         pm, wm = I.shock_droplets(512)
         forms["mixed"] = time_form("mixed", pm, wm, max(2, args.steps // 2), args.warmup, local, rank, world)
@@ -330,10 +333,10 @@ def run_ours(args):
     roof = roofline_for("fp64", res, fp64_peak, "measured (FP64 FMA-chain probe)", hbm_peak, hbm_src)
     out_forms = {}
     for name, r in forms.items():
-        peak = fp64_peak if name == "fp64" else fp32_peak
+        peak = fp32_peak if name == "mixed" else fp64_peak
         rf = roofline_for(name, r, peak, "measured FMA-chain probe", hbm_peak, hbm_src)
         out_forms[name] = {"grind": round(r["grind"], 5), "unit": UNIT, "ms_per_step": round(r["ms"] / (
-            args.steps if name == "fp64" else max(2, args.steps // 2)), 3), "cells": r["ncell"],
+            max(2, args.steps // 2) if name == "mixed" else args.steps), 3), "cells": r["ncell"],
             "hbm_frac": rf["hbm"]["frac"], "hbm_gbs_algorithmic": rf["hbm"]["achieved_gbs"],
             "alu_frac": rf["frac"], "dominant_kernel": rf["kernel"],
             "kernel_ms": {k: round(v[0] / max(1, v[1]), 4) for k, v in r["kernels"].items() if v[1]},

@@ -21,9 +21,11 @@ LIB = os.path.join(LIBDIR, "libmfc5.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,
           "--expt-relaxed-constexpr"]
-# per-unit extra flags: the mixed form uses fast FP32 division/square root
-EXTRA = {"sweep_mixed.cu": ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"]}
-UNITS = ["capi.cu", "aux.cu", "sweep_fp64.cu", "sweep_mixed.cu", "noalloc.cu"]
+# per-unit extra flags: the mixed form uses fast FP32 division/square root; the
+# reference-order FP64 units must not contract a*b+c into FMAs
+EXTRA = {"sweep_mixed.cu": ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"],
+         "sweep_fp64x.cu": ["-fmad=false"], "aux.cu": ["-fmad=false"]}
+UNITS = ["capi.cu", "aux.cu", "sweep_fp64.cu", "sweep_fp64x.cu", "sweep_mixed.cu", "noalloc.cu"]
 
 
 def nvcc() -> str:

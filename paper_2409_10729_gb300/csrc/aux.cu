@@ -1,6 +1,8 @@
 // aux.cu -- small kernels around the sweeps: primitive -> conservative
 // conversion, the FP32 working copy of the mixed form, the standalone CFL
-// wave-speed reduction, and the per-step control kernel.
+// wave-speed reduction, and the per-step control kernel.  Built with
+// -fmad=false: the conversion and the wave speed follow the reference
+// operation order bit for bit, so every form starts from the same state.
 #include "sweep.cuh"
 
 namespace mfc5 {
@@ -15,24 +17,19 @@ static unsigned aux_blocks(long long n) {
 }
 
 // Primitive (alpha1 rho1, alpha2 rho2, u_k, p, alpha1) -> conservative, in
-// place (Sec. II-A: rho E = Gamma p + Pi + rho |u|^2 / 2).
+// place (Sec. II-A: rho E = Gamma p + Pi + rho |u|^2 / 2), in the reference
+// operation order (this file is built with -fmad=false).
 template <int NDIM>
 __global__ void prim_to_cons_kernel(double* q, long long nc, Eos e) {
     using FL = Fields<NDIM>;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < nc;
          c += (long long)gridDim.x * blockDim.x) {
-        double rho = q[c] + q[nc + c];
-        double ke2 = 0.0;
+        double w[FL::NEQ], v[FL::NEQ];
 #pragma unroll
-        for (int k = 0; k < NDIM; ++k) {
-            double u = q[(2 + k) * nc + c];
-            ke2 += u * u;
-            q[(2 + k) * nc + c] = rho * u;
-        }
-        double a1 = q[FL::IA * nc + c];
-        double G, Pi;
-        mixture(e, a1, G, Pi);
-        q[FL::IE * nc + c] = G * q[FL::IE * nc + c] + Pi + 0.5 * rho * ke2;
+        for (int f = 0; f < FL::NEQ; ++f) w[f] = q[f * nc + c];
+        exact::prim_to_cons<NDIM>(e, w, v);
+#pragma unroll
+        for (int f = 0; f < FL::NEQ; ++f) q[f * nc + c] = v[f];
     }
 }
 
@@ -53,12 +50,14 @@ __global__ void make_mixed_state_kernel(const double* __restrict__ qn, float* __
     }
 }
 
-// S = max over cells of sum_d (|u_d| + c)/dx_d of an FP64 state.
+// S = max over cells of sum_d (|u_d| + c)/dx_d of an FP64 state, in the
+// reference operation order.
 template <int NDIM>
-__global__ void wavespeed_kernel(const double* __restrict__ q, long long nc, Eos e, double idx0,
-                                 double idx1, double idx2, DevCtrl* ctrl) {
+__global__ void wavespeed_kernel(const double* __restrict__ q, long long nc, Eos e, double dx0, double dx1,
+                                 double dx2, double rdx0, double rdx1, double rdx2, DevCtrl* ctrl) {
     using FL = Fields<NDIM>;
-    const double inv_dx[3] = {idx0, idx1, idx2};
+    const double dx[3] = {dx0, dx1, dx2};
+    const double rdx[3] = {rdx0, rdx1, rdx2};
     double smax = 0.0;
     bool bad = false;
     long long stride = (long long)gridDim.x * blockDim.x;
@@ -69,9 +68,10 @@ __global__ void wavespeed_kernel(const double* __restrict__ q, long long nc, Eos
     for (long long it = 0; it < iters; ++it) {
         long long c = start + it * stride;
         if (c < nc) {
-            double w[FL::NEQ];
-            load_prim<NDIM>(q, c, nc, e, w);
-            double s = cell_wavespeed<NDIM, double>(e, w, inv_dx, bad);
+            double v[FL::NEQ];
+#pragma unroll
+            for (int f = 0; f < FL::NEQ; ++f) v[f] = __ldg(q + f * nc + c);
+            double s = exact::cell_wavespeed<NDIM>(e, v, dx, rdx, bad);
             smax = s > smax ? s : smax;
         }
     }
@@ -116,15 +116,17 @@ cudaError_t launch_make_mixed_state(int ndim, const double* qn, float* s0, long 
     return cudaGetLastError();
 }
 
-cudaError_t launch_wavespeed(int ndim, const double* q, long long nc, const int* n, const double* inv_dx,
+cudaError_t launch_wavespeed(int ndim, const double* q, long long nc, const double* dx, const double* rdx,
                              const Eos& e, DevCtrl* ctrl, cudaStream_t s) {
-    (void)n;
     cudaError_t err = cudaMemsetAsync(&ctrl->S_bits, 0, sizeof(unsigned long long), s);
     if (err != cudaSuccess) return err;
     unsigned g = aux_blocks(nc);
-    if (ndim == 1) wavespeed_kernel<1><<<g, kAuxThreads, 0, s>>>(q, nc, e, inv_dx[0], inv_dx[1], inv_dx[2], ctrl);
-    else if (ndim == 2) wavespeed_kernel<2><<<g, kAuxThreads, 0, s>>>(q, nc, e, inv_dx[0], inv_dx[1], inv_dx[2], ctrl);
-    else wavespeed_kernel<3><<<g, kAuxThreads, 0, s>>>(q, nc, e, inv_dx[0], inv_dx[1], inv_dx[2], ctrl);
+    if (ndim == 1)
+        wavespeed_kernel<1><<<g, kAuxThreads, 0, s>>>(q, nc, e, dx[0], dx[1], dx[2], rdx[0], rdx[1], rdx[2], ctrl);
+    else if (ndim == 2)
+        wavespeed_kernel<2><<<g, kAuxThreads, 0, s>>>(q, nc, e, dx[0], dx[1], dx[2], rdx[0], rdx[1], rdx[2], ctrl);
+    else
+        wavespeed_kernel<3><<<g, kAuxThreads, 0, s>>>(q, nc, e, dx[0], dx[1], dx[2], rdx[0], rdx[1], rdx[2], ctrl);
     return cudaGetLastError();
 }
 

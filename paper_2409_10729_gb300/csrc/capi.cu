@@ -31,6 +31,7 @@ struct mfc_ctx {
     int n[3];
     long long ncell;
     double inv_dx[3];
+    double dx[3], rdx[3];
     int periodic[3];
     int seg[3];
     Eos eos;
@@ -76,7 +77,7 @@ static int validate(const mfc_params* p) {
         if (!(p->gamma[i] > 1.0) || !isfinite(p->gamma[i]) || !(p->pi_inf[i] >= 0.0) || !isfinite(p->pi_inf[i]))
             return MFC_EINVAL;
     if (!(p->weno_eps > 0.0) || !isfinite(p->weno_eps)) return MFC_EINVAL;
-    if (p->precision != MFC_FP64 && p->precision != MFC_MIXED) return MFC_EINVAL;
+    if (p->precision != MFC_FP64 && p->precision != MFC_MIXED && p->precision != MFC_FP64_FAST) return MFC_EINVAL;
     return MFC_OK;
 }
 
@@ -89,8 +90,8 @@ static int pick_seg(int dir, const int* n) {
     return seg;
 }
 
-static size_t state_elem(const mfc_ctx* c) { return c->form == FORM_FP64 ? sizeof(double) : sizeof(float); }
-static int state_fields(const mfc_ctx* c) { return c->form == FORM_FP64 ? c->neq : c->neq + 1; }
+static size_t state_elem(const mfc_ctx* c) { return c->form == FORM_MIXED ? sizeof(float) : sizeof(double); }
+static int state_fields(const mfc_ctx* c) { return c->form == FORM_MIXED ? c->neq + 1 : c->neq; }
 
 static void free_all(mfc_ctx* c) {
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
@@ -113,12 +114,15 @@ extern "C" int mfc_create(const mfc_params* params, void* cuda_stream, mfc_ctx**
     ctx->p = *params;
     ctx->ndim = params->ndim;
     ctx->neq = params->ndim + 4;
-    ctx->form = params->precision == MFC_FP64 ? FORM_FP64 : FORM_MIXED;
+    ctx->form = params->precision == MFC_FP64 ? FORM_FP64_EXACT
+                : (params->precision == MFC_FP64_FAST ? FORM_FP64_FAST : FORM_MIXED);
     ctx->ncell = 1;
     for (int d = 0; d < 3; ++d) {
         ctx->n[d] = d < ctx->ndim ? params->n[d] : 1;
         ctx->ncell *= ctx->n[d];
         ctx->inv_dx[d] = d < ctx->ndim ? (double)ctx->n[d] / (params->hi[d] - params->lo[d]) : 0.0;
+        ctx->dx[d] = d < ctx->ndim ? (params->hi[d] - params->lo[d]) / (double)ctx->n[d] : 1.0;
+        ctx->rdx[d] = 1.0 / ctx->dx[d];
         ctx->periodic[d] = d < ctx->ndim ? params->bc[d][0] == MFC_BC_PERIODIC : 0;
     }
     for (int d = 0; d < ctx->ndim; ++d) ctx->seg[d] = pick_seg(d, ctx->n);
@@ -128,9 +132,8 @@ extern "C" int mfc_create(const mfc_params* params, void* cuda_stream, mfc_ctx**
     ctx->eos = Eos{g1, g2, P1, P2, g1 - g2, P1 - P2};
     ctx->stream = (cudaStream_t)cuda_stream;
 
-    cudaError_t e;
-    if ((e = cudaGetDevice(&ctx->device)) != cudaSuccess ||
-        (e = cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking)) != cudaSuccess) {
+    if (cudaGetDevice(&ctx->device) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
         free_all(ctx);
         free(ctx);
         return MFC_ECUDA;
@@ -178,6 +181,8 @@ static SweepArgs base_args(mfc_ctx* ctx) {
     for (int d = 0; d < 3; ++d) {
         a.n[d] = ctx->n[d];
         a.inv_dx[d] = ctx->inv_dx[d];
+        a.dx[d] = ctx->dx[d];
+        a.rdx[d] = ctx->rdx[d];
     }
     a.ncell = ctx->ncell;
     a.eos = ctx->eos;
@@ -191,13 +196,16 @@ static SweepArgs base_args(mfc_ctx* ctx) {
 static cudaError_t launch_sweep(mfc_ctx* ctx, int dir, int mode, SweepArgs a, cudaStream_t s) {
     a.periodic = ctx->periodic[dir];
     a.seg = ctx->seg[dir];
-    return ctx->form == FORM_FP64 ? launch_sweep_fp64(ctx->ndim, dir, mode, a, s)
-                                  : launch_sweep_mixed(ctx->ndim, dir, mode, a, s);
+    switch (ctx->form) {
+        case FORM_FP64_EXACT: return launch_sweep_fp64x(ctx->ndim, dir, mode, a, s);
+        case FORM_FP64_FAST: return launch_sweep_fp64(ctx->ndim, dir, mode, a, s);
+        default: return launch_sweep_mixed(ctx->ndim, dir, mode, a, s);
+    }
 }
 
 // The stage input/output buffers of stage k (1..3).
 static void stage_buffers(mfc_ctx* ctx, int k, SweepArgs& a) {
-    const void* in0 = ctx->form == FORM_FP64 ? (const void*)ctx->qn : (const void*)ctx->s0;
+    const void* in0 = ctx->form == FORM_MIXED ? (const void*)ctx->s0 : (const void*)ctx->qn;
     a.stage = k;
     a.qin = k == 1 ? in0 : (k == 2 ? ctx->sa : ctx->sb);
     a.qout = k == 1 ? ctx->sa : (k == 2 ? ctx->sb : (void*)ctx->qn);
@@ -256,7 +264,7 @@ static int ensure_graph(mfc_ctx* ctx) {
 static int after_state_change(mfc_ctx* ctx) {
     if (ctx->form == FORM_MIXED)
         CK(launch_make_mixed_state(ctx->ndim, ctx->qn, ctx->s0, ctx->ncell, ctx->eos, ctx->stream));
-    CK(launch_wavespeed(ctx->ndim, ctx->qn, ctx->ncell, ctx->n, ctx->inv_dx, ctx->eos, ctx->ctrl, ctx->stream));
+    CK(launch_wavespeed(ctx->ndim, ctx->qn, ctx->ncell, ctx->dx, ctx->rdx, ctx->eos, ctx->ctrl, ctx->stream));
     ctx->have_state = true;
     return MFC_OK;
 }
@@ -319,7 +327,7 @@ extern "C" int mfc_rhs(mfc_ctx* ctx, double* rhs, int on_device) {
     if (st) return st;
     double* out = on_device ? rhs : NULL;
     if (!out) {
-        if (ctx->form == FORM_FP64) {
+        if (ctx->form != FORM_MIXED) {
             out = (double*)ctx->acc;  // the last sweep reads and writes each cell in place
         } else {
             if (!ctx->tmp64 && cudaMalloc((void**)&ctx->tmp64, (size_t)ctx->ncell * ctx->neq * sizeof(double)) !=
@@ -331,7 +339,7 @@ extern "C" int mfc_rhs(mfc_ctx* ctx, double* rhs, int on_device) {
         }
     }
     SweepArgs a = base_args(ctx);
-    a.qin = ctx->form == FORM_FP64 ? (const void*)ctx->qn : (const void*)ctx->s0;
+    a.qin = ctx->form == FORM_MIXED ? (const void*)ctx->s0 : (const void*)ctx->qn;
     a.qout = out;
     a.stage = 0;
     for (int d = 0; d < ctx->ndim; ++d) {
@@ -351,7 +359,7 @@ extern "C" int mfc_max_wavespeed(mfc_ctx* ctx, double* s) {
     if (!ctx->have_state) return MFC_ESTATE;
     int st = write_ctrl_params(ctx, 0.0, 0.0);
     if (st) return st;
-    CK(launch_wavespeed(ctx->ndim, ctx->qn, ctx->ncell, ctx->n, ctx->inv_dx, ctx->eos, ctx->ctrl, ctx->stream));
+    CK(launch_wavespeed(ctx->ndim, ctx->qn, ctx->ncell, ctx->dx, ctx->rdx, ctx->eos, ctx->ctrl, ctx->stream));
     st = read_ctrl(ctx);
     if (st) return st;
     unsigned long long bits = ctx->ctrl_h->S_bits;

@@ -36,7 +36,9 @@ struct SweepArgs {
     void* qout2;          // mixed form, stage 3: FP32 copy of q^{n+1} with p
     int n[3];
     long long ncell;
-    double inv_dx[3];
+    double inv_dx[3];     // n/(hi - lo) per direction (reformulated forms)
+    double dx[3];         // (hi - lo)/n per direction
+    double rdx[3];        // RN(1/dx) per direction (reference-order form)
     Eos eos;
     double eps;
     int periodic;         // along the sweep direction
@@ -45,18 +47,22 @@ struct SweepArgs {
     DevCtrl* ctrl;
 };
 
-// Form selectors
-enum Form { FORM_FP64 = 0, FORM_MIXED = 1 };
+// Arithmetic forms of the sweep kernels:
+//   FORM_FP64_FAST   FP64, formulas reorganised for fewer FP64 instructions
+//   FORM_MIXED       FP32 stencils/Riemann, FP64 pressure numerator and RK update
+//   FORM_FP64_EXACT  FP64 in the reference operation order (bit-identical to it)
+enum Form { FORM_FP64_FAST = 0, FORM_MIXED = 1, FORM_FP64_EXACT = 2 };
 
 cudaError_t launch_sweep_fp64(int ndim, int dir, int mode, const SweepArgs& a, cudaStream_t s);
 cudaError_t launch_sweep_mixed(int ndim, int dir, int mode, const SweepArgs& a, cudaStream_t s);
+cudaError_t launch_sweep_fp64x(int ndim, int dir, int mode, const SweepArgs& a, cudaStream_t s);
 
 // auxiliary kernels (aux.cu)
 cudaError_t launch_prim_to_cons(int ndim, double* q, long long ncell, const Eos& e, cudaStream_t s);
 cudaError_t launch_make_mixed_state(int ndim, const double* qn, float* s0, long long ncell,
                                     const Eos& e, cudaStream_t s);
-cudaError_t launch_wavespeed(int ndim, const double* q, long long ncell, const int* n,
-                             const double* inv_dx, const Eos& e, DevCtrl* ctrl, cudaStream_t s);
+cudaError_t launch_wavespeed(int ndim, const double* q, long long ncell, const double* dx,
+                             const double* rdx, const Eos& e, DevCtrl* ctrl, cudaStream_t s);
 cudaError_t launch_step_begin(DevCtrl* ctrl, cudaStream_t s);
 cudaError_t launch_f32_to_f64(const float* src, double* dst, long long count, cudaStream_t s);
 cudaError_t run_fma_probe(int fp64, double* tflops, cudaStream_t s);

@@ -32,13 +32,14 @@
 
 using namespace mfc5;
 
+// The fixed scratch: a file-scope device array of the library image.
+static __device__ __align__(256) double g_noalloc_scratch[MFC_NOALLOC_MAX_DOUBLES];
+
 namespace {
 
 // First 32 doubles: the control block (status word); the rest: accumulator.
 constexpr long long kCtrlDoubles = 32;
 static_assert(sizeof(DevCtrl) <= kCtrlDoubles * sizeof(double), "control block does not fit");
-
-__device__ __align__(256) double g_noalloc_scratch[MFC_NOALLOC_MAX_DOUBLES];
 
 constexpr int kMaxDevices = 64;
 double* g_scratch_addr[kMaxDevices];  // device address of g_noalloc_scratch, per device
@@ -105,6 +106,8 @@ extern "C" int mfc_rhs_noalloc(const mfc_params* params, const double* q, double
     for (int d = 0; d < 3; ++d) {
         a.n[d] = n[d];
         a.inv_dx[d] = d < ndim ? (double)n[d] / (params->hi[d] - params->lo[d]) : 0.0;
+        a.dx[d] = d < ndim ? (params->hi[d] - params->lo[d]) / (double)n[d] : 1.0;
+        a.rdx[d] = 1.0 / a.dx[d];
     }
     a.ncell = ncell;
     a.eos = Eos{g1, g2, P1, P2, g1 - g2, P1 - P2};
@@ -120,7 +123,7 @@ extern "C" int mfc_rhs_noalloc(const mfc_params* params, const double* q, double
         while (seg > 4 && sweep_warps(d, n, seg) * 32 < 152LL * 256) seg >>= 1;
         a.seg = seg;
         int mode = d == ndim - 1 ? SW_LAST_RHS : (d == 0 ? SW_FIRST : SW_MID);
-        if (launch_sweep_fp64(ndim, d, mode, a, s) != cudaSuccess) return MFC_ECUDA;
+        if (launch_sweep_fp64x(ndim, d, mode, a, s) != cudaSuccess) return MFC_ECUDA;
     }
     unsigned int status = 0;
     if (cudaMemcpyAsync(&status, &ctrl->status, sizeof(status), cudaMemcpyDeviceToHost, s) != cudaSuccess ||

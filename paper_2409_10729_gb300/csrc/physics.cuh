@@ -39,27 +39,44 @@ __device__ __forceinline__ R rdiv(R a, R b) { return a / b; }
 template <typename R>
 __device__ __forceinline__ R sqrt_pos(R x) { return sqrt(x); }
 
+// EOS constants in the working precision R (converted once per thread, so the
+// FP32 path issues no FP64 conversions per face).
+template <typename R>
+struct EosR {
+    R dg, g2, dP, P2;
+    __device__ __forceinline__ explicit EosR(const Eos& e) : dg(R(e.dg)), g2(R(e.g2)), dP(R(e.dP)), P2(R(e.P2)) {}
+};
+
 // Mixture Gamma and Pi at volume fraction a1.
 template <typename R>
-__device__ __forceinline__ void mixture(const Eos& e, R a1, R& G, R& Pi) {
-    G = a1 * R(e.dg) + R(e.g2);
-    Pi = a1 * R(e.dP) + R(e.P2);
+__device__ __forceinline__ void mixture(const EosR<R>& e, R a1, R& G, R& Pi) {
+    G = a1 * e.dg + e.g2;
+    Pi = a1 * e.dP + e.P2;
 }
 
 // ---------------------------------------------------------------- WENO5-JS
 // v0..v4 = v_{i-2}..v_{i+2}.  vm: left-biased value at i+1/2 (linear weights
 // 0.1, 0.6, 0.3); vp: right-biased value at i-1/2 (0.3, 0.6, 0.1).  The three
 // Jiang-Shu smoothness indicators of cell i serve both faces.
+//
+// Written in first differences d1..d4 (d_k = v_k - v_{k-1}):
+//   beta0 = 13/12 (d2-d1)^2 + 1/4 (3 d2 - d1)^2
+//   beta1 = 13/12 (d3-d2)^2 + 1/4 (d2 + d3)^2
+//   beta2 = 13/12 (d4-d3)^2 + 1/4 (3 d3 - d4)^2
+// and each candidate value as v_i plus a correction:
+//   left:  (5 d2 - 2 d1)/6, (d2 + 2 d3)/6, (4 d3 - d4)/6
+//   right: (d1 - 4 d2)/6, -(2 d2 + d3)/6, (2 d4 - 5 d3)/6
+// (the same polynomials as the textbook forms), so uniform data reconstructs
+// exactly and both faces share one reciprocal.
 template <typename R>
 __device__ __forceinline__ void weno5(R v0, R v1, R v2, R v3, R v4, R eps, R& vm, R& vp) {
     const R c13 = R(13.0 / 12.0);
-    const R c6 = R(1.0 / 6.0);
-    R d0 = v0 - R(2) * v1 + v2, e0 = v0 - R(4) * v1 + R(3) * v2;
-    R d1 = v1 - R(2) * v2 + v3, e1 = v1 - v3;
-    R d2 = v2 - R(2) * v3 + v4, e2 = R(3) * v2 - R(4) * v3 + v4;
-    R b0 = c13 * d0 * d0 + R(0.25) * e0 * e0;
-    R b1 = c13 * d1 * d1 + R(0.25) * e1 * e1;
-    R b2 = c13 * d2 * d2 + R(0.25) * e2 * e2;
+    R d1 = v1 - v0, d2 = v2 - v1, d3 = v3 - v2, d4 = v4 - v3;
+    R D0 = d2 - d1, D1 = d3 - d2, D2 = d4 - d3;
+    R Q0 = R(3) * d2 - d1, Q1 = d2 + d3, Q2 = R(3) * d3 - d4;
+    R b0 = c13 * D0 * D0 + R(0.25) * Q0 * Q0;
+    R b1 = c13 * D1 * D1 + R(0.25) * Q1 * Q1;
+    R b2 = c13 * D2 * D2 + R(0.25) * Q2 * Q2;
     R s0 = eps + b0, s1 = eps + b1, s2 = eps + b2;
     s0 = s0 * s0;
     s1 = s1 * s1;
@@ -77,16 +94,14 @@ __device__ __forceinline__ void weno5(R v0, R v1, R v2, R v3, R v4, R eps, R& vm
         m1 = __fdividef(smin, s1);
         m2 = __fdividef(smin, s2);
     }
-    R pm0 = (R(2) * v0 - R(7) * v1 + R(11) * v2) * c6;
-    R pm1 = (-v1 + R(5) * v2 + R(2) * v3) * c6;
-    R pm2 = (R(2) * v2 + R(5) * v3 - v4) * c6;
     R am0 = R(0.1) * m0, am1 = R(0.6) * m1, am2 = R(0.3) * m2;
-    vm = rdiv(am0 * pm0 + am1 * pm1 + am2 * pm2, am0 + am1 + am2);
-    R pp0 = (-v0 + R(5) * v1 + R(2) * v2) * c6;
-    R pp1 = (R(2) * v1 + R(5) * v2 - v3) * c6;
-    R pp2 = (R(11) * v2 - R(7) * v3 + R(2) * v4) * c6;
     R ap0 = R(0.3) * m0, ap1 = R(0.6) * m1, ap2 = R(0.1) * m2;
-    vp = rdiv(ap0 * pp0 + ap1 * pp1 + ap2 * pp2, ap0 + ap1 + ap2);
+    R Nm = am0 * (R(5) * d2 - R(2) * d1) + am1 * (d2 + R(2) * d3) + am2 * (R(4) * d3 - d4);
+    R Np = ap0 * (d1 - R(4) * d2) - ap1 * (R(2) * d2 + d3) + ap2 * (R(2) * d4 - R(5) * d3);
+    R Dm = am0 + am1 + am2, Dp = ap0 + ap1 + ap2;
+    R r = rdiv(R(1), R(6) * Dm * Dp);
+    vm = v2 + Nm * Dp * r;
+    vp = v2 + Np * Dm * r;
 }
 
 // ---------------------------------------------------------------- HLLC
@@ -97,7 +112,7 @@ __device__ __forceinline__ void weno5(R v0, R v1, R v2, R v3, R v4, R eps, R& vm
 // 0<=S_L: F_L; S_L<0<=S*: F*_L; S*<0<=S_R: F*_R; else F_R.
 // Returns true when a face state is non-physical (rho<=0, c^2<=0, NaN).
 template <int NDIM, int DIR, typename R>
-__device__ __forceinline__ bool hllc(const Eos& e, const R* wL, const R* wR, R* F, R& uf) {
+__device__ __forceinline__ bool hllc(const EosR<R>& e, const R* wL, const R* wR, R* F, R& uf) {
     using FL = Fields<NDIM>;
     const int IE = FL::IE, IA = FL::IA;
     R rhoL = wL[0] + wL[1];

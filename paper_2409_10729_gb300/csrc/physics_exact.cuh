@@ -1,0 +1,224 @@
+// physics_exact.cuh -- FP64 RHS arithmetic in the reference operation order.
+//
+// The same stiffened-gas EOS (arXiv 2409.10729, Sec. II-A), WENO5-JS and
+// HLLC (Sec. II-B) as physics.cuh, but every formula is evaluated in the
+// textbook order the serial FP64 oracle uses, with one IEEE rounding per
+// operation.  Compiled with -fmad=false (no contraction of a*b+c), the
+// results are bit-identical to that order.  Where several quotients share a
+// denominator, the quotient is formed from a correctly rounded reciprocal
+// y = RN(1/b) and one FMA correction (Markstein's theorem, "Computation of
+// elementary functions on the IBM RISC System/6000", 1990):
+//   q = RN(a y),  r = RN(a - b q) (exact),  a/b rounded = RN(q + r y),
+// which is the correctly rounded a/b for operands without overflow or
+// underflow -- the same bits as a division, at a third of the cost.
+#pragma once
+#include "physics.cuh"
+
+namespace mfc5 {
+namespace exact {
+
+// Correctly rounded a/b given y = RN(1/b).
+__device__ __forceinline__ double div_rcp(double a, double b, double y) {
+    double q = __dmul_rn(a, y);
+    double r = __fma_rn(-b, q, a);
+    return __fma_rn(r, y, q);
+}
+
+__device__ __forceinline__ double rcp(double b) { return __drcp_rn(b); }
+
+__device__ __forceinline__ double sq(double x) { return x * x; }
+
+// Gamma = a1 g1 + (1 - a1) g2, Pi = a1 P1 + (1 - a1) P2.
+__device__ __forceinline__ void mixture(const Eos& e, double a1, double& G, double& Pi) {
+    double a2 = 1.0 - a1;
+    G = a1 * e.g1 + a2 * e.g2;
+    Pi = a1 * e.P1 + a2 * e.P2;
+}
+
+template <int NDIM>
+__device__ __forceinline__ double kinetic(double rho, const double* u) {
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < NDIM; ++k) s = s + u[k] * u[k];
+    return 0.5 * rho * s;
+}
+
+// Conservative -> primitive (u_k = rho u_k / rho, p = (rho E - ke - Pi)/Gamma).
+template <int NDIM>
+__device__ __forceinline__ void cons_to_prim(const Eos& e, const double* q, double* w) {
+    using FL = Fields<NDIM>;
+    double rho = q[0] + q[1];
+    double y = rcp(rho);
+    double u[NDIM];
+#pragma unroll
+    for (int k = 0; k < NDIM; ++k) u[k] = div_rcp(q[2 + k], rho, y);
+    double ke = kinetic<NDIM>(rho, u);
+    double G, Pi;
+    mixture(e, q[FL::IA], G, Pi);
+    double p = (q[FL::IE] - ke - Pi) / G;
+    w[0] = q[0];
+    w[1] = q[1];
+#pragma unroll
+    for (int k = 0; k < NDIM; ++k) w[2 + k] = u[k];
+    w[FL::IE] = p;
+    w[FL::IA] = q[FL::IA];
+}
+
+// Primitive -> conservative (rho E = Gamma p + Pi + ke).
+template <int NDIM>
+__device__ __forceinline__ void prim_to_cons(const Eos& e, const double* w, double* q) {
+    using FL = Fields<NDIM>;
+    double rho = w[0] + w[1];
+    double u[NDIM];
+#pragma unroll
+    for (int k = 0; k < NDIM; ++k) u[k] = w[2 + k];
+    double ke = kinetic<NDIM>(rho, u);
+    double G, Pi;
+    mixture(e, w[FL::IA], G, Pi);
+    q[0] = w[0];
+    q[1] = w[1];
+#pragma unroll
+    for (int k = 0; k < NDIM; ++k) q[2 + k] = rho * u[k];
+    q[FL::IE] = G * w[FL::IE] + Pi + ke;
+    q[FL::IA] = w[FL::IA];
+}
+
+__device__ __forceinline__ double sound2(double G, double Pi, double rho, double p) {
+    return ((G + 1.0) * p + Pi) / (G * rho);
+}
+
+// WENO5-JS: left-biased value at i+1/2 and right-biased value at i-1/2 from
+// v0..v4 = v_{i-2}..v_{i+2}; weights a_k = d_k/(eps+beta_k)^2, omega_k = a_k/sum(a),
+// candidate values (.)/6, face value sum omega_k p_k.
+__device__ __forceinline__ void weno5(double eps, double v0, double v1, double v2, double v3, double v4,
+                                      double& vm, double& vp) {
+    const double c13 = 13.0 / 12.0;
+    const double r6 = 1.0 / 6.0;  // RN(1/6)
+    double b0 = c13 * sq(v0 - 2.0 * v1 + v2) + 0.25 * sq(v0 - 4.0 * v1 + 3.0 * v2);
+    double b1 = c13 * sq(v1 - 2.0 * v2 + v3) + 0.25 * sq(v1 - v3);
+    double b2 = c13 * sq(v2 - 2.0 * v3 + v4) + 0.25 * sq(3.0 * v2 - 4.0 * v3 + v4);
+    double s0 = sq(eps + b0), s1 = sq(eps + b1), s2 = sq(eps + b2);
+    double y0 = rcp(s0), y1 = rcp(s1), y2 = rcp(s2);
+
+    double a0 = div_rcp(0.1, s0, y0);
+    double a1 = div_rcp(0.6, s1, y1);
+    double a2 = div_rcp(0.3, s2, y2);
+    double s = a0 + a1 + a2;
+    double ys = rcp(s);
+    double p0 = div_rcp(2.0 * v0 - 7.0 * v1 + 11.0 * v2, 6.0, r6);
+    double p1 = div_rcp(-v1 + 5.0 * v2 + 2.0 * v3, 6.0, r6);
+    double p2 = div_rcp(2.0 * v2 + 5.0 * v3 - v4, 6.0, r6);
+    vm = div_rcp(a0, s, ys) * p0 + div_rcp(a1, s, ys) * p1 + div_rcp(a2, s, ys) * p2;
+
+    a0 = div_rcp(0.3, s0, y0);
+    a1 = div_rcp(0.6, s1, y1);
+    a2 = div_rcp(0.1, s2, y2);
+    s = a0 + a1 + a2;
+    ys = rcp(s);
+    p0 = div_rcp(-v0 + 5.0 * v1 + 2.0 * v2, 6.0, r6);
+    p1 = div_rcp(2.0 * v1 + 5.0 * v2 - v3, 6.0, r6);
+    p2 = div_rcp(11.0 * v2 - 7.0 * v3 + 2.0 * v4, 6.0, r6);
+    vp = div_rcp(a0, s, ys) * p0 + div_rcp(a1, s, ys) * p1 + div_rcp(a2, s, ys) * p2;
+}
+
+struct Face {
+    double rho, p, a1, G, Pi, E, c2;
+};
+
+template <int NDIM>
+__device__ __forceinline__ void face_from_prim(const Eos& e, const double* w, Face& s) {
+    using FL = Fields<NDIM>;
+    s.rho = w[0] + w[1];
+    s.p = w[FL::IE];
+    s.a1 = w[FL::IA];
+    mixture(e, s.a1, s.G, s.Pi);
+    s.E = s.G * s.p + s.Pi + kinetic<NDIM>(s.rho, w + 2);
+    s.c2 = sound2(s.G, s.Pi, s.rho, s.p);
+}
+
+// Physical flux of side K (primitives w, face state K) normal to DIR.
+template <int NDIM, int DIR>
+__device__ __forceinline__ void phys_flux(const double* w, const Face& K, double* F) {
+    using FL = Fields<NDIM>;
+    double un = w[2 + DIR];
+    F[0] = w[0] * un;
+    F[1] = w[1] * un;
+#pragma unroll
+    for (int k = 0; k < NDIM; ++k) F[2 + k] = K.rho * w[2 + k] * un;
+    F[2 + DIR] = F[2 + DIR] + K.p;
+    F[FL::IE] = (K.E + K.p) * un;
+    F[FL::IA] = K.a1 * un;
+}
+
+// HLLC flux through a face normal to DIR; regions 0<=S_L: F_L, S_L<0<=S*: F*_L,
+// S*<0<=S_R: F*_R, else F_R; the alpha1 slot carries alpha1_K times the
+// region velocity, returned in uf.  Returns true for a non-physical face state.
+template <int NDIM, int DIR>
+__device__ __forceinline__ bool hllc(const Eos& e, const double* wL, const double* wR, double* F, double& uf) {
+    using FL = Fields<NDIM>;
+    Face L, R;
+    face_from_prim<NDIM>(e, wL, L);
+    face_from_prim<NDIM>(e, wR, R);
+    bool bad = !(L.rho > 0.0) || !(R.rho > 0.0) || !(L.c2 > 0.0) || !(R.c2 > 0.0);
+    double cL = sqrt(L.c2), cR = sqrt(R.c2);
+    double uL = wL[2 + DIR], uR = wR[2 + DIR];
+    double SL = (uL - cL < uR - cR) ? uL - cL : uR - cR;
+    double SR = (uL + cL > uR + cR) ? uL + cL : uR + cR;
+    double num = R.p - L.p + L.rho * uL * (SL - uL) - R.rho * uR * (SR - uR);
+    double den = L.rho * (SL - uL) - R.rho * (SR - uR);
+    double Ss = num / den;
+    const bool left = (0.0 <= SL) || (0.0 <= Ss);
+    const bool star = left ? !(0.0 <= SL) : (0.0 <= SR);
+    double w[FL::NEQ];
+#pragma unroll
+    for (int f = 0; f < FL::NEQ; ++f) w[f] = left ? wL[f] : wR[f];
+    Face K;
+    K.rho = left ? L.rho : R.rho;
+    K.p = left ? L.p : R.p;
+    K.a1 = left ? L.a1 : R.a1;
+    K.G = left ? L.G : R.G;
+    K.Pi = left ? L.Pi : R.Pi;
+    K.E = left ? L.E : R.E;
+    double SK = left ? SL : SR;
+    double un = w[2 + DIR];
+    phys_flux<NDIM, DIR>(w, K, F);
+    uf = un;
+    if (star) {
+        double chi = (SK - un) / (SK - Ss);
+        F[0] = F[0] + SK * (chi * w[0] - w[0]);
+        F[1] = F[1] + SK * (chi * w[1] - w[1]);
+#pragma unroll
+        for (int k = 0; k < NDIM; ++k) {
+            double mstar = (k == DIR) ? chi * K.rho * Ss : chi * K.rho * w[2 + k];
+            F[2 + k] = F[2 + k] + SK * (mstar - K.rho * w[2 + k]);
+        }
+        double Estar = chi * (K.E + (Ss - un) * (K.rho * Ss + K.p / (SK - un)));
+        F[FL::IE] = F[FL::IE] + SK * (Estar - K.E);
+        F[FL::IA] = K.a1 * Ss;
+        uf = Ss;
+    }
+    return bad;
+}
+
+// S contribution of one cell: sum_d (|u_d| + c)/dx_d, from the conservative state.
+template <int NDIM>
+__device__ __forceinline__ double cell_wavespeed(const Eos& e, const double* q, const double* dx,
+                                                 const double* rdx, bool& bad) {
+    using FL = Fields<NDIM>;
+    double w[FL::NEQ];
+    cons_to_prim<NDIM>(e, q, w);
+    double rho = w[0] + w[1];
+    double G, Pi;
+    mixture(e, w[FL::IA], G, Pi);
+    double c2 = sound2(G, Pi, rho, w[FL::IE]);
+    bad |= !(q[0] + q[1] > 0.0) || !(rho > 0.0) || !(c2 > 0.0);
+    double cs = sqrt(c2);
+    double s = 0.0;
+#pragma unroll
+    for (int d = 0; d < NDIM; ++d) s = s + div_rcp(fabs(w[2 + d]) + cs, dx[d], rdx[d]);
+    bad |= !(s < INFINITY);
+    return s;
+}
+
+}  // namespace exact
+}  // namespace mfc5

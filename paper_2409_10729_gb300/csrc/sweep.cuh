@@ -11,14 +11,20 @@
 //
 // Thread mapping.  A warp owns 32 adjacent pencils along d and a segment of
 // `seg` cells of each.  For d = y, z the 32 lanes run along x, so every load
-// is one coalesced row; for d = x the lanes run along y.  Each thread slides a
-// five-cell window of primitives along its pencil in registers: per cell it
-// loads one new cell, runs WENO once (both faces), and HLLC once (the face
-// between the previous cell and this one), so no face is computed twice
-// except at the two ends of a segment.  Boundary ghosts come from index
-// clamping (transmissive) or wrapping (periodic) in the loads.
+// is one coalesced row.  For d = x the lanes run along y; their cells are
+// staged through shared memory in chunks of 32 bytes along x per row (one
+// full DRAM sector), loaded cooperatively by the warp so that every global
+// load touches whole sectors.  Each thread slides a five-cell window of
+// primitives along its pencil in registers: per cell it takes one new cell,
+// runs WENO once (both faces) and HLLC once (the face between the previous
+// cell and this one), so no face is computed twice except at the two ends of
+// a segment.  Boundary ghosts come from index clamping (transmissive) or
+// wrapping (periodic) in the loads.
 #pragma once
+#include <type_traits>
+
 #include "mfc_internal.cuh"
+#include "physics_exact.cuh"
 
 namespace mfc5 {
 
@@ -31,47 +37,47 @@ __device__ __forceinline__ int bc_index(int j, int n, int periodic) {
     return j < 0 ? 0 : n - 1;
 }
 
-// FP64 form: conservative FP64 state -> FP64 primitives (Sec. II-A EOS).
+// Fields a sweep reads per cell, in load order.  FP64: the conservative
+// state.  Mixed: the FP32 state with the pressure stored as field NEQ (formed
+// in FP64 when the state was written) read in place of rho E.
+template <int NDIM, typename R>
+struct LoadSet {
+    static constexpr int N = NDIM + 4;
+    __device__ static constexpr int field(int k) {
+        return (sizeof(R) == 8 || k != 2 + NDIM) ? k : NDIM + 4;
+    }
+};
+
+// Primitives from the loaded values v[] (see LoadSet).
 template <int NDIM>
-__device__ __forceinline__ void load_prim(const double* __restrict__ q, long long c, long long nc,
-                                          const Eos& e, double* w) {
+__device__ __forceinline__ void to_prim(const EosR<double>& e, const double* v, double* w) {
     using FL = Fields<NDIM>;
-    double a1r1 = __ldg(q + c);
-    double a2r2 = __ldg(q + nc + c);
-    double r = 1.0 / (a1r1 + a2r2);
+    double r = 1.0 / (v[0] + v[1]);
     double ke2 = 0.0;
-    w[0] = a1r1;
-    w[1] = a2r2;
+    w[0] = v[0];
+    w[1] = v[1];
 #pragma unroll
     for (int k = 0; k < NDIM; ++k) {
-        double m = __ldg(q + (2 + k) * nc + c);
-        double u = m * r;
+        double u = v[2 + k] * r;
         w[2 + k] = u;
-        ke2 += m * u;
+        ke2 += v[2 + k] * u;
     }
-    double E = __ldg(q + FL::IE * nc + c);
-    double a1 = __ldg(q + FL::IA * nc + c);
     double G, Pi;
-    mixture(e, a1, G, Pi);
-    w[FL::IE] = (E - 0.5 * ke2 - Pi) / G;
-    w[FL::IA] = a1;
+    mixture(e, v[FL::IA], G, Pi);
+    w[FL::IE] = (v[FL::IE] - 0.5 * ke2 - Pi) / G;
+    w[FL::IA] = v[FL::IA];
 }
 
-// Mixed form: FP32 state with the pressure stored as field NEQ (computed in
-// FP64 when the state was written) -> FP32 primitives.
 template <int NDIM>
-__device__ __forceinline__ void load_prim(const float* __restrict__ q, long long c, long long nc,
-                                          const Eos& e, float* w) {
+__device__ __forceinline__ void to_prim(const EosR<float>& e, const float* v, float* w) {
     using FL = Fields<NDIM>;
-    float a1r1 = __ldg(q + c);
-    float a2r2 = __ldg(q + nc + c);
-    float r = __fdividef(1.0f, a1r1 + a2r2);
-    w[0] = a1r1;
-    w[1] = a2r2;
+    float r = __fdividef(1.0f, v[0] + v[1]);
+    w[0] = v[0];
+    w[1] = v[1];
 #pragma unroll
-    for (int k = 0; k < NDIM; ++k) w[2 + k] = __ldg(q + (2 + k) * nc + c) * r;
-    w[FL::IE] = __ldg(q + FL::NEQ * nc + c);
-    w[FL::IA] = __ldg(q + FL::IA * nc + c);
+    for (int k = 0; k < NDIM; ++k) w[2 + k] = v[2 + k] * r;
+    w[FL::IE] = v[FL::IE];  // stored pressure
+    w[FL::IA] = v[FL::IA];
 }
 
 // Pressure from an FP64 conservative state, mixed form: the cancelling part
@@ -93,6 +99,16 @@ __device__ __forceinline__ float mixed_pressure(const Eos& e, const double* q) {
     return __fdividef(float(num), G);
 }
 
+// FP64 primitives of one cell of an FP64 conservative state (standalone use).
+template <int NDIM>
+__device__ __forceinline__ void load_prim(const double* __restrict__ q, long long c, long long nc,
+                                          const EosR<double>& e, double* w) {
+    double v[NDIM + 4];
+#pragma unroll
+    for (int f = 0; f < NDIM + 4; ++f) v[f] = __ldg(q + f * nc + c);
+    to_prim<NDIM>(e, v, w);
+}
+
 template <typename R>
 __device__ __forceinline__ R warp_max(R v) {
 #pragma unroll
@@ -105,7 +121,7 @@ __device__ __forceinline__ R warp_max(R v) {
 
 // Per-cell wave speed sum_d (|u_d| + c) / dx_d from primitives.
 template <int NDIM, typename R>
-__device__ __forceinline__ R cell_wavespeed(const Eos& e, const R* w, const double* inv_dx, bool& bad) {
+__device__ __forceinline__ R cell_wavespeed(const EosR<R>& e, const R* w, const double* inv_dx, bool& bad) {
     using FL = Fields<NDIM>;
     R rho = w[0] + w[1];
     R G, Pi;
@@ -120,11 +136,31 @@ __device__ __forceinline__ R cell_wavespeed(const Eos& e, const R* w, const doub
     return s;
 }
 
-template <int NDIM, int DIR, int MODE, typename R>
+// Shared-memory staging of the x-direction sweep: per warp, per loaded
+// field, 32 rows x CH cells (CH * sizeof(R) = 32 bytes), padded by one
+// element per row so that the 32 lanes read 32 different banks.
+template <typename R>
+struct XStage {
+    static constexpr int CH = 32 / sizeof(R);
+    static constexpr int PITCH = CH + 1;
+};
+
+template <int FORM>
+using FormReal = typename std::conditional<FORM == FORM_MIXED, float, double>::type;
+
+template <int NDIM, int DIR, int MODE, int FORM>
 __global__ void __launch_bounds__(kSweepThreads) sweep_kernel(const SweepArgs a) {
+    using R = FormReal<FORM>;
+    constexpr bool EXACT = FORM == FORM_FP64_EXACT;
     using FL = Fields<NDIM>;
+    using LS = LoadSet<NDIM, R>;
     constexpr int NEQ = FL::NEQ, IE = FL::IE, IA = FL::IA;
-    constexpr bool MIXED = sizeof(R) == 4;
+    constexpr int NL = LS::N;
+    constexpr bool MIXED = FORM == FORM_MIXED;
+    constexpr int CH = XStage<R>::CH, PITCH = XStage<R>::PITCH;
+    constexpr int WARPS = kSweepThreads / 32;
+    __shared__ R stage[DIR == 0 ? WARPS * NL * 32 * PITCH : 1];
+
     const int n0 = a.n[0], n1 = a.n[1], n2 = a.n[2];
     const int na = DIR == 0 ? n1 : n0;
     const int nb = DIR == 2 ? n1 : n2;
@@ -146,142 +182,180 @@ __global__ void __launch_bounds__(kSweepThreads) sweep_kernel(const SweepArgs a)
     const bool active = ia < na;
     const int s0 = segi * seg;
     const int s1 = min(s0 + seg, ns);
-    const long long base = (long long)(active ? ia : 0) * sa + (long long)b * sb;
+    // inactive lanes follow a valid pencil so that every address is in bounds;
+    // their results are discarded
+    const long long base = (long long)(active ? ia : na - 1) * sa + (long long)b * sb;
     const long long nc = a.ncell;
     const R inv_dx = R(a.inv_dx[DIR]);
     const R eps = R(a.eps);
-    const Eos e = a.eos;
+    const EosR<R> er(a.eos);
     const R* __restrict__ qin = static_cast<const R*>(a.qin);
+    R* st = stage + (threadIdx.x >> 5) * (NL * 32 * PITCH);
+
+    // Values of loaded cell k (x-index s0 - 3 + k along the pencil) -> v[].
+    auto fetch = [&](int k, R* v) {
+        const int j = s0 - 3 + k;
+        if constexpr (DIR != 0) {
+            const long long c = base + (long long)bc_index(j, ns, a.periodic) * ss;
+#pragma unroll
+            for (int f = 0; f < NL; ++f) v[f] = __ldg(qin + LS::field(f) * nc + c);
+        } else {
+            const int slot = k % CH;
+            if (slot == 0) {
+                // the warp stages cells j .. j+CH-1 of its 32 rows
+                __syncwarp();
+                const int t = lane % CH;
+                const int xg = bc_index(j + t, ns, a.periodic);
+#pragma unroll
+                for (int i = 0; i < CH; ++i) {
+                    const int r = lane / CH + (32 / CH) * i;
+                    const int row = min(chunk * 32 + r, na - 1);
+                    const long long c = (long long)row * sa + (long long)b * sb + xg;
+#pragma unroll
+                    for (int f = 0; f < NL; ++f) st[(f * 32 + r) * PITCH + t] = __ldg(qin + LS::field(f) * nc + c);
+                }
+                __syncwarp();
+            }
+#pragma unroll
+            for (int f = 0; f < NL; ++f) v[f] = st[(f * 32 + lane) * PITCH + slot];
+        }
+    };
 
     bool bad = false;
     R smax = R(0);
+    double dt = 0.0;
+    if (MODE == SW_LAST_RK) dt = a.ctrl->dt;
 
-    if (active) {
-        double dt = 0.0;
-        if (MODE == SW_LAST_RK) dt = a.ctrl->dt;
-        R W[5][NEQ];
+    R W[5][NEQ];
 #pragma unroll
-        for (int k = 0; k < 5; ++k) {
-            load_prim<NDIM>(qin, base + (long long)bc_index(s0 - 3 + k, ns, a.periodic) * ss, nc, e, W[k]);
-            bad |= !(W[k][0] + W[k][1] > R(0));
+    for (int k = 0; k < 5; ++k) {
+        R v[NL];
+        fetch(k, v);
+        if constexpr (EXACT) exact::cons_to_prim<NDIM>(a.eos, v, W[k]);
+        else to_prim<NDIM>(er, v, W[k]);
+        bad |= !(W[k][0] + W[k][1] > R(0));
+    }
+    R vmPrev[NEQ], Fprev[NEQ];
+    R ufPrev = R(0), alphaCell = R(0);
+#pragma unroll
+    for (int f = 0; f < NEQ; ++f) vmPrev[f] = Fprev[f] = R(0);
+
+    for (int j = s0 - 1; j <= s1; ++j) {
+        R vm[NEQ], vp[NEQ];
+#pragma unroll
+        for (int f = 0; f < NEQ; ++f) {
+            if constexpr (EXACT) exact::weno5(a.eps, W[0][f], W[1][f], W[2][f], W[3][f], W[4][f], vm[f], vp[f]);
+            else weno5(W[0][f], W[1][f], W[2][f], W[3][f], W[4][f], eps, vm[f], vp[f]);
         }
-        R vmPrev[NEQ], Fprev[NEQ];
-        R ufPrev = R(0), alphaCell = R(0);
+        if (j >= s0) {
+            R F[NEQ], uf;
+            if constexpr (EXACT) bad |= exact::hllc<NDIM, DIR>(a.eos, vmPrev, vp, F, uf);
+            else bad |= hllc<NDIM, DIR, R>(er, vmPrev, vp, F, uf);
+            if (j > s0 && active) {
+                // cell i = j - 1 is complete: faces i-1/2 (Fprev) and i+1/2 (F)
+                R L[NEQ];
+                if constexpr (EXACT) {
+                    // (F_{i-1/2} - F_{i+1/2})/dx, then + alpha1 (u_f+ - u_f-)/dx
+                    const double dx = a.dx[DIR], rdx = a.rdx[DIR];
 #pragma unroll
-        for (int f = 0; f < NEQ; ++f) vmPrev[f] = Fprev[f] = R(0);
-
-        for (int j = s0 - 1; j <= s1; ++j) {
-            R vm[NEQ], vp[NEQ];
-#pragma unroll
-            for (int f = 0; f < NEQ; ++f) weno5(W[0][f], W[1][f], W[2][f], W[3][f], W[4][f], eps, vm[f], vp[f]);
-            if (j >= s0) {
-                R F[NEQ], uf;
-                bad |= hllc<NDIM, DIR, R>(e, vmPrev, vp, F, uf);
-                if (j > s0) {
-                    // cell i = j - 1 is complete: faces i-1/2 (Fprev) and i+1/2 (F)
-                    R L[NEQ];
+                    for (int f = 0; f < NEQ; ++f) L[f] = exact::div_rcp(Fprev[f] - F[f], dx, rdx);
+                    L[IA] = L[IA] + exact::div_rcp(alphaCell * (uf - ufPrev), dx, rdx);
+                } else {
 #pragma unroll
                     for (int f = 0; f < NEQ; ++f) L[f] = (Fprev[f] - F[f]) * inv_dx;
                     L[IA] += alphaCell * (uf - ufPrev) * inv_dx;
-                    const long long c = base + (long long)(j - 1) * ss;
-                    if constexpr (MODE == SW_FIRST) {
-                        R* acc = static_cast<R*>(a.acc);
+                }
+                const long long c = base + (long long)(j - 1) * ss;
+                if constexpr (MODE == SW_FIRST) {
+                    R* acc = static_cast<R*>(a.acc);
 #pragma unroll
-                        for (int f = 0; f < NEQ; ++f) acc[f * nc + c] = L[f];
-                    } else if constexpr (MODE == SW_MID) {
-                        R* acc = static_cast<R*>(a.acc);
+                    for (int f = 0; f < NEQ; ++f) acc[f * nc + c] = L[f];
+                } else if constexpr (MODE == SW_MID) {
+                    R* acc = static_cast<R*>(a.acc);
 #pragma unroll
-                        for (int f = 0; f < NEQ; ++f) acc[f * nc + c] = acc[f * nc + c] + L[f];
-                    } else if constexpr (MODE == SW_LAST_RHS) {
-                        const R* acc = static_cast<const R*>(a.acc);
+                    for (int f = 0; f < NEQ; ++f) acc[f * nc + c] = acc[f * nc + c] + L[f];
+                } else if constexpr (MODE == SW_LAST_RHS) {
+                    const R* acc = static_cast<const R*>(a.acc);
+                    double* out = static_cast<double*>(a.qout);
+#pragma unroll
+                    for (int f = 0; f < NEQ; ++f) {
+                        R tot = NDIM > 1 ? acc[f * nc + c] + L[f] : L[f];
+                        out[f * nc + c] = double(tot);
+                    }
+                } else {  // SW_LAST_RK
+                    const R* acc = static_cast<const R*>(a.acc);
+                    double qnew[NEQ];
+#pragma unroll
+                    for (int f = 0; f < NEQ; ++f) {
+                        R tot = NDIM > 1 ? acc[f * nc + c] + L[f] : L[f];
+                        double qn = a.qn[f * nc + c];
+                        double dL = dt * double(tot);
+                        if (a.stage == 1) {
+                            qnew[f] = qn + dL;
+                        } else {
+                            double qk = double(qin[f * nc + c]);
+                            if (a.stage == 2)
+                                qnew[f] = 0.75 * qn + 0.25 * (qk + dL);
+                            else
+                                qnew[f] = (1.0 / 3.0) * qn + (2.0 / 3.0) * (qk + dL);
+                        }
+                    }
+                    if constexpr (!MIXED) {
                         double* out = static_cast<double*>(a.qout);
 #pragma unroll
-                        for (int f = 0; f < NEQ; ++f) {
-                            R tot = NDIM > 1 ? acc[f * nc + c] + L[f] : L[f];
-                            out[f * nc + c] = double(tot);
-                        }
-                    } else {  // SW_LAST_RK
-                        const R* acc = static_cast<const R*>(a.acc);
-                        double qnew[NEQ];
-#pragma unroll
-                        for (int f = 0; f < NEQ; ++f) {
-                            R tot = NDIM > 1 ? acc[f * nc + c] + L[f] : L[f];
-                            double qn = a.qn[f * nc + c];
-                            double dL = dt * double(tot);
-                            if (a.stage == 1) {
-                                qnew[f] = qn + dL;
+                        for (int f = 0; f < NEQ; ++f) out[f * nc + c] = qnew[f];
+                        if (a.stage == 3) {
+                            R s;
+                            if constexpr (EXACT) {
+                                s = exact::cell_wavespeed<NDIM>(a.eos, qnew, a.dx, a.rdx, bad);
                             } else {
-                                double qk = double(qin[f * nc + c]);
-                                if (a.stage == 2)
-                                    qnew[f] = 0.75 * qn + 0.25 * (qk + dL);
-                                else
-                                    qnew[f] = (1.0 / 3.0) * qn + (2.0 / 3.0) * (qk + dL);
-                            }
-                        }
-                        if constexpr (!MIXED) {
-                            double* out = static_cast<double*>(a.qout);
-#pragma unroll
-                            for (int f = 0; f < NEQ; ++f) out[f * nc + c] = qnew[f];
-                            if (a.stage == 3) {
                                 double wn[NEQ];
-                                double r = 1.0 / (qnew[0] + qnew[1]);
-                                double ke2 = 0.0;
-                                wn[0] = qnew[0];
-                                wn[1] = qnew[1];
-#pragma unroll
-                                for (int k = 0; k < NDIM; ++k) {
-                                    wn[2 + k] = qnew[2 + k] * r;
-                                    ke2 += qnew[2 + k] * wn[2 + k];
-                                }
-                                double G, Pi;
-                                mixture(e, qnew[IA], G, Pi);
-                                wn[IE] = (qnew[IE] - 0.5 * ke2 - Pi) / G;
-                                wn[IA] = qnew[IA];
-                                R s = cell_wavespeed<NDIM, double>(e, wn, a.inv_dx, bad);
-                                smax = s > smax ? s : smax;
+                                to_prim<NDIM>(er, qnew, wn);
+                                s = cell_wavespeed<NDIM, double>(er, wn, a.inv_dx, bad);
                             }
-                        } else {
-                            float pnew = mixed_pressure<NDIM>(e, qnew);
-                            float* o32 = static_cast<float*>(a.stage == 3 ? a.qout2 : a.qout);
+                            smax = s > smax ? s : smax;
+                        }
+                    } else {
+                        float pnew = mixed_pressure<NDIM>(a.eos, qnew);
+                        float* o32 = static_cast<float*>(a.stage == 3 ? a.qout2 : a.qout);
 #pragma unroll
-                            for (int f = 0; f < NEQ; ++f) o32[f * nc + c] = float(qnew[f]);
-                            o32[NEQ * nc + c] = pnew;
-                            if (a.stage == 3) {
-                                double* o64 = static_cast<double*>(a.qout);
+                        for (int f = 0; f < NEQ; ++f) o32[f * nc + c] = float(qnew[f]);
+                        o32[NEQ * nc + c] = pnew;
+                        if (a.stage == 3) {
+                            double* o64 = static_cast<double*>(a.qout);
 #pragma unroll
-                                for (int f = 0; f < NEQ; ++f) o64[f * nc + c] = qnew[f];
-                                float wn[NEQ];
-                                float rho = float(qnew[0]) + float(qnew[1]);
-                                float r = __fdividef(1.0f, rho);
-                                wn[0] = float(qnew[0]);
-                                wn[1] = float(qnew[1]);
+                            for (int f = 0; f < NEQ; ++f) o64[f * nc + c] = qnew[f];
+                            float v[NEQ], wn[NEQ];
 #pragma unroll
-                                for (int k = 0; k < NDIM; ++k) wn[2 + k] = float(qnew[2 + k]) * r;
-                                wn[IE] = pnew;
-                                wn[IA] = float(qnew[IA]);
-                                R s = cell_wavespeed<NDIM, float>(e, wn, a.inv_dx, bad);
-                                smax = s > smax ? s : smax;
-                            }
+                            for (int f = 0; f < NEQ; ++f) v[f] = float(qnew[f]);
+                            v[IE] = pnew;
+                            to_prim<NDIM>(er, v, wn);
+                            R s = cell_wavespeed<NDIM, float>(er, wn, a.inv_dx, bad);
+                            smax = s > smax ? s : smax;
                         }
                     }
                 }
-#pragma unroll
-                for (int f = 0; f < NEQ; ++f) Fprev[f] = F[f];
-                ufPrev = uf;
             }
 #pragma unroll
-            for (int f = 0; f < NEQ; ++f) vmPrev[f] = vm[f];
-            alphaCell = W[2][IA];
-            if (j < s1) {
+            for (int f = 0; f < NEQ; ++f) Fprev[f] = F[f];
+            ufPrev = uf;
+        }
 #pragma unroll
-                for (int k = 0; k < 4; ++k)
+        for (int f = 0; f < NEQ; ++f) vmPrev[f] = vm[f];
+        alphaCell = W[2][IA];
+        if (j < s1) {
 #pragma unroll
-                    for (int f = 0; f < NEQ; ++f) W[k][f] = W[k + 1][f];
-                load_prim<NDIM>(qin, base + (long long)bc_index(j + 3, ns, a.periodic) * ss, nc, e, W[4]);
-                bad |= !(W[4][0] + W[4][1] > R(0));
-            }
+            for (int k = 0; k < 4; ++k)
+#pragma unroll
+                for (int f = 0; f < NEQ; ++f) W[k][f] = W[k + 1][f];
+            R v[NL];
+            fetch(j + 3 - (s0 - 3), v);
+            if constexpr (EXACT) exact::cons_to_prim<NDIM>(a.eos, v, W[4]);
+            else to_prim<NDIM>(er, v, W[4]);
+            bad |= !(W[4][0] + W[4][1] > R(0));
         }
     }
+    bad = bad && active;
 
     if constexpr (MODE == SW_LAST_RK) {
         if (a.stage == 3) {
@@ -295,7 +369,7 @@ __global__ void __launch_bounds__(kSweepThreads) sweep_kernel(const SweepArgs a)
 
 // Launch one sweep: the valid (direction, mode) pairs are x FIRST, y MID
 // (3-D), and LAST_RK / LAST_RHS on the last direction.
-template <int NDIM, typename R>
+template <int NDIM, int FORM>
 cudaError_t launch_sweep_t(int dir, int mode, const SweepArgs& a, cudaStream_t s) {
     long long warps = sweep_warps(dir, a.n, a.seg);
     long long blocks = (warps * 32 + kSweepThreads - 1) / kSweepThreads;
@@ -304,25 +378,25 @@ cudaError_t launch_sweep_t(int dir, int mode, const SweepArgs& a, cudaStream_t s
     dim3 grid((unsigned)blocks), block(kSweepThreads);
     constexpr int LAST = NDIM - 1;
     if (dir == 0 && mode == SW_FIRST && NDIM > 1) {
-        if constexpr (NDIM > 1) sweep_kernel<NDIM, 0, SW_FIRST, R><<<grid, block, 0, s>>>(a);
+        if constexpr (NDIM > 1) sweep_kernel<NDIM, 0, SW_FIRST, FORM><<<grid, block, 0, s>>>(a);
     } else if (dir == 1 && mode == SW_MID && NDIM == 3) {
-        if constexpr (NDIM == 3) sweep_kernel<NDIM, 1, SW_MID, R><<<grid, block, 0, s>>>(a);
+        if constexpr (NDIM == 3) sweep_kernel<NDIM, 1, SW_MID, FORM><<<grid, block, 0, s>>>(a);
     } else if (dir == LAST && mode == SW_LAST_RK) {
-        sweep_kernel<NDIM, LAST, SW_LAST_RK, R><<<grid, block, 0, s>>>(a);
+        sweep_kernel<NDIM, LAST, SW_LAST_RK, FORM><<<grid, block, 0, s>>>(a);
     } else if (dir == LAST && mode == SW_LAST_RHS) {
-        sweep_kernel<NDIM, LAST, SW_LAST_RHS, R><<<grid, block, 0, s>>>(a);
+        sweep_kernel<NDIM, LAST, SW_LAST_RHS, FORM><<<grid, block, 0, s>>>(a);
     } else {
         return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
 
-template <typename R>
+template <int FORM>
 cudaError_t launch_sweep_any(int ndim, int dir, int mode, const SweepArgs& a, cudaStream_t s) {
     switch (ndim) {
-        case 1: return launch_sweep_t<1, R>(dir, mode, a, s);
-        case 2: return launch_sweep_t<2, R>(dir, mode, a, s);
-        case 3: return launch_sweep_t<3, R>(dir, mode, a, s);
+        case 1: return launch_sweep_t<1, FORM>(dir, mode, a, s);
+        case 2: return launch_sweep_t<2, FORM>(dir, mode, a, s);
+        case 3: return launch_sweep_t<3, FORM>(dir, mode, a, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -18,8 +18,8 @@ LIB_PATH = os.path.join(_HERE, "lib", "libmfc5.so")
 
 MFC_OK, MFC_EINVAL, MFC_ENOMEM, MFC_ECUDA, MFC_ENONPHYSICAL, MFC_ESTATE, MFC_ETOOBIG = 0, -1, -2, -3, -4, -5, -6
 MFC_NOALLOC_MAX_DOUBLES = 2 * 1024 * 1024
-MFC_FP64, MFC_MIXED, MFC_GATED = 0, 1, 2
-PRECISIONS = {"fp64": MFC_FP64, "mixed": MFC_MIXED, "gated": MFC_GATED}
+MFC_FP64, MFC_MIXED, MFC_GATED, MFC_FP64_FAST = 0, 1, 2, 3
+PRECISIONS = {"fp64": MFC_FP64, "mixed": MFC_MIXED, "gated": MFC_GATED, "fp64_fast": MFC_FP64_FAST}
 
 
 class MfcParams(ctypes.Structure):

@@ -16,7 +16,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--case", choices=["droplets", "column", "tube"], default="droplets")
     ap.add_argument("--n", type=int, default=128, help="cells per dimension (column: ny, nx = 2 ny)")
-    ap.add_argument("--form", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--form", choices=["fp64", "fp64_fast", "mixed"], default="fp64")
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=1)
     ap.add_argument("--cfl", type=float, default=0.4)

@@ -3,9 +3,13 @@ results written by tests/golden/make_golden.py (which calls only the oracle).
 
 The 2-D shock / water-column case at 1024x512 for 500 steps and the 3-D
 shock / droplet case at 256^3 for 100 steps (CFL 0.4) are run on the GPU in
-the benchmark's launch configuration; the time advanced, per-field norms over
-all cells and the full state at ~1000 sampled cells must agree with the oracle
-to 1e-12 relative (momentum rows relative to the largest momentum component).
+the benchmark's launch configuration.  The FP64 form (reference operation
+order) must reproduce the time advanced, the per-field sums over all cells
+and the state at ~1000 sampled cells bit for bit.  The reorganised FP64 form
+is checked against a bound set by the flows themselves: re-running the
+oracle with FMA contraction (a change of rounding only) moves the 2-D
+momentum by 6.6e-12 relative after 500 steps, so it is held to 5e-11
+(momentum rows relative to the largest momentum component) and 1e-12 in t.
 """
 import hashlib
 import json
@@ -35,8 +39,9 @@ def built():
     torch.cuda.set_device(0)
 
 
+@pytest.mark.parametrize("form", ["fp64", "fp64_fast"])
 @pytest.mark.parametrize("name", sorted(CASES))
-def test_full_size_run_matches_stored_oracle(name):
+def test_full_size_run_matches_stored_oracle(name, form):
     from paper_2409_10729_gb300 import mfc
     path = os.path.join(HERE, "golden", f"{name}.json")
     if not os.path.exists(path):
@@ -46,7 +51,7 @@ def test_full_size_run_matches_stored_oracle(name):
     p, w = CASES[name]()
     assert hashlib.sha256(np.ascontiguousarray(w).tobytes()).hexdigest() == g["ic_sha256"], \
         "initial state differs from the one the stored oracle result was made from"
-    s = mfc.Solver(p, "fp64")
+    s = mfc.Solver(p, form)
     s.set_state_prim(w)
     t = s.step_rk3(g["cfl"], g["steps"])
     q = s.get_state()
@@ -54,14 +59,21 @@ def test_full_size_run_matches_stored_oracle(name):
     ndim = ne - 4
     qf = q.reshape(ne, -1)
     t_ref = float(g["t_final"])
-    assert abs(t - t_ref) <= TOL * t_ref
-    scale = np.array([float(v) for v in g["field_max_abs"]])
-    scale[2:2 + ndim] = scale[2:2 + ndim].max()
     ref = np.array([[float(v) for v in row] for row in g["values"]]).T
-    err = np.abs(qf[:, g["cells"]] - ref).max(1) / scale
-    assert err.max() <= TOL, f"sampled-cell error per field {err}"
     l1 = np.array([float(v) for v in g["field_l1"]])
-    assert np.all(np.abs(np.abs(qf).sum(1) - l1) <= TOL * l1)
     sums = np.array([float(v) for v in g["field_sum"]])
-    assert np.all(np.abs(qf.sum(1) - sums) <= TOL * l1)
+    if form == "fp64":
+        assert t == t_ref
+        assert np.array_equal(qf[:, g["cells"]], ref)
+        assert np.array_equal(np.abs(qf).max(1), np.array([float(v) for v in g["field_max_abs"]]))
+        # numpy's summation order may differ between machines: sums to round-off
+        assert np.all(np.abs(np.abs(qf).sum(1) - l1) <= 1e-14 * l1)
+        assert np.all(np.abs(qf.sum(1) - sums) <= 1e-14 * l1)
+    else:
+        assert abs(t - t_ref) <= TOL * t_ref
+        scale = np.array([float(v) for v in g["field_max_abs"]])
+        scale[2:2 + ndim] = scale[2:2 + ndim].max()
+        err = np.abs(qf[:, g["cells"]] - ref).max(1) / scale
+        assert err.max() <= 5e-11, f"sampled-cell error per field {err}"
+        assert np.all(np.abs(np.abs(qf).sum(1) - l1) <= 5e-11 * l1)
     s.close()
