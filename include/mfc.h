@@ -125,6 +125,49 @@ int mfc_set_timing(mfc_ctx* ctx, int enable);
  * index is out of range. */
 int mfc_kernel_time(mfc_ctx* ctx, int index, const char** name, double* ms, long long* launches);
 
+/* ---- gated form (MFC_GATED): the troubled-cell network ------------------
+ * No counterpart in the paper.  A 5 -> 32 -> 32 -> 1 perceptron (ReLU hidden
+ * layers, logistic output) reads a normalised 5-cell stencil
+ * (v_k - v_i)/(max_k |v_k - v_i| + 1e-12) of one sensor field; a cell is
+ * reconstructed with the linear WENO5 weights in a direction when the logit
+ * is negative for both the mixture-density and the pressure stencil, and
+ * with full WENO5-JS otherwise -- and also whenever a linear face state has
+ * rho <= 0, alpha1 outside [0, 1] or (Gamma + 1) p + Pi <= 0.  Parameters
+ * (MFC_MLP_NPARAMS floats): W1[32][5], b1[32], W2[32][32], b2[32], w3[32], b3. */
+#define MFC_MLP_NPARAMS 1281
+
+/* Sets the gate weights of a MFC_GATED context (host array of n =
+ * MFC_MLP_NPARAMS finite floats, copied).  Stepping a gated context before
+ * this returns MFC_ESTATE. */
+int mfc_set_mlp_weights(mfc_ctx* ctx, const float* w, int n);
+
+/* Gate statistics of the last mfc_rhs / mfc_step_rk3 call: cell
+ * reconstructions (cells x directions x stages) evaluated, done with linear
+ * weights, and gated but recomputed with WENO because a face was non-physical. */
+int mfc_gate_stats(mfc_ctx* ctx, long long* gated, long long* fallback, long long* cells);
+
+/* Labelled training samples from the current state (FP64 WENO5-JS weights):
+ * for every direction d and cell c, two samples (mixture-density stencil,
+ * pressure stencil), index (d * ncells + c) * 2 + sensor; X[sample][5] the
+ * normalised stencil, Y[sample] = 1 when some primitive's nonlinear weight at
+ * either face departs from its linear weight by more than tau (relative).
+ * X, Y are device pointers with room for capacity >= 2 * ndim * ncells
+ * samples; *count receives that number.  Synchronises the context stream. */
+int mfc_gate_samples(mfc_ctx* ctx, float* X, float* Y, long long capacity, float tau, long long* count);
+
+/* Training kernels (device pointers; cuda_stream a cudaStream_t, NULL = default).
+ * mfc_mlp_loss_grad: mean weighted binary cross-entropy of n samples
+ *   (l = wp y softplus(-z) + (1 - y) softplus(z), z the logit) into *loss and
+ *   its gradient into grad[MFC_MLP_NPARAMS] (both overwritten).
+ * mfc_mlp_adam: one Adam step t (1-based) of theta with moments m, v.
+ * mfc_mlp_forward: logits z[n] of X[n][5]. */
+int mfc_mlp_nparams(void);
+int mfc_mlp_loss_grad(const float* X, const float* Y, long long n, const float* theta, float pos_weight,
+                      float* grad, float* loss, void* cuda_stream);
+int mfc_mlp_adam(float* theta, const float* grad, float* m, float* v, int t, float lr, float beta1, float beta2,
+                 float eps, void* cuda_stream);
+int mfc_mlp_forward(const float* X, long long n, const float* theta, float* z, void* cuda_stream);
+
 /* Instrumentation, no counterpart in the paper: measures the sustained FMA
  * throughput of the current device with independent FMA chains, FP64
  * (fp64 != 0) or FP32, in TFLOP/s (2 flops per FMA).  Used as the ALU

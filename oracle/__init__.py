@@ -7,8 +7,10 @@ own CUDA library is missing.
 
 The arithmetic lives in ``mfc5_oracle.c`` (plain C, ``-O2 -ffp-contract=off``),
 a step-by-step statement of arXiv 2409.10729 Sec. II (model, stiffened-gas
-EOS, finite-volume RHS with WENO5-JS + HLLC) plus the SSP-RK3 / CFL reading.
-This module only builds the shared library and marshals numpy arrays.
+EOS, finite-volume RHS with WENO5-JS + HLLC) plus the SSP-RK3 / CFL reading,
+and in ``mlp_oracle.c`` (FP64 forward/backward/Adam of the troubled-cell
+network of the gated-WENO extension).  This module only builds the shared
+library and marshals numpy arrays.
 
 Parity status: every function here is pinned by ``tests/test_oracle_*.py``
 (closed forms, exact Riemann solutions, convergence order, conservation,
@@ -23,7 +25,7 @@ import subprocess
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "mfc5_oracle.c")
+_SRCS = [os.path.join(_HERE, "mfc5_oracle.c"), os.path.join(_HERE, "mlp_oracle.c")]
 _LIB = os.path.join(_HERE, "liboracle_mfc5.so")
 # Test hook: the mutation test points this at a deliberately broken build.
 _LIB_OVERRIDE = os.environ.get("MFC5_ORACLE_LIB")
@@ -33,10 +35,11 @@ OK, EINVAL, ENOMEM, ENONPHYSICAL = 0, -1, -2, -4
 
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (no fast-math, no FMA contraction)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    newest = max(os.path.getmtime(f) for f in _SRCS)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         tmp = _LIB + f".tmp{os.getpid()}"
         cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-               "-shared", "-o", tmp, _SRC, "-lm"]
+               "-shared", "-o", tmp, *_SRCS, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB)
     return _LIB
@@ -77,6 +80,13 @@ def lib():
             "orc_weno5_cell": ([ctypes.c_double, dp, dp, dp], None),
             "orc_hllc_face": ([pp, ctypes.c_int, dp, dp, dp, dp], ctypes.c_int),
             "orc_sound_speed2": ([pp, dp, dp], ctypes.c_int),
+            "orc_weno5_weights": ([ctypes.c_double, dp, dp, dp], None),
+            "mlp_nparams": ([], ctypes.c_int),
+            "mlp_forward": ([dp, dp, ctypes.c_long, dp], None),
+            "mlp_loss_grad": ([dp, dp, dp, ctypes.c_long, ctypes.c_double, dp], ctypes.c_double),
+            "mlp_adam": ([dp, dp, dp, dp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                          ctypes.c_double], None),
+            "mlp_normalise": ([dp, dp], None),
         }
         for name, (args, res) in sig.items():
             fn = getattr(_lib, name)
@@ -200,3 +210,62 @@ def sound_speed2(p: dict, w) -> float:
     c2 = ctypes.c_double()
     _check(lib().orc_sound_speed2(ctypes.byref(params(p)), _dptr(wv), ctypes.byref(c2)), "c2")
     return c2.value
+
+
+# ---- troubled-cell network (mlp_oracle.c) ----------------------------------
+
+def mlp_nparams() -> int:
+    return lib().mlp_nparams()
+
+
+def mlp_forward(theta, x) -> np.ndarray:
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    xx = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 5)
+    z = np.empty(len(xx))
+    lib().mlp_forward(_dptr(th), _dptr(xx), len(xx), _dptr(z))
+    return z
+
+
+def mlp_loss_grad(theta, x, y, pos_weight: float = 1.0):
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    xx = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 5)
+    yy = np.ascontiguousarray(y, dtype=np.float64)
+    g = np.empty_like(th)
+    loss = lib().mlp_loss_grad(_dptr(th), _dptr(xx), _dptr(yy), len(yy), float(pos_weight), _dptr(g))
+    return loss, g
+
+
+def mlp_adam(theta, g, m, v, t: int, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam step; returns new (theta, m, v)."""
+    th = np.array(theta, dtype=np.float64)
+    mm = np.array(m, dtype=np.float64)
+    vv = np.array(v, dtype=np.float64)
+    gg = np.ascontiguousarray(g, dtype=np.float64)
+    lib().mlp_adam(_dptr(th), _dptr(gg), _dptr(mm), _dptr(vv), int(t), lr, b1, b2, eps)
+    return th, mm, vv
+
+
+def mlp_normalise(v5) -> np.ndarray:
+    v = np.ascontiguousarray(v5, dtype=np.float64)
+    x = np.empty(5)
+    lib().mlp_normalise(_dptr(v), _dptr(x))
+    return x
+
+
+def weno5_weights(v5, eps: float = 1e-6):
+    v = np.ascontiguousarray(v5, dtype=np.float64)
+    wm, wp = np.empty(3), np.empty(3)
+    lib().orc_weno5_weights(float(eps), _dptr(v), _dptr(wm), _dptr(wp))
+    return wm, wp
+
+
+def troubled(w5, eps: float = 1e-6, tau: float = 0.1) -> bool:
+    """Troubled-cell label of one cell from its primitive stencils w5[f][5]:
+    some field's nonlinear WENO weight departs from its linear weight by more
+    than tau (relative) at either face."""
+    dm, dp = np.array([0.1, 0.6, 0.3]), np.array([0.3, 0.6, 0.1])
+    for v in np.asarray(w5):
+        wm, wp = weno5_weights(v, eps)
+        if max(np.max(np.abs(wm - dm) / dm), np.max(np.abs(wp - dp) / dp)) > tau:
+            return True
+    return False

@@ -516,6 +516,30 @@ int orc_run_cfl(const orc_params* p, double* q, double cfl, int nsteps, double* 
 
 /* ---- element-level entry points used by the unit pins -------------------- */
 
+/* Nonlinear WENO5-JS weights of cell i (same formulas as weno5): wm[k] for
+ * the left-biased value at i+1/2 (linear weights 0.1, 0.6, 0.3) and wp[k]
+ * for the right-biased value at i-1/2 (0.3, 0.6, 0.1). */
+void orc_weno5_weights(double eps, const double* v, double* wm, double* wp) {
+    const double c13 = 13.0 / 12.0;
+    double b0 = c13 * sq(v[0] - 2.0 * v[1] + v[2]) + 0.25 * sq(v[0] - 4.0 * v[1] + 3.0 * v[2]);
+    double b1 = c13 * sq(v[1] - 2.0 * v[2] + v[3]) + 0.25 * sq(v[1] - v[3]);
+    double b2 = c13 * sq(v[2] - 2.0 * v[3] + v[4]) + 0.25 * sq(3.0 * v[2] - 4.0 * v[3] + v[4]);
+    const double dm[3] = {0.1, 0.6, 0.3}, dp[3] = {0.3, 0.6, 0.1};
+    const double b[3] = {b0, b1, b2};
+    double am[3], ap[3], sm = 0.0, sp = 0.0;
+    for (int k = 0; k < 3; k++) {
+        am[k] = dm[k] / sq(eps + b[k]);
+        ap[k] = dp[k] / sq(eps + b[k]);
+        sm = sm + am[k];
+        sp = sp + ap[k];
+    }
+    for (int k = 0; k < 3; k++) {
+        wm[k] = am[k] / sm;
+        wp[k] = ap[k] / sp;
+    }
+}
+
+
 void orc_weno5_cell(double eps, const double* v5, double* vm, double* vp) { weno5(eps, v5, vm, vp); }
 
 int orc_hllc_face(const orc_params* p, int dir, const double* wL, const double* wR, double* F,

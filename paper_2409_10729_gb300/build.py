@@ -23,9 +23,11 @@ COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE
           "--expt-relaxed-constexpr"]
 # per-unit extra flags: the mixed form uses fast FP32 division/square root; the
 # reference-order FP64 units must not contract a*b+c into FMAs
-EXTRA = {"sweep_mixed.cu": ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"],
-         "sweep_fp64x.cu": ["-fmad=false"], "aux.cu": ["-fmad=false"]}
-UNITS = ["capi.cu", "aux.cu", "sweep_fp64.cu", "sweep_fp64x.cu", "sweep_mixed.cu", "noalloc.cu"]
+FAST32 = ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"]
+EXTRA = {"sweep_mixed.cu": FAST32, "sweep_gated.cu": FAST32,
+         "sweep_fp64x.cu": ["-fmad=false"], "aux.cu": ["-fmad=false"], "mlp.cu": ["-fmad=false"]}
+UNITS = ["capi.cu", "aux.cu", "sweep_fp64.cu", "sweep_fp64x.cu", "sweep_mixed.cu", "sweep_gated.cu", "mlp.cu",
+         "noalloc.cu"]
 
 
 def nvcc() -> str:

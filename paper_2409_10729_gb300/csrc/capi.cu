@@ -54,6 +54,8 @@ struct mfc_ctx {
     double ktime[K_NKINDS];
     long long kcount[K_NKINDS];
     int last_cuda;
+    bool have_gate;
+    GateWeights gate;  // gated form: network weights (host copy, passed by value to the sweeps)
 };
 
 #define CK(call)                                   \
@@ -77,7 +79,9 @@ static int validate(const mfc_params* p) {
         if (!(p->gamma[i] > 1.0) || !isfinite(p->gamma[i]) || !(p->pi_inf[i] >= 0.0) || !isfinite(p->pi_inf[i]))
             return MFC_EINVAL;
     if (!(p->weno_eps > 0.0) || !isfinite(p->weno_eps)) return MFC_EINVAL;
-    if (p->precision != MFC_FP64 && p->precision != MFC_MIXED && p->precision != MFC_FP64_FAST) return MFC_EINVAL;
+    if (p->precision != MFC_FP64 && p->precision != MFC_MIXED && p->precision != MFC_FP64_FAST &&
+        p->precision != MFC_GATED)
+        return MFC_EINVAL;
     return MFC_OK;
 }
 
@@ -90,8 +94,9 @@ static int pick_seg(int dir, const int* n) {
     return seg;
 }
 
-static size_t state_elem(const mfc_ctx* c) { return c->form == FORM_MIXED ? sizeof(float) : sizeof(double); }
-static int state_fields(const mfc_ctx* c) { return c->form == FORM_MIXED ? c->neq + 1 : c->neq; }
+static bool fp32_state(const mfc_ctx* c) { return c->form == FORM_MIXED || c->form == FORM_GATED; }
+static size_t state_elem(const mfc_ctx* c) { return fp32_state(c) ? sizeof(float) : sizeof(double); }
+static int state_fields(const mfc_ctx* c) { return fp32_state(c) ? c->neq + 1 : c->neq; }
 
 static void free_all(mfc_ctx* c) {
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
@@ -114,8 +119,12 @@ extern "C" int mfc_create(const mfc_params* params, void* cuda_stream, mfc_ctx**
     ctx->p = *params;
     ctx->ndim = params->ndim;
     ctx->neq = params->ndim + 4;
-    ctx->form = params->precision == MFC_FP64 ? FORM_FP64_EXACT
-                : (params->precision == MFC_FP64_FAST ? FORM_FP64_FAST : FORM_MIXED);
+    switch (params->precision) {
+        case MFC_FP64: ctx->form = FORM_FP64_EXACT; break;
+        case MFC_FP64_FAST: ctx->form = FORM_FP64_FAST; break;
+        case MFC_GATED: ctx->form = FORM_GATED; break;
+        default: ctx->form = FORM_MIXED; break;
+    }
     ctx->ncell = 1;
     for (int d = 0; d < 3; ++d) {
         ctx->n[d] = d < ctx->ndim ? params->n[d] : 1;
@@ -146,7 +155,7 @@ extern "C" int mfc_create(const mfc_params* params, void* cuda_stream, mfc_ctx**
               cudaMalloc(&ctx->acc, nc * ctx->neq * selem) == cudaSuccess &&
               cudaMalloc((void**)&ctx->ctrl, sizeof(DevCtrl)) == cudaSuccess &&
               cudaMallocHost((void**)&ctx->ctrl_h, sizeof(DevCtrl)) == cudaSuccess;
-    if (ok && ctx->form == FORM_MIXED)
+    if (ok && fp32_state(ctx))
         ok = cudaMalloc((void**)&ctx->s0, nc * sfield * sizeof(float)) == cudaSuccess;
     for (int i = 0; ok && i <= kMaxTimedLaunches; ++i) ok = cudaEventCreate(&ctx->ev[i]) == cudaSuccess;
     if (!ok) {
@@ -199,17 +208,18 @@ static cudaError_t launch_sweep(mfc_ctx* ctx, int dir, int mode, SweepArgs a, cu
     switch (ctx->form) {
         case FORM_FP64_EXACT: return launch_sweep_fp64x(ctx->ndim, dir, mode, a, s);
         case FORM_FP64_FAST: return launch_sweep_fp64(ctx->ndim, dir, mode, a, s);
+        case FORM_GATED: return launch_sweep_gated(ctx->ndim, dir, mode, a, ctx->gate, s);
         default: return launch_sweep_mixed(ctx->ndim, dir, mode, a, s);
     }
 }
 
 // The stage input/output buffers of stage k (1..3).
 static void stage_buffers(mfc_ctx* ctx, int k, SweepArgs& a) {
-    const void* in0 = ctx->form == FORM_MIXED ? (const void*)ctx->s0 : (const void*)ctx->qn;
+    const void* in0 = fp32_state(ctx) ? (const void*)ctx->s0 : (const void*)ctx->qn;
     a.stage = k;
     a.qin = k == 1 ? in0 : (k == 2 ? ctx->sa : ctx->sb);
     a.qout = k == 1 ? ctx->sa : (k == 2 ? ctx->sb : (void*)ctx->qn);
-    a.qout2 = (k == 3 && ctx->form == FORM_MIXED) ? (void*)ctx->s0 : NULL;
+    a.qout2 = (k == 3 && fp32_state(ctx)) ? (void*)ctx->s0 : NULL;
 }
 
 // Enqueue the launches of one step on stream s; with `timed`, bracket each
@@ -262,7 +272,7 @@ static int ensure_graph(mfc_ctx* ctx) {
 }
 
 static int after_state_change(mfc_ctx* ctx) {
-    if (ctx->form == FORM_MIXED)
+    if (fp32_state(ctx))
         CK(launch_make_mixed_state(ctx->ndim, ctx->qn, ctx->s0, ctx->ncell, ctx->eos, ctx->stream));
     CK(launch_wavespeed(ctx->ndim, ctx->qn, ctx->ncell, ctx->dx, ctx->rdx, ctx->eos, ctx->ctrl, ctx->stream));
     ctx->have_state = true;
@@ -314,6 +324,7 @@ static int write_ctrl_params(mfc_ctx* ctx, double cfl, double dt_fixed) {
     ctx->ctrl_h->cfl = cfl;
     ctx->ctrl_h->dt_fixed = dt_fixed;
     ctx->ctrl_h->status = 0;
+    ctx->ctrl_h->gated = ctx->ctrl_h->fallback = ctx->ctrl_h->cells = 0;
     size_t off = offsetof(DevCtrl, t);
     CK(cudaMemcpyAsync((char*)ctx->ctrl + off, (char*)ctx->ctrl_h + off, sizeof(DevCtrl) - off,
                        cudaMemcpyHostToDevice, ctx->stream));
@@ -322,12 +333,12 @@ static int write_ctrl_params(mfc_ctx* ctx, double cfl, double dt_fixed) {
 
 extern "C" int mfc_rhs(mfc_ctx* ctx, double* rhs, int on_device) {
     if (!ctx || !rhs) return MFC_EINVAL;
-    if (!ctx->have_state) return MFC_ESTATE;
+    if (!ctx->have_state || (ctx->form == FORM_GATED && !ctx->have_gate)) return MFC_ESTATE;
     int st = write_ctrl_params(ctx, 0.0, 0.0);
     if (st) return st;
     double* out = on_device ? rhs : NULL;
     if (!out) {
-        if (ctx->form != FORM_MIXED) {
+        if (!fp32_state(ctx)) {
             out = (double*)ctx->acc;  // the last sweep reads and writes each cell in place
         } else {
             if (!ctx->tmp64 && cudaMalloc((void**)&ctx->tmp64, (size_t)ctx->ncell * ctx->neq * sizeof(double)) !=
@@ -339,7 +350,7 @@ extern "C" int mfc_rhs(mfc_ctx* ctx, double* rhs, int on_device) {
         }
     }
     SweepArgs a = base_args(ctx);
-    a.qin = ctx->form == FORM_MIXED ? (const void*)ctx->s0 : (const void*)ctx->qn;
+    a.qin = fp32_state(ctx) ? (const void*)ctx->s0 : (const void*)ctx->qn;
     a.qout = out;
     a.stage = 0;
     for (int d = 0; d < ctx->ndim; ++d) {
@@ -368,7 +379,7 @@ extern "C" int mfc_max_wavespeed(mfc_ctx* ctx, double* s) {
 }
 
 static int run_steps(mfc_ctx* ctx, double cfl, double dt_fixed, int nsteps, double* t_out) {
-    if (!ctx->have_state) return MFC_ESTATE;
+    if (!ctx->have_state || (ctx->form == FORM_GATED && !ctx->have_gate)) return MFC_ESTATE;
     int st = write_ctrl_params(ctx, cfl, dt_fixed);
     if (st) return st;
     if (ctx->timing) {
@@ -402,6 +413,41 @@ extern "C" int mfc_step_rk3(mfc_ctx* ctx, double cfl, int nsteps, double* t_adva
 extern "C" int mfc_step_rk3_dt(mfc_ctx* ctx, double dt, int nsteps) {
     if (!ctx || nsteps < 0 || !(dt > 0.0) || !isfinite(dt)) return MFC_EINVAL;
     return run_steps(ctx, 0.0, dt, nsteps, NULL);
+}
+
+extern "C" int mfc_set_mlp_weights(mfc_ctx* ctx, const float* w, int n) {
+    if (!ctx || !w || n != kGateParams) return MFC_EINVAL;
+    if (ctx->form != FORM_GATED) return MFC_EINVAL;
+    for (int k = 0; k < n; ++k)
+        if (!isfinite(w[k])) return MFC_EINVAL;
+    memcpy(ctx->gate.w, w, sizeof(ctx->gate.w));
+    ctx->have_gate = true;
+    if (ctx->gexec) {  // the captured step holds the previous weights
+        cudaGraphExecDestroy(ctx->gexec);
+        ctx->gexec = NULL;
+    }
+    ctx->graph_ok = false;
+    return MFC_OK;
+}
+
+extern "C" int mfc_gate_stats(mfc_ctx* ctx, long long* gated, long long* fallback, long long* cells) {
+    if (!ctx) return MFC_EINVAL;
+    if (gated) *gated = (long long)ctx->ctrl_h->gated;
+    if (fallback) *fallback = (long long)ctx->ctrl_h->fallback;
+    if (cells) *cells = (long long)ctx->ctrl_h->cells;
+    return MFC_OK;
+}
+
+extern "C" int mfc_gate_samples(mfc_ctx* ctx, float* X, float* Y, long long capacity, float tau, long long* count) {
+    if (!ctx || !X || !Y || !(tau > 0.f)) return MFC_EINVAL;
+    if (!ctx->have_state) return MFC_ESTATE;
+    long long need = 2LL * ctx->ndim * ctx->ncell;
+    if (capacity < need) return MFC_EINVAL;
+    CK(launch_gate_samples(ctx->ndim, ctx->qn, ctx->n, ctx->periodic, ctx->eos, ctx->p.weno_eps, tau, X, Y,
+                           ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (count) *count = need;
+    return MFC_OK;
 }
 
 extern "C" int mfc_launches_per_step(mfc_ctx* ctx, int* launches) {

@@ -19,6 +19,9 @@ struct DevCtrl {
     double dt_fixed;            // > 0 selects fixed-dt mode
     unsigned int status;        // bit 0: non-physical face state; bit 1: bad wave speed or dt
     unsigned int pad;
+    unsigned long long gated;   // gated form: cell reconstructions done with linear weights
+    unsigned long long fallback;  // gated form: gated cells recomputed with WENO (non-physical faces)
+    unsigned long long cells;   // gated form: cell reconstructions evaluated
 };
 
 enum SweepMode {
@@ -51,11 +54,22 @@ struct SweepArgs {
 //   FORM_FP64_FAST   FP64, formulas reorganised for fewer FP64 instructions
 //   FORM_MIXED       FP32 stencils/Riemann, FP64 pressure numerator and RK update
 //   FORM_FP64_EXACT  FP64 in the reference operation order (bit-identical to it)
-enum Form { FORM_FP64_FAST = 0, FORM_MIXED = 1, FORM_FP64_EXACT = 2 };
+//   FORM_GATED       FORM_MIXED with the MLP gate (linear weights in smooth cells)
+enum Form { FORM_FP64_FAST = 0, FORM_MIXED = 1, FORM_FP64_EXACT = 2, FORM_GATED = 3 };
+
+// Parameters of the gate network, passed by value to the gated sweep (they
+// live in the kernel's constant parameter bank).
+constexpr int kGateParams = 1281;
+struct GateWeights {
+    float w[kGateParams];
+};
 
 cudaError_t launch_sweep_fp64(int ndim, int dir, int mode, const SweepArgs& a, cudaStream_t s);
 cudaError_t launch_sweep_mixed(int ndim, int dir, int mode, const SweepArgs& a, cudaStream_t s);
 cudaError_t launch_sweep_fp64x(int ndim, int dir, int mode, const SweepArgs& a, cudaStream_t s);
+cudaError_t launch_sweep_gated(int ndim, int dir, int mode, const SweepArgs& a, const GateWeights& g, cudaStream_t s);
+cudaError_t launch_gate_samples(int ndim, const double* q, const int* n, const int* periodic, const Eos& e,
+                                double eps, float tau, float* X, float* Y, cudaStream_t s);
 
 // auxiliary kernels (aux.cu)
 cudaError_t launch_prim_to_cons(int ndim, double* q, long long ncell, const Eos& e, cudaStream_t s);

@@ -146,17 +146,77 @@ struct XStage {
 };
 
 template <int FORM>
-using FormReal = typename std::conditional<FORM == FORM_MIXED, float, double>::type;
+using FormReal = typename std::conditional<FORM == FORM_MIXED || FORM == FORM_GATED, float, double>::type;
+
+// Gate-network argument of a sweep: the 1281 weights for the gated form,
+// nothing otherwise.
+template <int FORM>
+struct GateArg {
+    float w[FORM == FORM_GATED ? kGateParams : 1];
+};
+
+// Logit of the gate network for a normalised stencil x[5]; th indexes the
+// kernel-parameter copy of the weights at compile-time offsets.
+__device__ __forceinline__ float gate_logit(const float* th, const float* x) {
+    constexpr int H = 32, OB1 = 160, OW2 = 192, OB2 = 1216, OW3 = 1248, OB3 = 1280;
+    float h1[H];
+#pragma unroll
+    for (int j = 0; j < H; ++j) {
+        float a = th[OB1 + j];
+#pragma unroll
+        for (int i = 0; i < 5; ++i) a = fmaf(th[j * 5 + i], x[i], a);
+        h1[j] = fmaxf(a, 0.f);
+    }
+    float z = th[OB3];
+#pragma unroll
+    for (int j = 0; j < H; ++j) {
+        float a = th[OB2 + j];
+#pragma unroll
+        for (int i = 0; i < H; ++i) a = fmaf(th[OW2 + j * H + i], h1[i], a);
+        z = fmaf(th[OW3 + j], fmaxf(a, 0.f), z);
+    }
+    return z;
+}
+
+// Normalised sensor stencil (v_k - v_2) / (max_k |v_k - v_2| + 1e-12).
+__device__ __forceinline__ void gate_input(const float* v, float* x) {
+    float m = 0.f;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) m = fmaxf(m, fabsf(v[k] - v[2]));
+    float r = __fdividef(1.f, m + 1e-12f);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) x[k] = (v[k] - v[2]) * r;
+}
+
+// Linear-weight (fifth-order upwind) face values of cell i: the WENO5
+// candidates combined with the linear weights, written in differences.
+__device__ __forceinline__ void linear5(float v0, float v1, float v2, float v3, float v4, float& vm, float& vp) {
+    float d1 = v1 - v0, d2 = v2 - v1, d3 = v3 - v2, d4 = v4 - v3;
+    vm = v2 + (0.1f * (5.f * d2 - 2.f * d1) + 0.6f * (d2 + 2.f * d3) + 0.3f * (4.f * d3 - d4)) * (1.f / 6.f);
+    vp = v2 + (0.3f * (d1 - 4.f * d2) - 0.6f * (2.f * d2 + d3) + 0.1f * (2.f * d4 - 5.f * d3)) * (1.f / 6.f);
+}
+
+// A reconstructed face state is usable when rho > 0, 0 <= alpha1 <= 1 and
+// p + pi_inf of the mixture is positive ((Gamma + 1) p + Pi > 0).
+template <int NDIM>
+__device__ __forceinline__ bool face_ok(const EosR<float>& e, const float* w) {
+    using FL = Fields<NDIM>;
+    float a1 = w[FL::IA];
+    float G, Pi;
+    mixture(e, a1, G, Pi);
+    return (w[0] + w[1] > 0.f) && (a1 >= 0.f) && (a1 <= 1.f) && ((G + 1.f) * w[FL::IE] + Pi > 0.f);
+}
 
 template <int NDIM, int DIR, int MODE, int FORM>
-__global__ void __launch_bounds__(kSweepThreads) sweep_kernel(const SweepArgs a) {
+__global__ void __launch_bounds__(kSweepThreads) sweep_kernel(const SweepArgs a, const GateArg<FORM> gate) {
     using R = FormReal<FORM>;
     constexpr bool EXACT = FORM == FORM_FP64_EXACT;
+    constexpr bool GATED = FORM == FORM_GATED;
     using FL = Fields<NDIM>;
     using LS = LoadSet<NDIM, R>;
     constexpr int NEQ = FL::NEQ, IE = FL::IE, IA = FL::IA;
     constexpr int NL = LS::N;
-    constexpr bool MIXED = FORM == FORM_MIXED;
+    constexpr bool MIXED = FORM == FORM_MIXED || FORM == FORM_GATED;
     constexpr int CH = XStage<R>::CH, PITCH = XStage<R>::PITCH;
     constexpr int WARPS = kSweepThreads / 32;
     __shared__ R stage[DIR == 0 ? WARPS * NL * 32 * PITCH : 1];
@@ -223,6 +283,7 @@ __global__ void __launch_bounds__(kSweepThreads) sweep_kernel(const SweepArgs a)
 
     bool bad = false;
     R smax = R(0);
+    unsigned n_gated = 0, n_fallback = 0, n_cells = 0;
     double dt = 0.0;
     if (MODE == SW_LAST_RK) dt = a.ctrl->dt;
 
@@ -242,10 +303,36 @@ __global__ void __launch_bounds__(kSweepThreads) sweep_kernel(const SweepArgs a)
 
     for (int j = s0 - 1; j <= s1; ++j) {
         R vm[NEQ], vp[NEQ];
+        bool use_weno = true;
+        if constexpr (GATED) {
+            // gate: linear weights when the network calls both the density and
+            // the pressure stencil smooth (logit < 0) and the faces stay physical
+            float sens[5], x[5];
+            bool smooth = true;
+#pragma unroll 1
+            for (int sensor = 0; sensor < 2 && smooth; ++sensor) {
 #pragma unroll
-        for (int f = 0; f < NEQ; ++f) {
-            if constexpr (EXACT) exact::weno5(a.eps, W[0][f], W[1][f], W[2][f], W[3][f], W[4][f], vm[f], vp[f]);
-            else weno5(W[0][f], W[1][f], W[2][f], W[3][f], W[4][f], eps, vm[f], vp[f]);
+                for (int k = 0; k < 5; ++k) sens[k] = sensor == 0 ? W[k][0] + W[k][1] : W[k][IE];
+                gate_input(sens, x);
+                smooth = gate_logit(gate.w, x) < 0.f;
+            }
+            if (smooth) {
+#pragma unroll
+                for (int f = 0; f < NEQ; ++f) linear5(W[0][f], W[1][f], W[2][f], W[3][f], W[4][f], vm[f], vp[f]);
+                use_weno = !(face_ok<NDIM>(er, vm) && face_ok<NDIM>(er, vp));
+            }
+            if (j >= s0 && j < s1) {   // count each cell once (not the segment halos)
+                n_fallback += smooth && use_weno;
+                n_gated += smooth && !use_weno;
+                n_cells += 1;
+            }
+        }
+        if (use_weno) {
+#pragma unroll
+            for (int f = 0; f < NEQ; ++f) {
+                if constexpr (EXACT) exact::weno5(a.eps, W[0][f], W[1][f], W[2][f], W[3][f], W[4][f], vm[f], vp[f]);
+                else weno5(W[0][f], W[1][f], W[2][f], W[3][f], W[4][f], eps, vm[f], vp[f]);
+            }
         }
         if (j >= s0) {
             R F[NEQ], uf;
@@ -365,12 +452,27 @@ __global__ void __launch_bounds__(kSweepThreads) sweep_kernel(const SweepArgs a)
         }
     }
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&a.ctrl->status, 1u);
+    if constexpr (GATED) {
+        // only cells this lane owns count (inactive lanes and segment halos excluded)
+        if (!active) n_gated = n_fallback = n_cells = 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            n_gated += __shfl_xor_sync(0xffffffffu, n_gated, o);
+            n_fallback += __shfl_xor_sync(0xffffffffu, n_fallback, o);
+            n_cells += __shfl_xor_sync(0xffffffffu, n_cells, o);
+        }
+        if (lane == 0) {
+            atomicAdd(&a.ctrl->gated, (unsigned long long)n_gated);
+            atomicAdd(&a.ctrl->fallback, (unsigned long long)n_fallback);
+            atomicAdd(&a.ctrl->cells, (unsigned long long)n_cells);
+        }
+    }
 }
 
 // Launch one sweep: the valid (direction, mode) pairs are x FIRST, y MID
 // (3-D), and LAST_RK / LAST_RHS on the last direction.
 template <int NDIM, int FORM>
-cudaError_t launch_sweep_t(int dir, int mode, const SweepArgs& a, cudaStream_t s) {
+cudaError_t launch_sweep_t(int dir, int mode, const SweepArgs& a, const GateArg<FORM>& g, cudaStream_t s) {
     long long warps = sweep_warps(dir, a.n, a.seg);
     long long blocks = (warps * 32 + kSweepThreads - 1) / kSweepThreads;
     if (blocks <= 0) return cudaSuccess;
@@ -378,13 +480,13 @@ cudaError_t launch_sweep_t(int dir, int mode, const SweepArgs& a, cudaStream_t s
     dim3 grid((unsigned)blocks), block(kSweepThreads);
     constexpr int LAST = NDIM - 1;
     if (dir == 0 && mode == SW_FIRST && NDIM > 1) {
-        if constexpr (NDIM > 1) sweep_kernel<NDIM, 0, SW_FIRST, FORM><<<grid, block, 0, s>>>(a);
+        if constexpr (NDIM > 1) sweep_kernel<NDIM, 0, SW_FIRST, FORM><<<grid, block, 0, s>>>(a, g);
     } else if (dir == 1 && mode == SW_MID && NDIM == 3) {
-        if constexpr (NDIM == 3) sweep_kernel<NDIM, 1, SW_MID, FORM><<<grid, block, 0, s>>>(a);
+        if constexpr (NDIM == 3) sweep_kernel<NDIM, 1, SW_MID, FORM><<<grid, block, 0, s>>>(a, g);
     } else if (dir == LAST && mode == SW_LAST_RK) {
-        sweep_kernel<NDIM, LAST, SW_LAST_RK, FORM><<<grid, block, 0, s>>>(a);
+        sweep_kernel<NDIM, LAST, SW_LAST_RK, FORM><<<grid, block, 0, s>>>(a, g);
     } else if (dir == LAST && mode == SW_LAST_RHS) {
-        sweep_kernel<NDIM, LAST, SW_LAST_RHS, FORM><<<grid, block, 0, s>>>(a);
+        sweep_kernel<NDIM, LAST, SW_LAST_RHS, FORM><<<grid, block, 0, s>>>(a, g);
     } else {
         return cudaErrorInvalidValue;
     }
@@ -392,11 +494,12 @@ cudaError_t launch_sweep_t(int dir, int mode, const SweepArgs& a, cudaStream_t s
 }
 
 template <int FORM>
-cudaError_t launch_sweep_any(int ndim, int dir, int mode, const SweepArgs& a, cudaStream_t s) {
+cudaError_t launch_sweep_any(int ndim, int dir, int mode, const SweepArgs& a, const GateArg<FORM>& g,
+                             cudaStream_t s) {
     switch (ndim) {
-        case 1: return launch_sweep_t<1, FORM>(dir, mode, a, s);
-        case 2: return launch_sweep_t<2, FORM>(dir, mode, a, s);
-        case 3: return launch_sweep_t<3, FORM>(dir, mode, a, s);
+        case 1: return launch_sweep_t<1, FORM>(dir, mode, a, g, s);
+        case 2: return launch_sweep_t<2, FORM>(dir, mode, a, g, s);
+        case 3: return launch_sweep_t<3, FORM>(dir, mode, a, g, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -69,6 +69,16 @@ def lib() -> ctypes.CDLL:
                                  ctypes.POINTER(ctypes.c_longlong)], ip),
             "mfc_alu_peak": ([ip, dp], ip),
             "mfc_rhs_noalloc": ([ctypes.POINTER(MfcParams), vp, vp, vp], ip),
+            "mfc_set_mlp_weights": ([vp, ctypes.POINTER(ctypes.c_float), ip], ip),
+            "mfc_gate_stats": ([vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
+                                ctypes.POINTER(ctypes.c_longlong)], ip),
+            "mfc_gate_samples": ([vp, vp, vp, ctypes.c_longlong, ctypes.c_float,
+                                  ctypes.POINTER(ctypes.c_longlong)], ip),
+            "mfc_mlp_nparams": ([], ip),
+            "mfc_mlp_loss_grad": ([vp, vp, ctypes.c_longlong, vp, ctypes.c_float, vp, vp, vp], ip),
+            "mfc_mlp_adam": ([vp, vp, vp, vp, ip, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                              vp], ip),
+            "mfc_mlp_forward": ([vp, ctypes.c_longlong, vp, vp, vp], ip),
             "mfc_strerror": ([ip], ctypes.c_char_p),
             "mfc_last_cuda_error": ([vp], ip),
         }
@@ -200,6 +210,30 @@ class Solver:
                                        "mfc_step_rk3", allow)
         return t.value
 
+    def set_mlp_weights(self, w):
+        """Gate weights (1281 floats) of a gated context."""
+        arr = np.ascontiguousarray(w, dtype=np.float32)
+        return self._check(lib().mfc_set_mlp_weights(self.ctx, arr.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                                     arr.size), "mfc_set_mlp_weights")
+
+    def gate_stats(self):
+        """(gated, fallback, cells) of the last rhs/step call."""
+        g, f, c = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_longlong()
+        self._check(lib().mfc_gate_stats(self.ctx, ctypes.byref(g), ctypes.byref(f), ctypes.byref(c)),
+                    "mfc_gate_stats")
+        return g.value, f.value, c.value
+
+    def gate_samples(self, tau: float = 0.1):
+        """Labelled samples (X [n,5], Y [n]) of the current state as torch CUDA tensors."""
+        import torch
+        n = 2 * int(self.p["ndim"]) * int(np.prod(self.shape[1:]))
+        X = torch.empty((n, 5), dtype=torch.float32, device="cuda")
+        Y = torch.empty(n, dtype=torch.float32, device="cuda")
+        cnt = ctypes.c_longlong()
+        self._check(lib().mfc_gate_samples(self.ctx, ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(Y.data_ptr()),
+                                           n, float(tau), ctypes.byref(cnt)), "mfc_gate_samples")
+        return X, Y
+
     def step_rk3_dt(self, dt: float, nsteps: int):
         return self._check(lib().mfc_step_rk3_dt(self.ctx, float(dt), int(nsteps)), "mfc_step_rk3_dt")
 
@@ -223,3 +257,34 @@ class Solver:
             out[name.value.decode()] = (ms.value, cnt.value)
             i += 1
         return out
+
+
+# ---- training kernels of the gate network (device tensors) ----------------
+
+def _dev(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def mlp_loss_grad(X, Y, theta, grad, loss, pos_weight: float = 1.0):
+    st = lib().mfc_mlp_loss_grad(_dev(X), _dev(Y), int(Y.numel()), _dev(theta), float(pos_weight), _dev(grad),
+                                 _dev(loss), _stream())
+    if st != MFC_OK:
+        raise MfcError(st, "mfc_mlp_loss_grad")
+
+
+def mlp_adam(theta, grad, m, v, t: int, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+    st = lib().mfc_mlp_adam(_dev(theta), _dev(grad), _dev(m), _dev(v), int(t), float(lr), float(beta1), float(beta2),
+                            float(eps), _stream())
+    if st != MFC_OK:
+        raise MfcError(st, "mfc_mlp_adam")
+
+
+def mlp_forward(X, theta, z):
+    st = lib().mfc_mlp_forward(_dev(X), int(X.shape[0]), _dev(theta), _dev(z), _stream())
+    if st != MFC_OK:
+        raise MfcError(st, "mfc_mlp_forward")
