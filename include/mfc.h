@@ -160,13 +160,16 @@ int mfc_gate_samples(mfc_ctx* ctx, float* X, float* Y, long long capacity, float
  *   (l = wp y softplus(-z) + (1 - y) softplus(z), z the logit) into *loss and
  *   its gradient into grad[MFC_MLP_NPARAMS] (both overwritten).
  * mfc_mlp_adam: one Adam step t (1-based) of theta with moments m, v.
- * mfc_mlp_forward: logits z[n] of X[n][5]. */
+ * mfc_mlp_forward: logits z[n] of X[n][5] (FP32 CUDA cores).
+ * mfc_mlp_forward_tc: the same logits as the gated sweep computes them --
+ *   both hidden layers on the tensor cores, fp16 operands, FP32 accumulation. */
 int mfc_mlp_nparams(void);
 int mfc_mlp_loss_grad(const float* X, const float* Y, long long n, const float* theta, float pos_weight,
                       float* grad, float* loss, void* cuda_stream);
 int mfc_mlp_adam(float* theta, const float* grad, float* m, float* v, int t, float lr, float beta1, float beta2,
                  float eps, void* cuda_stream);
 int mfc_mlp_forward(const float* X, long long n, const float* theta, float* z, void* cuda_stream);
+int mfc_mlp_forward_tc(const float* X, long long n, const float* theta, float* z, void* cuda_stream);
 
 /* Instrumentation, no counterpart in the paper: measures the sustained FMA
  * throughput of the current device with independent FMA chains, FP64

@@ -55,7 +55,7 @@ struct mfc_ctx {
     long long kcount[K_NKINDS];
     int last_cuda;
     bool have_gate;
-    GateWeights gate;  // gated form: network weights (host copy, passed by value to the sweeps)
+    float* gate_w;     // gated form: network weights (device)
 };
 
 #define CK(call)                                   \
@@ -100,7 +100,7 @@ static int state_fields(const mfc_ctx* c) { return fp32_state(c) ? c->neq + 1 : 
 
 static void free_all(mfc_ctx* c) {
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
-    void* bufs[] = {c->qn, c->sa, c->sb, c->s0, c->acc, c->tmp64, c->ctrl};
+    void* bufs[] = {c->qn, c->sa, c->sb, c->s0, c->acc, c->tmp64, c->ctrl, c->gate_w};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (c->ctrl_h) cudaFreeHost(c->ctrl_h);
@@ -157,6 +157,8 @@ extern "C" int mfc_create(const mfc_params* params, void* cuda_stream, mfc_ctx**
               cudaMallocHost((void**)&ctx->ctrl_h, sizeof(DevCtrl)) == cudaSuccess;
     if (ok && fp32_state(ctx))
         ok = cudaMalloc((void**)&ctx->s0, nc * sfield * sizeof(float)) == cudaSuccess;
+    if (ok && ctx->form == FORM_GATED)
+        ok = cudaMalloc((void**)&ctx->gate_w, kGateParams * sizeof(float)) == cudaSuccess;
     for (int i = 0; ok && i <= kMaxTimedLaunches; ++i) ok = cudaEventCreate(&ctx->ev[i]) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
@@ -199,6 +201,7 @@ static SweepArgs base_args(mfc_ctx* ctx) {
     a.ctrl = ctx->ctrl;
     a.acc = ctx->acc;
     a.qn = ctx->qn;
+    a.gate_w = ctx->gate_w;
     return a;
 }
 
@@ -208,7 +211,7 @@ static cudaError_t launch_sweep(mfc_ctx* ctx, int dir, int mode, SweepArgs a, cu
     switch (ctx->form) {
         case FORM_FP64_EXACT: return launch_sweep_fp64x(ctx->ndim, dir, mode, a, s);
         case FORM_FP64_FAST: return launch_sweep_fp64(ctx->ndim, dir, mode, a, s);
-        case FORM_GATED: return launch_sweep_gated(ctx->ndim, dir, mode, a, ctx->gate, s);
+        case FORM_GATED: return launch_sweep_gated(ctx->ndim, dir, mode, a, s);
         default: return launch_sweep_mixed(ctx->ndim, dir, mode, a, s);
     }
 }
@@ -420,13 +423,9 @@ extern "C" int mfc_set_mlp_weights(mfc_ctx* ctx, const float* w, int n) {
     if (ctx->form != FORM_GATED) return MFC_EINVAL;
     for (int k = 0; k < n; ++k)
         if (!isfinite(w[k])) return MFC_EINVAL;
-    memcpy(ctx->gate.w, w, sizeof(ctx->gate.w));
+    CK(cudaMemcpyAsync(ctx->gate_w, w, kGateParams * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
     ctx->have_gate = true;
-    if (ctx->gexec) {  // the captured step holds the previous weights
-        cudaGraphExecDestroy(ctx->gexec);
-        ctx->gexec = NULL;
-    }
-    ctx->graph_ok = false;
     return MFC_OK;
 }
 

@@ -48,6 +48,7 @@ struct SweepArgs {
     int seg;              // cells per thread along the sweep direction
     int stage;            // 1, 2, 3
     DevCtrl* ctrl;
+    const float* gate_w;  // gated form: the 1281 network weights (device)
 };
 
 // Arithmetic forms of the sweep kernels:
@@ -57,17 +58,13 @@ struct SweepArgs {
 //   FORM_GATED       FORM_MIXED with the MLP gate (linear weights in smooth cells)
 enum Form { FORM_FP64_FAST = 0, FORM_MIXED = 1, FORM_FP64_EXACT = 2, FORM_GATED = 3 };
 
-// Parameters of the gate network, passed by value to the gated sweep (they
-// live in the kernel's constant parameter bank).
+// Number of parameters of the gate network (W1[32][5], b1, W2[32][32], b2, w3, b3).
 constexpr int kGateParams = 1281;
-struct GateWeights {
-    float w[kGateParams];
-};
 
 cudaError_t launch_sweep_fp64(int ndim, int dir, int mode, const SweepArgs& a, cudaStream_t s);
 cudaError_t launch_sweep_mixed(int ndim, int dir, int mode, const SweepArgs& a, cudaStream_t s);
 cudaError_t launch_sweep_fp64x(int ndim, int dir, int mode, const SweepArgs& a, cudaStream_t s);
-cudaError_t launch_sweep_gated(int ndim, int dir, int mode, const SweepArgs& a, const GateWeights& g, cudaStream_t s);
+cudaError_t launch_sweep_gated(int ndim, int dir, int mode, const SweepArgs& a, cudaStream_t s);
 cudaError_t launch_gate_samples(int ndim, const double* q, const int* n, const int* periodic, const Eos& e,
                                 double eps, float tau, float* X, float* Y, cudaStream_t s);
 

@@ -21,6 +21,8 @@
 // a segment.  Boundary ghosts come from index clamping (transmissive) or
 // wrapping (periodic) in the loads.
 #pragma once
+#include <cuda_fp16.h>
+
 #include <type_traits>
 
 #include "mfc_internal.cuh"
@@ -148,34 +150,126 @@ struct XStage {
 template <int FORM>
 using FormReal = typename std::conditional<FORM == FORM_MIXED || FORM == FORM_GATED, float, double>::type;
 
-// Gate-network argument of a sweep: the 1281 weights for the gated form,
-// nothing otherwise.
-template <int FORM>
-struct GateArg {
-    float w[FORM == FORM_GATED ? kGateParams : 1];
+// ---- gate network on the tensor cores -------------------------------------
+// A warp evaluates the network for its 32 cells x 2 sensors = 64 samples at
+// once: layer 1 (5 -> 32, K padded to 8) as 4x4 mma.m16n8k8 and layer 2
+// (32 -> 32) as 4x4x2 mma.m16n8k16, fp16 operands with FP32 accumulation;
+// the fragments of layer 1's result are layer 2's A fragments as they stand.
+// The 32 -> 1 output is a dot product of the layer-2 fragments with w3,
+// reduced over the four lanes of a fragment group.
+struct GateSmem {
+    unsigned w1f[4][32];       // layer-1 B fragments, per n-tile and lane
+    unsigned w2f[2][4][32][2]; // layer-2 B fragments, per k-tile, n-tile, lane
+    float b1[32], b2[32], w3[32], b3;
 };
 
-// Logit of the gate network for a normalised stencil x[5]; th indexes the
-// kernel-parameter copy of the weights at compile-time offsets.
-__device__ __forceinline__ float gate_logit(const float* th, const float* x) {
-    constexpr int H = 32, OB1 = 160, OW2 = 192, OB2 = 1216, OW3 = 1248, OB3 = 1280;
-    float h1[H];
-#pragma unroll
-    for (int j = 0; j < H; ++j) {
-        float a = th[OB1 + j];
-#pragma unroll
-        for (int i = 0; i < 5; ++i) a = fmaf(th[j * 5 + i], x[i], a);
-        h1[j] = fmaxf(a, 0.f);
+__device__ __forceinline__ unsigned pack_half2(float lo, float hi) {
+    __half2 h = __floats2half2_rn(lo, hi);
+    return *reinterpret_cast<unsigned*>(&h);
+}
+
+// Fill the block's fragment tables from the 1281 weights (all threads).
+__device__ __forceinline__ void gate_fill(GateSmem& g, const float* __restrict__ w) {
+    constexpr int OB1 = 160, OW2 = 192, OB2 = 1216, OW3 = 1248, OB3 = 1280;
+    for (int i = threadIdx.x; i < 4 * 32; i += blockDim.x) {
+        int nt = i / 32, l = i % 32, gq = l / 4, t = l % 4;
+        int n = nt * 8 + gq, k = 2 * t;
+        float lo = k < 5 ? w[n * 5 + k] : 0.f, hi = k + 1 < 5 ? w[n * 5 + k + 1] : 0.f;
+        g.w1f[nt][l] = pack_half2(lo, hi);
     }
-    float z = th[OB3];
-#pragma unroll
-    for (int j = 0; j < H; ++j) {
-        float a = th[OB2 + j];
-#pragma unroll
-        for (int i = 0; i < H; ++i) a = fmaf(th[OW2 + j * H + i], h1[i], a);
-        z = fmaf(th[OW3 + j], fmaxf(a, 0.f), z);
+    for (int i = threadIdx.x; i < 2 * 4 * 32; i += blockDim.x) {
+        int kt = i / 128, nt = (i / 32) % 4, l = i % 32, gq = l / 4, t = l % 4;
+        int n = nt * 8 + gq, k = kt * 16 + 2 * t;
+        g.w2f[kt][nt][l][0] = pack_half2(w[OW2 + n * 32 + k], w[OW2 + n * 32 + k + 1]);
+        g.w2f[kt][nt][l][1] = pack_half2(w[OW2 + n * 32 + k + 8], w[OW2 + n * 32 + k + 9]);
     }
-    return z;
+    for (int i = threadIdx.x; i < 32; i += blockDim.x) {
+        g.b1[i] = w[OB1 + i];
+        g.b2[i] = w[OB2 + i];
+        g.w3[i] = w[OW3 + i];
+    }
+    if (threadIdx.x == 0) g.b3 = w[OB3];
+}
+
+__device__ __forceinline__ void ldsm_x4(unsigned& r0, unsigned& r1, unsigned& r2, unsigned& r3, const void* row) {
+    unsigned a = (unsigned)__cvta_generic_to_shared(row);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(a));
+}
+
+__device__ __forceinline__ void mma_k8(float* d, unsigned a0, unsigned a1, unsigned b0) {
+    asm("mma.sync.aligned.m16n8k8.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5}, {%6}, {%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(b0));
+}
+
+__device__ __forceinline__ void mma_k16(float* d, unsigned a0, unsigned a1, unsigned a2, unsigned a3, unsigned b0,
+                                        unsigned b1) {
+    asm("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// Logits of this lane's cell for both sensors.  xr, xp: the normalised
+// density and pressure stencils of the lane's cell; tile: this warp's 1 KB
+// A tile (64 rows x 8 halves).  Must be called by all 32 lanes together.
+__device__ __forceinline__ void gate_logits(const GateSmem& g, uint4* tile, const float* xr, const float* xp,
+                                            float& zr, float& zp) {
+    const int lane = threadIdx.x & 31, t = lane & 3;
+    __syncwarp();
+    tile[lane] = make_uint4(pack_half2(xr[0], xr[1]), pack_half2(xr[2], xr[3]), pack_half2(xr[4], 0.f), 0u);
+    tile[32 + lane] = make_uint4(pack_half2(xp[0], xp[1]), pack_half2(xp[2], xp[3]), pack_half2(xp[4], 0.f), 0u);
+    __syncwarp();
+    unsigned a[4][2];   // layer-1 A fragments of the 4 m-tiles (rows 16 mt .. 16 mt + 15)
+    ldsm_x4(a[0][0], a[0][1], a[1][0], a[1][1], tile + lane);
+    ldsm_x4(a[2][0], a[2][1], a[3][0], a[3][1], tile + 32 + lane);
+    float part[4][2];   // partial logits of rows gq and gq + 8 of each m-tile
+#pragma unroll
+    for (int mt = 0; mt < 4; ++mt) {
+        unsigned a2[2][4];
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt) {
+            float c[4] = {0.f, 0.f, 0.f, 0.f};
+            mma_k8(c, a[mt][0], a[mt][1], g.w1f[nt][lane]);
+            const float bl = g.b1[nt * 8 + 2 * t], bh = g.b1[nt * 8 + 2 * t + 1];
+            unsigned lo = pack_half2(fmaxf(c[0] + bl, 0.f), fmaxf(c[1] + bh, 0.f));
+            unsigned hi = pack_half2(fmaxf(c[2] + bl, 0.f), fmaxf(c[3] + bh, 0.f));
+            a2[nt >> 1][(nt & 1) * 2 + 0] = lo;
+            a2[nt >> 1][(nt & 1) * 2 + 1] = hi;
+        }
+        float p0 = 0.f, p1 = 0.f;
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt) {
+            float c[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int kt = 0; kt < 2; ++kt)
+                mma_k16(c, a2[kt][0], a2[kt][1], a2[kt][2], a2[kt][3], g.w2f[kt][nt][lane][0], g.w2f[kt][nt][lane][1]);
+            const int n0 = nt * 8 + 2 * t;
+            p0 = fmaf(fmaxf(c[0] + g.b2[n0], 0.f), g.w3[n0], p0);
+            p0 = fmaf(fmaxf(c[1] + g.b2[n0 + 1], 0.f), g.w3[n0 + 1], p0);
+            p1 = fmaf(fmaxf(c[2] + g.b2[n0], 0.f), g.w3[n0], p1);
+            p1 = fmaf(fmaxf(c[3] + g.b2[n0 + 1], 0.f), g.w3[n0 + 1], p1);
+        }
+        p0 += __shfl_xor_sync(0xffffffffu, p0, 1);
+        p0 += __shfl_xor_sync(0xffffffffu, p0, 2);
+        p1 += __shfl_xor_sync(0xffffffffu, p1, 1);
+        p1 += __shfl_xor_sync(0xffffffffu, p1, 2);
+        part[mt][0] = p0 + g.b3;
+        part[mt][1] = p1 + g.b3;
+    }
+    // sample row r of m-tile mt sits in fragment group r % 8, half r / 8; the
+    // lane's own rows are (mt = lane / 16, r = lane % 16) for the density and
+    // (mt = 2 + lane / 16, same r) for the pressure
+    const int src = 4 * (lane & 7), half = (lane >> 3) & 1, hi16 = lane >> 4;
+    float v[4][2];
+#pragma unroll
+    for (int mt = 0; mt < 4; ++mt)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) v[mt][h] = __shfl_sync(0xffffffffu, part[mt][h], src);
+    zr = hi16 ? (half ? v[1][1] : v[1][0]) : (half ? v[0][1] : v[0][0]);
+    zp = hi16 ? (half ? v[3][1] : v[3][0]) : (half ? v[2][1] : v[2][0]);
 }
 
 // Normalised sensor stencil (v_k - v_2) / (max_k |v_k - v_2| + 1e-12).
@@ -208,7 +302,7 @@ __device__ __forceinline__ bool face_ok(const EosR<float>& e, const float* w) {
 }
 
 template <int NDIM, int DIR, int MODE, int FORM>
-__global__ void __launch_bounds__(kSweepThreads) sweep_kernel(const SweepArgs a, const GateArg<FORM> gate) {
+__global__ void __launch_bounds__(kSweepThreads) sweep_kernel(const SweepArgs a) {
     using R = FormReal<FORM>;
     constexpr bool EXACT = FORM == FORM_FP64_EXACT;
     constexpr bool GATED = FORM == FORM_GATED;
@@ -220,6 +314,12 @@ __global__ void __launch_bounds__(kSweepThreads) sweep_kernel(const SweepArgs a,
     constexpr int CH = XStage<R>::CH, PITCH = XStage<R>::PITCH;
     constexpr int WARPS = kSweepThreads / 32;
     __shared__ R stage[DIR == 0 ? WARPS * NL * 32 * PITCH : 1];
+    __shared__ GateSmem gsm[GATED ? 1 : 0 + 1];
+    __shared__ uint4 gtile[GATED ? WARPS * 64 : 1];
+    if constexpr (GATED) {
+        gate_fill(gsm[0], a.gate_w);   // every thread, before any warp leaves
+        __syncthreads();
+    }
 
     const int n0 = a.n[0], n1 = a.n[1], n2 = a.n[2];
     const int na = DIR == 0 ? n1 : n0;
@@ -306,16 +406,18 @@ __global__ void __launch_bounds__(kSweepThreads) sweep_kernel(const SweepArgs a,
         bool use_weno = true;
         if constexpr (GATED) {
             // gate: linear weights when the network calls both the density and
-            // the pressure stencil smooth (logit < 0) and the faces stay physical
-            float sens[5], x[5];
-            bool smooth = true;
-#pragma unroll 1
-            for (int sensor = 0; sensor < 2 && smooth; ++sensor) {
+            // the pressure stencil smooth (logit < 0) and the faces stay physical;
+            // all 32 lanes take part in the tensor-core evaluation
+            float sr[5], sp[5], xr[5], xp[5], zr, zp;
 #pragma unroll
-                for (int k = 0; k < 5; ++k) sens[k] = sensor == 0 ? W[k][0] + W[k][1] : W[k][IE];
-                gate_input(sens, x);
-                smooth = gate_logit(gate.w, x) < 0.f;
+            for (int k = 0; k < 5; ++k) {
+                sr[k] = W[k][0] + W[k][1];
+                sp[k] = W[k][IE];
             }
+            gate_input(sr, xr);
+            gate_input(sp, xp);
+            gate_logits(gsm[0], gtile + (threadIdx.x >> 5) * 64, xr, xp, zr, zp);
+            const bool smooth = zr < 0.f && zp < 0.f;
             if (smooth) {
 #pragma unroll
                 for (int f = 0; f < NEQ; ++f) linear5(W[0][f], W[1][f], W[2][f], W[3][f], W[4][f], vm[f], vp[f]);
@@ -472,7 +574,7 @@ __global__ void __launch_bounds__(kSweepThreads) sweep_kernel(const SweepArgs a,
 // Launch one sweep: the valid (direction, mode) pairs are x FIRST, y MID
 // (3-D), and LAST_RK / LAST_RHS on the last direction.
 template <int NDIM, int FORM>
-cudaError_t launch_sweep_t(int dir, int mode, const SweepArgs& a, const GateArg<FORM>& g, cudaStream_t s) {
+cudaError_t launch_sweep_t(int dir, int mode, const SweepArgs& a, cudaStream_t s) {
     long long warps = sweep_warps(dir, a.n, a.seg);
     long long blocks = (warps * 32 + kSweepThreads - 1) / kSweepThreads;
     if (blocks <= 0) return cudaSuccess;
@@ -480,13 +582,13 @@ cudaError_t launch_sweep_t(int dir, int mode, const SweepArgs& a, const GateArg<
     dim3 grid((unsigned)blocks), block(kSweepThreads);
     constexpr int LAST = NDIM - 1;
     if (dir == 0 && mode == SW_FIRST && NDIM > 1) {
-        if constexpr (NDIM > 1) sweep_kernel<NDIM, 0, SW_FIRST, FORM><<<grid, block, 0, s>>>(a, g);
+        if constexpr (NDIM > 1) sweep_kernel<NDIM, 0, SW_FIRST, FORM><<<grid, block, 0, s>>>(a);
     } else if (dir == 1 && mode == SW_MID && NDIM == 3) {
-        if constexpr (NDIM == 3) sweep_kernel<NDIM, 1, SW_MID, FORM><<<grid, block, 0, s>>>(a, g);
+        if constexpr (NDIM == 3) sweep_kernel<NDIM, 1, SW_MID, FORM><<<grid, block, 0, s>>>(a);
     } else if (dir == LAST && mode == SW_LAST_RK) {
-        sweep_kernel<NDIM, LAST, SW_LAST_RK, FORM><<<grid, block, 0, s>>>(a, g);
+        sweep_kernel<NDIM, LAST, SW_LAST_RK, FORM><<<grid, block, 0, s>>>(a);
     } else if (dir == LAST && mode == SW_LAST_RHS) {
-        sweep_kernel<NDIM, LAST, SW_LAST_RHS, FORM><<<grid, block, 0, s>>>(a, g);
+        sweep_kernel<NDIM, LAST, SW_LAST_RHS, FORM><<<grid, block, 0, s>>>(a);
     } else {
         return cudaErrorInvalidValue;
     }
@@ -494,12 +596,11 @@ cudaError_t launch_sweep_t(int dir, int mode, const SweepArgs& a, const GateArg<
 }
 
 template <int FORM>
-cudaError_t launch_sweep_any(int ndim, int dir, int mode, const SweepArgs& a, const GateArg<FORM>& g,
-                             cudaStream_t s) {
+cudaError_t launch_sweep_any(int ndim, int dir, int mode, const SweepArgs& a, cudaStream_t s) {
     switch (ndim) {
-        case 1: return launch_sweep_t<1, FORM>(dir, mode, a, g, s);
-        case 2: return launch_sweep_t<2, FORM>(dir, mode, a, g, s);
-        case 3: return launch_sweep_t<3, FORM>(dir, mode, a, g, s);
+        case 1: return launch_sweep_t<1, FORM>(dir, mode, a, s);
+        case 2: return launch_sweep_t<2, FORM>(dir, mode, a, s);
+        case 3: return launch_sweep_t<3, FORM>(dir, mode, a, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -5,6 +5,6 @@
 
 namespace mfc5 {
 cudaError_t launch_sweep_fp64x(int ndim, int dir, int mode, const SweepArgs& a, cudaStream_t s) {
-    return launch_sweep_any<FORM_FP64_EXACT>(ndim, dir, mode, a, GateArg<FORM_FP64_EXACT>{}, s);
+    return launch_sweep_any<FORM_FP64_EXACT>(ndim, dir, mode, a, s);
 }
 }  // namespace mfc5

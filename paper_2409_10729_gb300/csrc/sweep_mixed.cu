@@ -6,6 +6,6 @@
 
 namespace mfc5 {
 cudaError_t launch_sweep_mixed(int ndim, int dir, int mode, const SweepArgs& a, cudaStream_t s) {
-    return launch_sweep_any<FORM_MIXED>(ndim, dir, mode, a, GateArg<FORM_MIXED>{}, s);
+    return launch_sweep_any<FORM_MIXED>(ndim, dir, mode, a, s);
 }
 }  // namespace mfc5

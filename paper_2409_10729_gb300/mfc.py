@@ -79,6 +79,7 @@ def lib() -> ctypes.CDLL:
             "mfc_mlp_adam": ([vp, vp, vp, vp, ip, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                               vp], ip),
             "mfc_mlp_forward": ([vp, ctypes.c_longlong, vp, vp, vp], ip),
+            "mfc_mlp_forward_tc": ([vp, ctypes.c_longlong, vp, vp, vp], ip),
             "mfc_strerror": ([ip], ctypes.c_char_p),
             "mfc_last_cuda_error": ([vp], ip),
         }
@@ -288,3 +289,10 @@ def mlp_forward(X, theta, z):
     st = lib().mfc_mlp_forward(_dev(X), int(X.shape[0]), _dev(theta), _dev(z), _stream())
     if st != MFC_OK:
         raise MfcError(st, "mfc_mlp_forward")
+
+
+def mlp_forward_tc(X, theta, z):
+    """Logits with the gated sweep's tensor-core evaluation (fp16 operands)."""
+    st = lib().mfc_mlp_forward_tc(_dev(X), int(X.shape[0]), _dev(theta), _dev(z), _stream())
+    if st != MFC_OK:
+        raise MfcError(st, "mfc_mlp_forward_tc")

@@ -16,7 +16,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--case", choices=["droplets", "column", "tube"], default="droplets")
     ap.add_argument("--n", type=int, default=128, help="cells per dimension (column: ny, nx = 2 ny)")
-    ap.add_argument("--form", choices=["fp64", "fp64_fast", "mixed"], default="fp64")
+    ap.add_argument("--form", choices=["fp64", "fp64_fast", "mixed", "gated"], default="fp64")
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=1)
     ap.add_argument("--cfl", type=float, default=0.4)
@@ -36,6 +36,10 @@ def main():
     else:
         p, w = I.air_water_shock_tube(args.n)
     s = mfc.Solver(p, args.form)
+    if args.form == "gated":
+        import numpy as np
+        import os
+        s.set_mlp_weights(np.load(os.path.join(os.path.dirname(os.path.abspath(__file__)), "gate_weights.npy")))
     s.set_state_prim(w)
     s.step_rk3(args.cfl, args.warmup)
     torch.cuda.synchronize()

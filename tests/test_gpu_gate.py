@@ -200,6 +200,40 @@ def test_gate_falls_back_to_weno_on_sharp_interface():
     assert np.all(np.isfinite(q)) and np.all(q[4] >= -1e-6) and np.all(q[0] + q[1] > 0)
 
 
+def test_tensor_core_logits_match_fp32_network():
+    """The gated sweep's network (hidden layers on the tensor cores, fp16
+    operands, FP32 accumulation) against the FP32 network and the FP64
+    oracle on the same inputs: real solver stencils and random ones, with the
+    trained weights and with random weights; ragged sample count."""
+    import torch
+    from paper_2409_10729_gb300 import mfc
+    p, w = I.shock_water_column(96, 48)
+    s = mfc.Solver(p, "fp64")
+    s.set_state_prim(w)
+    s.step_rk3(0.4, 100)
+    Xs, _ = s.gate_samples(0.1)
+    rng = np.random.default_rng(11)
+    Xr = _cuda(rng.uniform(-1, 1, (4099, 5)))
+    wpath = os.path.join(ROOT, "paper_2409_10729_gb300", "gate_weights.npy")
+    thetas = [rng.normal(0, 0.3, 1281).astype(np.float32)]
+    if os.path.exists(wpath):
+        thetas.append(np.load(wpath))
+    for th in thetas:
+        T = _cuda(th)
+        for X in (Xs, Xr):
+            X = X[:X.shape[0] - 3].contiguous()
+            z32 = torch.empty(X.shape[0], device="cuda")
+            ztc = torch.empty(X.shape[0], device="cuda")
+            mfc.mlp_forward(X, T, z32)
+            mfc.mlp_forward_tc(X, T, ztc)
+            z64 = O.mlp_forward(th.astype(np.float64), X.cpu().numpy().astype(np.float64))
+            a, b = ztc.cpu().numpy(), z32.cpu().numpy()
+            assert np.max(np.abs(b - z64)) <= 1e-4 * max(1.0, np.max(np.abs(z64)))
+            # fp16 operands: a few 1e-3 of the logit scale
+            assert np.max(np.abs(a - z64)) <= 2e-2 * max(1.0, np.max(np.abs(z64)))
+            assert np.mean((a < 0) == (z64 < 0)) > 0.99
+
+
 def test_training_on_gpu_lowers_the_loss():
     from paper_2409_10729_gb300 import train_gate as T
     rng = np.random.default_rng(0)
