@@ -4,7 +4,8 @@
 Metric: grind time, ns per (cell x equation x RHS evaluation), lower is better,
 and the fraction of the HBM roofline it reaches, for the FP64 form (reference
 operation order, bit-identical to the oracle; the headline value), the
-reorganised FP64 form and the mixed-precision form.
+reorganised FP64 form, the mixed-precision form (512^3) and the MLP-gated
+form (256^3, trained weights from paper_2409_10729_gb300/gate_weights.npy).
 
 Workload (per GPU): the 3-D shock / droplet array, 256^3 cells, 7 equations,
 FP64, SSP-RK3 at CFL 0.4 (the timed "step" is one RK3 step = 3 RHS
@@ -43,7 +44,8 @@ FLOPS_RK_CELL = 28                                     # stage update, mean over
 FLOPS_WAVESPEED_CELL = 45                              # once per step, in the last stage
 # Algorithmic bytes per cell, equation and RHS: stage 1 reads q^n and writes
 # q^(1); stages 2-3 read q^(k) and q^n and write q^(k+1): 8/3 state arrays.
-ALG_BYTES = {"fp64": 8.0 / 3.0 * 8.0, "fp64_fast": 8.0 / 3.0 * 8.0, "mixed": (12.0 + 16.0 + 20.0) / 3.0}
+ALG_BYTES = {"fp64": 8.0 / 3.0 * 8.0, "fp64_fast": 8.0 / 3.0 * 8.0, "mixed": (12.0 + 16.0 + 20.0) / 3.0,
+             "gated": (12.0 + 16.0 + 20.0) / 3.0}
 
 
 def dist_env():
@@ -118,7 +120,7 @@ def read_traffic(kernel: str):
     import hashlib
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     src = b""
-    for f in ("sweep.cuh", "physics.cuh"):
+    for f in ("sweep.cuh", "physics.cuh", "physics_exact.cuh"):
         with open(os.path.join(ROOT, "paper_2409_10729_gb300", "csrc", f), "rb") as fh:
             src += fh.read()
     sha = hashlib.sha256(src).hexdigest()[:16]
@@ -133,11 +135,18 @@ def read_traffic(kernel: str):
     return None
 
 
+def gate_weights():
+    import numpy as np
+    return np.load(os.path.join(ROOT, "paper_2409_10729_gb300", "gate_weights.npy"))
+
+
 def time_form(form, p, w, steps, warmup, device_index, rank, world):
     """Run `warmup` + `steps` RK3 steps of one form; returns a result dict."""
     import torch
     from paper_2409_10729_gb300 import mfc
     s = mfc.Solver(p, form)
+    if form == "gated":
+        s.set_mlp_weights(gate_weights())
     s.set_state_prim(w)
     s.step_rk3(CFL, warmup)
     s.set_timing(True)
@@ -159,6 +168,7 @@ def time_form(form, p, w, steps, warmup, device_index, rank, world):
         ms = float(t.item())
         torch.distributed.barrier()
     kt = s.kernel_times()
+    gate = s.gate_stats() if form == "gated" else None
     launches = s.launches_per_step() * steps
     s.set_timing(False)
     ncell = p["n"][0] * p["n"][1] * p["n"][2]
@@ -168,7 +178,7 @@ def time_form(form, p, w, steps, warmup, device_index, rank, world):
     del s
     torch.cuda.empty_cache()
     return {"ms": ms, "grind": grind, "kernels": kt, "launches": launches, "clocks": clocks,
-            "t_advanced": t_adv, "ncell": ncell, "neq": neq}
+            "t_advanced": t_adv, "ncell": ncell, "neq": neq, "steps": steps, "gate": gate}
 
 
 def roofline_for(form, res, peak_alu, alu_src, hbm_peak, hbm_src):
@@ -288,6 +298,7 @@ def run_ours(args):
     forms = {"fp64": res}
     forms["fp64_fast"] = time_form("fp64_fast", p, w, args.steps, args.warmup, local, rank, world)
     if not args.no_mixed:
+        forms["gated"] = time_form("gated", p, w, args.steps, args.warmup, local, rank, world)
         pm, wm = I.shock_droplets(512)
         forms["mixed"] = time_form("mixed", pm, wm, max(2, args.steps // 2), args.warmup, local, rank, world)
         del wm
@@ -333,14 +344,18 @@ def run_ours(args):
     roof = roofline_for("fp64", res, fp64_peak, "measured (FP64 FMA-chain probe)", hbm_peak, hbm_src)
     out_forms = {}
     for name, r in forms.items():
-        peak = fp32_peak if name == "mixed" else fp64_peak
+        peak = fp32_peak if name in ("mixed", "gated") else fp64_peak
         rf = roofline_for(name, r, peak, "measured FMA-chain probe", hbm_peak, hbm_src)
-        out_forms[name] = {"grind": round(r["grind"], 5), "unit": UNIT, "ms_per_step": round(r["ms"] / (
-            max(2, args.steps // 2) if name == "mixed" else args.steps), 3), "cells": r["ncell"],
+        out_forms[name] = {"grind": round(r["grind"], 5), "unit": UNIT, "ms_per_step": round(r["ms"] / r["steps"], 3),
+            "cells": r["ncell"],
             "hbm_frac": rf["hbm"]["frac"], "hbm_gbs_algorithmic": rf["hbm"]["achieved_gbs"],
             "alu_frac": rf["frac"], "dominant_kernel": rf["kernel"],
             "kernel_ms": {k: round(v[0] / max(1, v[1]), 4) for k, v in r["kernels"].items() if v[1]},
             "clocks": r["clocks"]}
+        if r["gate"]:
+            g, f, c = r["gate"]
+            out_forms[name]["fraction_gated_linear"] = round(g / max(c, 1), 4)
+            out_forms[name]["fraction_fallback"] = round(f / max(c, 1), 4)
     line = {
         "metric": METRIC, "value": round(res["grind"], 5), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(res["ms"] / args.steps, 3),
@@ -354,7 +369,7 @@ def run_ours(args):
         "forms": out_forms,
         "e2e": {"value": round(e2e_grind, 5), "unit": UNIT, "h2d_bytes_per_step": ncell * neq * 8,
                 "d2h_bytes_per_step": ncell * neq * 8, "steps": e2e_steps},
-        "gpu_launches": res["launches"],
+        "gpu_launches": sum(r["launches"] for r in forms.values()),
         "clocks": res["clocks"],
         "cpu_baseline": base,
         "alu_peaks_tflops": {"fp64": round(fp64_peak, 3), "fp32": round(fp32_peak, 2)},
