@@ -204,6 +204,13 @@ int mfc_alu_peak(int fp64, double* tflops);
  * the status; returns MFC_ENONPHYSICAL as mfc_rhs does. */
 int mfc_rhs_noalloc(const mfc_params* params, const double* q, double* rhs, void* cuda_stream);
 
+/* Instrumentation, no counterpart in the paper: checks the mixed form's
+ * integer-pipe float<->double conversions against the hardware conversions on
+ * n pseudo-random bit patterns (all exponent ranges); *mismatches receives the
+ * number of differing results (0 expected).  Allocates 4 bytes of device
+ * memory and synchronises the legacy default stream. */
+int mfc_selfcheck_conversions(long long n, unsigned long long seed, long long* mismatches);
+
 /* Message for a status code (static storage). */
 const char* mfc_strerror(int status);
 

@@ -26,6 +26,9 @@ COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE
 FAST32 = ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"]
 EXTRA = {"sweep_mixed.cu": FAST32, "sweep_gated.cu": FAST32,
          "sweep_fp64x.cu": ["-fmad=false"], "aux.cu": ["-fmad=false"], "mlp.cu": ["-fmad=false"]}
+# extra nvcc flags for every unit (e.g. -DMFC_MIN_BLOCKS_MIXED=3); changing them
+# needs build(force=True)
+USER_FLAGS = os.environ.get("MFC5_NVCC_FLAGS", "").split()
 UNITS = ["capi.cu", "aux.cu", "sweep_fp64.cu", "sweep_fp64x.cu", "sweep_mixed.cu", "sweep_gated.cu", "mlp.cu",
          "noalloc.cu"]
 
@@ -52,7 +55,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
 
     def compile_unit(unit):
         obj = os.path.join(objdir, unit.replace(".cu", ".o"))
-        cmd = [cc, *ARCH, *COMMON, *EXTRA.get(unit, []), "-c", os.path.join(CSRC, unit), "-o", obj]
+        cmd = [cc, *ARCH, *COMMON, *EXTRA.get(unit, []), *USER_FLAGS, "-c", os.path.join(CSRC, unit), "-o", obj]
         if ptxas_info:
             cmd.insert(1, "-Xptxas=-v")
         r = subprocess.run(cmd, capture_output=True, text=True)

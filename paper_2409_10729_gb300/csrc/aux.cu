@@ -41,12 +41,14 @@ __global__ void make_mixed_state_kernel(const double* __restrict__ qn, float* __
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < nc;
          c += (long long)gridDim.x * blockDim.x) {
         double q[FL::NEQ];
+        float q32[FL::NEQ];
 #pragma unroll
         for (int f = 0; f < FL::NEQ; ++f) {
             q[f] = qn[f * nc + c];
-            s0[f * nc + c] = float(q[f]);
+            q32[f] = d2f_bits(q[f]);
+            s0[f * nc + c] = q32[f];
         }
-        s0[FL::NEQ * nc + c] = mixed_pressure<NDIM>(e, q);
+        s0[FL::NEQ * nc + c] = mixed_pressure<NDIM>(e, q, q32);
     }
 }
 
@@ -196,3 +198,46 @@ cudaError_t run_fma_probe(int fp64, double* tflops, cudaStream_t s) {
 }
 
 }  // namespace mfc5
+
+namespace mfc5 {
+
+// Self-check of the integer-pipe conversions against the hardware ones on
+// pseudo-random bit patterns spanning every exponent (splitmix64 sequence).
+__global__ void conversion_check_kernel(long long n, unsigned long long seed, unsigned* mismatches) {
+    unsigned bad = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        unsigned long long z = seed + (unsigned long long)i * 0x9e3779b97f4a7c15ULL;
+        z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+        z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+        z ^= z >> 31;
+        // doubles around the float range (exponents 880..1170) and arbitrary floats
+        unsigned long long db = (z & 0x800fffffffffffffULL) | ((unsigned long long)(880 + (z >> 52) % 291) << 52);
+        double x = __longlong_as_double((long long)db);
+        float fr = __uint_as_float((unsigned)(z >> 17));
+        float a = d2f_bits(x), b = __double2float_rn(x);
+        if (__float_as_uint(a) != __float_as_uint(b) && !(a != a && b != b)) ++bad;
+        unsigned e = (__float_as_uint(fr) >> 23) & 0xffu;
+        if (e != 0u && e != 0xffu) {   // normal floats (flushed subnormals and NaN payloads aside)
+            double c = f2d_bits(fr), d = (double)fr;
+            if (__double_as_longlong(c) != __double_as_longlong(d)) ++bad;
+        }
+    }
+    if (bad) atomicAdd(mismatches, bad);
+}
+
+}  // namespace mfc5
+
+extern "C" int mfc_selfcheck_conversions(long long n, unsigned long long seed, long long* mismatches) {
+    if (n <= 0 || !mismatches) return -1;
+    unsigned* d = nullptr;
+    if (cudaMalloc(&d, sizeof(unsigned)) != cudaSuccess) return -3;
+    cudaMemset(d, 0, sizeof(unsigned));
+    mfc5::conversion_check_kernel<<<152 * 8, 256>>>(n, seed, d);
+    unsigned h = 0;
+    cudaError_t err = cudaMemcpy(&h, d, sizeof(unsigned), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (err != cudaSuccess) return -3;
+    *mismatches = (long long)h;
+    return 0;
+}

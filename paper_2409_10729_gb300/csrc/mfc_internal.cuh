@@ -80,6 +80,25 @@ cudaError_t run_fma_probe(int fp64, double* tflops, cudaStream_t s);
 
 // thread-block size of every sweep launch
 constexpr int kSweepThreads = 128;
+// Resident 128-thread sweep blocks per SM requested from the register
+// allocator, per form (1: up to 255 registers a thread; 2: 255; 3: 168;
+// 4: 128).  The FP64 forms are bound by the FP64 pipe and lose nothing at
+// two blocks; the FP32 forms need the warps to cover their load latency.
+#ifndef MFC_MIN_BLOCKS_FP64
+#define MFC_MIN_BLOCKS_FP64 1
+#endif
+#ifndef MFC_MIN_BLOCKS_MIXED
+#define MFC_MIN_BLOCKS_MIXED 4
+#endif
+#ifndef MFC_MIN_BLOCKS_GATED
+#define MFC_MIN_BLOCKS_GATED 3
+#endif
+// 1: the sweeps issue the loads of the cell entering the stencil window at the
+// top of each step along the pencil (they complete under that step's
+// arithmetic); 0: at the bottom, just before they are used.
+#ifndef MFC_PREFETCH
+#define MFC_PREFETCH 1
+#endif
 
 __host__ __device__ inline long long sweep_warps(int dir, const int* n, int seg) {
     int na = dir == 0 ? n[1] : n[0];

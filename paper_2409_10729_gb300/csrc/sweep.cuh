@@ -82,23 +82,48 @@ __device__ __forceinline__ void to_prim(const EosR<float>& e, const float* v, fl
     w[FL::IA] = v[FL::IA];
 }
 
+// Exact float -> double and round-to-nearest-even double -> float conversions
+// done on the integer pipes by rearranging the IEEE 754 bit fields (binary32:
+// 8-bit exponent bias 127, 23-bit fraction; binary64: 11-bit bias 1023,
+// 52-bit fraction).  They return the same bits as the hardware conversions
+// (zeros and subnormals of the -ftz build flush to signed zero; the rare
+// out-of-range cases take the hardware path) and keep the conversions of the
+// mixed form's FP64 stage update off GB300's narrow FP64 pipe.
+__device__ __forceinline__ double f2d_bits(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned e = (u >> 23) & 0xffu;
+    const unsigned m = e == 0u ? 0u : (u & 0x7fffffu);
+    const unsigned ed = e == 0u ? 0u : (e == 0xffu ? 0x7ffu : e + 896u);
+    const unsigned hi = (u & 0x80000000u) | (ed << 20) | (m >> 3);
+    return __hiloint2double((int)hi, (int)(m << 29));
+}
+
+__device__ __forceinline__ float d2f_bits(double x) {
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const unsigned e = (hi >> 20) & 0x7ffu;
+    const unsigned s = hi & 0x80000000u;
+    if (e == 0u) return __uint_as_float(s);                  // zero (and FP64 subnormals)
+    if (e < 897u || e > 1150u) return __double2float_rn(x);  // outside the normal float range
+    unsigned mag = ((e - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+    const unsigned rem = lo & 0x1fffffffu;
+    mag += (rem > 0x10000000u) || (rem == 0x10000000u && (mag & 1u));
+    return __uint_as_float(s | mag);
+}
+
 // Pressure from an FP64 conservative state, mixed form: the cancelling part
 // rho E - Pi is formed in FP64, the rest in FP32.
 template <int NDIM>
-__device__ __forceinline__ float mixed_pressure(const Eos& e, const double* q) {
+__device__ __forceinline__ float mixed_pressure(const Eos& e, const double* q, const float* q32) {
     using FL = Fields<NDIM>;
-    float rho = float(q[0] + q[1]);
+    float rho = q32[0] + q32[1];
     float r = __fdividef(1.0f, rho);
     float ke2 = 0.0f;
 #pragma unroll
-    for (int k = 0; k < NDIM; ++k) {
-        float m = float(q[2 + k]);
-        ke2 += m * (m * r);
-    }
+    for (int k = 0; k < NDIM; ++k) ke2 += q32[2 + k] * (q32[2 + k] * r);
     double a1 = q[FL::IA];
-    double num = (q[FL::IE] - (a1 * e.dP + e.P2)) - double(0.5f * ke2);
-    float G = float(a1) * float(e.dg) + float(e.g2);
-    return __fdividef(float(num), G);
+    double num = (q[FL::IE] - (a1 * e.dP + e.P2)) - f2d_bits(0.5f * ke2);
+    float G = q32[FL::IA] * float(e.dg) + float(e.g2);
+    return __fdividef(d2f_bits(num), G);
 }
 
 // FP64 primitives of one cell of an FP64 conservative state (standalone use).
@@ -301,8 +326,13 @@ __device__ __forceinline__ bool face_ok(const EosR<float>& e, const float* w) {
     return (w[0] + w[1] > 0.f) && (a1 >= 0.f) && (a1 <= 1.f) && ((G + 1.f) * w[FL::IE] + Pi > 0.f);
 }
 
+template <int FORM>
+constexpr int sweep_min_blocks() {
+    return FORM == FORM_MIXED ? MFC_MIN_BLOCKS_MIXED : FORM == FORM_GATED ? MFC_MIN_BLOCKS_GATED : MFC_MIN_BLOCKS_FP64;
+}
+
 template <int NDIM, int DIR, int MODE, int FORM>
-__global__ void __launch_bounds__(kSweepThreads) sweep_kernel(const SweepArgs a) {
+__global__ void __launch_bounds__(kSweepThreads, sweep_min_blocks<FORM>()) sweep_kernel(const SweepArgs a) {
     using R = FormReal<FORM>;
     constexpr bool EXACT = FORM == FORM_FP64_EXACT;
     constexpr bool GATED = FORM == FORM_GATED;
@@ -381,6 +411,7 @@ __global__ void __launch_bounds__(kSweepThreads) sweep_kernel(const SweepArgs a)
         }
     };
 
+    constexpr bool PREFETCH = MFC_PREFETCH != 0;
     bool bad = false;
     R smax = R(0);
     unsigned n_gated = 0, n_fallback = 0, n_cells = 0;
@@ -402,6 +433,10 @@ __global__ void __launch_bounds__(kSweepThreads) sweep_kernel(const SweepArgs a)
     for (int f = 0; f < NEQ; ++f) vmPrev[f] = Fprev[f] = R(0);
 
     for (int j = s0 - 1; j <= s1; ++j) {
+        // the cell that enters the window at the end of this iteration: its
+        // loads are issued now and complete under this iteration's arithmetic
+        R vnext[NL];
+        if (PREFETCH && j < s1) fetch(j + 3 - (s0 - 3), vnext);
         R vm[NEQ], vp[NEQ];
         bool use_weno = true;
         if constexpr (GATED) {
@@ -478,15 +513,19 @@ __global__ void __launch_bounds__(kSweepThreads) sweep_kernel(const SweepArgs a)
                     for (int f = 0; f < NEQ; ++f) {
                         R tot = NDIM > 1 ? acc[f * nc + c] + L[f] : L[f];
                         double qn = a.qn[f * nc + c];
-                        double dL = dt * double(tot);
+                        double totd, qkd;
+                        if constexpr (MIXED) totd = f2d_bits(tot);
+                        else totd = double(tot);
+                        double dL = dt * totd;
                         if (a.stage == 1) {
                             qnew[f] = qn + dL;
                         } else {
-                            double qk = double(qin[f * nc + c]);
+                            if constexpr (MIXED) qkd = f2d_bits(qin[f * nc + c]);
+                            else qkd = double(qin[f * nc + c]);
                             if (a.stage == 2)
-                                qnew[f] = 0.75 * qn + 0.25 * (qk + dL);
+                                qnew[f] = 0.75 * qn + 0.25 * (qkd + dL);
                             else
-                                qnew[f] = (1.0 / 3.0) * qn + (2.0 / 3.0) * (qk + dL);
+                                qnew[f] = (1.0 / 3.0) * qn + (2.0 / 3.0) * (qkd + dL);
                         }
                     }
                     if constexpr (!MIXED) {
@@ -505,10 +544,13 @@ __global__ void __launch_bounds__(kSweepThreads) sweep_kernel(const SweepArgs a)
                             smax = s > smax ? s : smax;
                         }
                     } else {
-                        float pnew = mixed_pressure<NDIM>(a.eos, qnew);
+                        float q32[NEQ];
+#pragma unroll
+                        for (int f = 0; f < NEQ; ++f) q32[f] = d2f_bits(qnew[f]);
+                        float pnew = mixed_pressure<NDIM>(a.eos, qnew, q32);
                         float* o32 = static_cast<float*>(a.stage == 3 ? a.qout2 : a.qout);
 #pragma unroll
-                        for (int f = 0; f < NEQ; ++f) o32[f * nc + c] = float(qnew[f]);
+                        for (int f = 0; f < NEQ; ++f) o32[f * nc + c] = q32[f];
                         o32[NEQ * nc + c] = pnew;
                         if (a.stage == 3) {
                             double* o64 = static_cast<double*>(a.qout);
@@ -516,7 +558,7 @@ __global__ void __launch_bounds__(kSweepThreads) sweep_kernel(const SweepArgs a)
                             for (int f = 0; f < NEQ; ++f) o64[f * nc + c] = qnew[f];
                             float v[NEQ], wn[NEQ];
 #pragma unroll
-                            for (int f = 0; f < NEQ; ++f) v[f] = float(qnew[f]);
+                            for (int f = 0; f < NEQ; ++f) v[f] = q32[f];
                             v[IE] = pnew;
                             to_prim<NDIM>(er, v, wn);
                             R s = cell_wavespeed<NDIM, float>(er, wn, a.inv_dx, bad);
@@ -537,10 +579,9 @@ __global__ void __launch_bounds__(kSweepThreads) sweep_kernel(const SweepArgs a)
             for (int k = 0; k < 4; ++k)
 #pragma unroll
                 for (int f = 0; f < NEQ; ++f) W[k][f] = W[k + 1][f];
-            R v[NL];
-            fetch(j + 3 - (s0 - 3), v);
-            if constexpr (EXACT) exact::cons_to_prim<NDIM>(a.eos, v, W[4]);
-            else to_prim<NDIM>(er, v, W[4]);
+            if (!PREFETCH) fetch(j + 3 - (s0 - 3), vnext);
+            if constexpr (EXACT) exact::cons_to_prim<NDIM>(a.eos, vnext, W[4]);
+            else to_prim<NDIM>(er, vnext, W[4]);
             bad |= !(W[4][0] + W[4][1] > R(0));
         }
     }

@@ -294,3 +294,13 @@ def test_device_arrays_and_timing_mode():
     kt = s1.kernel_times()
     assert kt["sweep_z"][1] == 12 and kt["step_begin"][1] == 4
     assert s1.launches_per_step() == 10
+
+
+def test_integer_conversions_match_hardware():
+    """The mixed form's integer-pipe float<->double conversions return the
+    hardware conversions' bits on 16M pseudo-random patterns."""
+    import ctypes
+    from paper_2409_10729_gb300 import mfc
+    bad = ctypes.c_longlong(-1)
+    assert mfc.lib().mfc_selfcheck_conversions(1 << 24, 2409, ctypes.byref(bad)) == 0
+    assert bad.value == 0
