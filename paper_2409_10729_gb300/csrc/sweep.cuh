@@ -185,7 +185,8 @@ using FormReal = typename std::conditional<FORM == FORM_MIXED || FORM == FORM_GA
 struct GateSmem {
     unsigned w1f[4][32];       // layer-1 B fragments, per n-tile and lane
     unsigned w2f[2][4][32][2]; // layer-2 B fragments, per k-tile, n-tile, lane
-    float b1[32], b2[32], w3[32], b3;
+    unsigned w3f[2][32][2];    // layer-3 B fragments (w3 in every column), per k-tile, lane
+    float b1[32], b2[32], b3;
 };
 
 __device__ __forceinline__ unsigned pack_half2(float lo, float hi) {
@@ -193,7 +194,17 @@ __device__ __forceinline__ unsigned pack_half2(float lo, float hi) {
     return *reinterpret_cast<unsigned*>(&h);
 }
 
+// max(lo, 0) and max(hi, 0) rounded to f16 and packed (lo in the low half).
+__device__ __forceinline__ unsigned relu_half2(float lo, float hi) {
+    unsigned r;
+    asm("cvt.rn.relu.f16x2.f32 %0, %1, %2;\n" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
+}
+
 // Fill the block's fragment tables from the 1281 weights (all threads).
+// Fragment layouts follow the PTX m16n8k8 / m16n8k16 f16 B operand: lane
+// (g = lane / 4, t = lane % 4) holds column n = g, rows k = 2t, 2t + 1 (and
+// k = 2t + 8, 2t + 9 in its second register for k16).
 __device__ __forceinline__ void gate_fill(GateSmem& g, const float* __restrict__ w) {
     constexpr int OB1 = 160, OW2 = 192, OB2 = 1216, OW3 = 1248, OB3 = 1280;
     for (int i = threadIdx.x; i < 4 * 32; i += blockDim.x) {
@@ -208,12 +219,38 @@ __device__ __forceinline__ void gate_fill(GateSmem& g, const float* __restrict__
         g.w2f[kt][nt][l][0] = pack_half2(w[OW2 + n * 32 + k], w[OW2 + n * 32 + k + 1]);
         g.w2f[kt][nt][l][1] = pack_half2(w[OW2 + n * 32 + k + 8], w[OW2 + n * 32 + k + 9]);
     }
+    for (int i = threadIdx.x; i < 2 * 32; i += blockDim.x) {
+        int kt = i / 32, l = i % 32, t = l % 4;
+        int k = kt * 16 + 2 * t;
+        g.w3f[kt][l][0] = pack_half2(w[OW3 + k], w[OW3 + k + 1]);
+        g.w3f[kt][l][1] = pack_half2(w[OW3 + k + 8], w[OW3 + k + 9]);
+    }
     for (int i = threadIdx.x; i < 32; i += blockDim.x) {
         g.b1[i] = w[OB1 + i];
         g.b2[i] = w[OB2 + i];
-        g.w3[i] = w[OW3 + i];
     }
     if (threadIdx.x == 0) g.b3 = w[OB3];
+}
+
+// Shared-memory loads the compiler keeps at their place of use: the gate's
+// weight fragments are re-read per evaluation instead of being held in
+// registers across the whole pencil.
+__device__ __forceinline__ unsigned lds_u32(const void* p) {
+    unsigned v, a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ld.shared.b32 %0, [%1];\n" : "=r"(v) : "r"(a));
+    return v;
+}
+
+__device__ __forceinline__ uint2 lds_u64(const void* p) {
+    uint2 v;
+    unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    asm volatile("ld.shared.v2.b32 {%0,%1}, [%2];\n" : "=r"(v.x), "=r"(v.y) : "r"(a));
+    return v;
+}
+
+__device__ __forceinline__ void ldsm_x2(unsigned& r0, unsigned& r1, const void* row) {
+    unsigned a = (unsigned)__cvta_generic_to_shared(row);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n" : "=r"(r0), "=r"(r1) : "r"(a));
 }
 
 __device__ __forceinline__ void ldsm_x4(unsigned& r0, unsigned& r1, unsigned& r2, unsigned& r3, const void* row) {
@@ -223,12 +260,22 @@ __device__ __forceinline__ void ldsm_x4(unsigned& r0, unsigned& r1, unsigned& r2
                  : "r"(a));
 }
 
-__device__ __forceinline__ void mma_k8(float* d, unsigned a0, unsigned a1, unsigned b0) {
-    asm("mma.sync.aligned.m16n8k8.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5}, {%6}, {%0,%1,%2,%3};\n"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a0), "r"(a1), "r"(b0));
+// d = a b + c, f16 operands, f32 accumulate (c and d distinct).
+__device__ __forceinline__ void mma_k8(float* d, unsigned a0, unsigned a1, unsigned b0, float c0, float c1) {
+    asm("mma.sync.aligned.m16n8k8.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5}, {%6}, {%7,%8,%7,%8};\n"
+        : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
+        : "r"(a0), "r"(a1), "r"(b0), "f"(c0), "f"(c1));
 }
 
+__device__ __forceinline__ void mma_k16c(float* d, unsigned a0, unsigned a1, unsigned a2, unsigned a3, unsigned b0,
+                                         unsigned b1, float c0, float c1) {
+    asm("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%10,%11,%10,%11};\n"
+        : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1), "f"(c0), "f"(c1));
+}
+
+// d += a b, f16 operands, f32 accumulate.
 __device__ __forceinline__ void mma_k16(float* d, unsigned a0, unsigned a1, unsigned a2, unsigned a3, unsigned b0,
                                         unsigned b1) {
     asm("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
@@ -240,6 +287,11 @@ __device__ __forceinline__ void mma_k16(float* d, unsigned a0, unsigned a1, unsi
 // Logits of this lane's cell for both sensors.  xr, xp: the normalised
 // density and pressure stencils of the lane's cell; tile: this warp's 1 KB
 // A tile (64 rows x 8 halves).  Must be called by all 32 lanes together.
+// All three layers run as m16n8 MMAs over four 16-row tiles (rows 0-31: the
+// warp's density stencils, 32-63: its pressure stencils).  Biases enter as
+// the accumulator input; ReLU and the f16 rounding of the hidden activations
+// are one conversion, and the accumulator layout of one layer is the A
+// fragment layout of the next, so the activations never leave registers.
 __device__ __forceinline__ void gate_logits(const GateSmem& g, uint4* tile, const float* xr, const float* xp,
                                             float& zr, float& zp) {
     const int lane = threadIdx.x & 31, t = lane & 3;
@@ -247,54 +299,43 @@ __device__ __forceinline__ void gate_logits(const GateSmem& g, uint4* tile, cons
     tile[lane] = make_uint4(pack_half2(xr[0], xr[1]), pack_half2(xr[2], xr[3]), pack_half2(xr[4], 0.f), 0u);
     tile[32 + lane] = make_uint4(pack_half2(xp[0], xp[1]), pack_half2(xp[2], xp[3]), pack_half2(xp[4], 0.f), 0u);
     __syncwarp();
-    unsigned a[4][2];   // layer-1 A fragments of the 4 m-tiles (rows 16 mt .. 16 mt + 15)
-    ldsm_x4(a[0][0], a[0][1], a[1][0], a[1][1], tile + lane);
-    ldsm_x4(a[2][0], a[2][1], a[3][0], a[3][1], tile + 32 + lane);
-    float part[4][2];   // partial logits of rows gq and gq + 8 of each m-tile
-#pragma unroll
-    for (int mt = 0; mt < 4; ++mt) {
-        unsigned a2[2][4];
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt) {
-            float c[4] = {0.f, 0.f, 0.f, 0.f};
-            mma_k8(c, a[mt][0], a[mt][1], g.w1f[nt][lane]);
-            const float bl = g.b1[nt * 8 + 2 * t], bh = g.b1[nt * 8 + 2 * t + 1];
-            unsigned lo = pack_half2(fmaxf(c[0] + bl, 0.f), fmaxf(c[1] + bh, 0.f));
-            unsigned hi = pack_half2(fmaxf(c[2] + bl, 0.f), fmaxf(c[3] + bh, 0.f));
-            a2[nt >> 1][(nt & 1) * 2 + 0] = lo;
-            a2[nt >> 1][(nt & 1) * 2 + 1] = hi;
-        }
-        float p0 = 0.f, p1 = 0.f;
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt) {
-            float c[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-            for (int kt = 0; kt < 2; ++kt)
-                mma_k16(c, a2[kt][0], a2[kt][1], a2[kt][2], a2[kt][3], g.w2f[kt][nt][lane][0], g.w2f[kt][nt][lane][1]);
-            const int n0 = nt * 8 + 2 * t;
-            p0 = fmaf(fmaxf(c[0] + g.b2[n0], 0.f), g.w3[n0], p0);
-            p0 = fmaf(fmaxf(c[1] + g.b2[n0 + 1], 0.f), g.w3[n0 + 1], p0);
-            p1 = fmaf(fmaxf(c[2] + g.b2[n0], 0.f), g.w3[n0], p1);
-            p1 = fmaf(fmaxf(c[3] + g.b2[n0 + 1], 0.f), g.w3[n0 + 1], p1);
-        }
-        p0 += __shfl_xor_sync(0xffffffffu, p0, 1);
-        p0 += __shfl_xor_sync(0xffffffffu, p0, 2);
-        p1 += __shfl_xor_sync(0xffffffffu, p1, 1);
-        p1 += __shfl_xor_sync(0xffffffffu, p1, 2);
-        part[mt][0] = p0 + g.b3;
-        part[mt][1] = p1 + g.b3;
-    }
-    // sample row r of m-tile mt sits in fragment group r % 8, half r / 8; the
-    // lane's own rows are (mt = lane / 16, r = lane % 16) for the density and
-    // (mt = 2 + lane / 16, same r) for the pressure
+    // sample row r of m-tile mt ends in fragment group r % 8, half r / 8 (c[0]
+    // or c[2]); the lane's own rows are (mt = lane / 16, r = lane % 16) for
+    // the density and (mt = 2 + lane / 16, same r) for the pressure
     const int src = 4 * (lane & 7), half = (lane >> 3) & 1, hi16 = lane >> 4;
-    float v[4][2];
+#pragma unroll 1
+    for (int mt = 0; mt < 4; ++mt) {
+        unsigned a0, a1, h1[2][4], h2[2][4];
+        ldsm_x2(a0, a1, tile + 16 * mt + (lane & 15));
 #pragma unroll
-    for (int mt = 0; mt < 4; ++mt)
+        for (int nt = 0; nt < 4; ++nt) {
+            const uint2 bb = lds_u64(&g.b1[nt * 8 + 2 * t]);
+            float c[4];
+            mma_k8(c, a0, a1, lds_u32(&g.w1f[nt][lane]), __uint_as_float(bb.x), __uint_as_float(bb.y));
+            h1[nt >> 1][(nt & 1) * 2 + 0] = relu_half2(c[0], c[1]);
+            h1[nt >> 1][(nt & 1) * 2 + 1] = relu_half2(c[2], c[3]);
+        }
 #pragma unroll
-        for (int h = 0; h < 2; ++h) v[mt][h] = __shfl_sync(0xffffffffu, part[mt][h], src);
-    zr = hi16 ? (half ? v[1][1] : v[1][0]) : (half ? v[0][1] : v[0][0]);
-    zp = hi16 ? (half ? v[3][1] : v[3][0]) : (half ? v[2][1] : v[2][0]);
+        for (int nt = 0; nt < 4; ++nt) {
+            const uint2 bb = lds_u64(&g.b2[nt * 8 + 2 * t]);
+            const uint2 w0 = lds_u64(&g.w2f[0][nt][lane][0]), w1 = lds_u64(&g.w2f[1][nt][lane][0]);
+            float c[4];
+            mma_k16c(c, h1[0][0], h1[0][1], h1[0][2], h1[0][3], w0.x, w0.y, __uint_as_float(bb.x),
+                     __uint_as_float(bb.y));
+            mma_k16(c, h1[1][0], h1[1][1], h1[1][2], h1[1][3], w1.x, w1.y);
+            h2[nt >> 1][(nt & 1) * 2 + 0] = relu_half2(c[0], c[1]);
+            h2[nt >> 1][(nt & 1) * 2 + 1] = relu_half2(c[2], c[3]);
+        }
+        const uint2 w0 = lds_u64(&g.w3f[0][lane][0]), w1 = lds_u64(&g.w3f[1][lane][0]);
+        const float b3 = __uint_as_float(lds_u32(&g.b3));
+        float c[4];
+        mma_k16c(c, h2[0][0], h2[0][1], h2[0][2], h2[0][3], w0.x, w0.y, b3, b3);
+        mma_k16(c, h2[1][0], h2[1][1], h2[1][2], h2[1][3], w1.x, w1.y);
+        const float v0 = __shfl_sync(0xffffffffu, c[0], src), v1 = __shfl_sync(0xffffffffu, c[2], src);
+        const float v = half ? v1 : v0;
+        if (mt == hi16) zr = v;
+        if (mt == 2 + hi16) zp = v;
+    }
 }
 
 // Normalised sensor stencil (v_k - v_2) / (max_k |v_k - v_2| + 1e-12).
