@@ -81,7 +81,8 @@ cudaError_t run_fma_probe(int fp64, double* tflops, cudaStream_t s);
 // thread-block size of every sweep launch
 constexpr int kSweepThreads = 128;
 // Resident 128-thread sweep blocks per SM requested from the register
-// allocator, per form (1: up to 255 registers a thread; 2: 255; 3: 168;
+// allocator, per form, and for the FP32 forms separately for the last sweep
+// with its stage update (1: up to 255 registers a thread; 2: 255; 3: 168;
 // 4: 128).  The FP64 forms are bound by the FP64 pipe and lose nothing at
 // two blocks; the FP32 forms need the warps to cover their load latency.
 #ifndef MFC_MIN_BLOCKS_FP64
@@ -90,8 +91,14 @@ constexpr int kSweepThreads = 128;
 #ifndef MFC_MIN_BLOCKS_MIXED
 #define MFC_MIN_BLOCKS_MIXED 4
 #endif
+#ifndef MFC_MIN_BLOCKS_MIXED_RK
+#define MFC_MIN_BLOCKS_MIXED_RK 3
+#endif
 #ifndef MFC_MIN_BLOCKS_GATED
-#define MFC_MIN_BLOCKS_GATED 3
+#define MFC_MIN_BLOCKS_GATED 2
+#endif
+#ifndef MFC_MIN_BLOCKS_GATED_RK
+#define MFC_MIN_BLOCKS_GATED_RK 2
 #endif
 // 1: the sweeps issue the loads of the cell entering the stencil window at the
 // top of each step along the pencil (they complete under that step's

@@ -367,13 +367,15 @@ __device__ __forceinline__ bool face_ok(const EosR<float>& e, const float* w) {
     return (w[0] + w[1] > 0.f) && (a1 >= 0.f) && (a1 <= 1.f) && ((G + 1.f) * w[FL::IE] + Pi > 0.f);
 }
 
-template <int FORM>
+template <int FORM, int MODE>
 constexpr int sweep_min_blocks() {
-    return FORM == FORM_MIXED ? MFC_MIN_BLOCKS_MIXED : FORM == FORM_GATED ? MFC_MIN_BLOCKS_GATED : MFC_MIN_BLOCKS_FP64;
+    return FORM == FORM_MIXED   ? (MODE == SW_LAST_RK ? MFC_MIN_BLOCKS_MIXED_RK : MFC_MIN_BLOCKS_MIXED)
+           : FORM == FORM_GATED ? (MODE == SW_LAST_RK ? MFC_MIN_BLOCKS_GATED_RK : MFC_MIN_BLOCKS_GATED)
+                                : MFC_MIN_BLOCKS_FP64;
 }
 
 template <int NDIM, int DIR, int MODE, int FORM>
-__global__ void __launch_bounds__(kSweepThreads, sweep_min_blocks<FORM>()) sweep_kernel(const SweepArgs a) {
+__global__ void __launch_bounds__(kSweepThreads, sweep_min_blocks<FORM, MODE>()) sweep_kernel(const SweepArgs a) {
     using R = FormReal<FORM>;
     constexpr bool EXACT = FORM == FORM_FP64_EXACT;
     constexpr bool GATED = FORM == FORM_GATED;
@@ -453,6 +455,7 @@ __global__ void __launch_bounds__(kSweepThreads, sweep_min_blocks<FORM>()) sweep
     };
 
     constexpr bool PREFETCH = MFC_PREFETCH != 0;
+    constexpr bool EPI_PREFETCH = PREFETCH && MIXED;
     bool bad = false;
     R smax = R(0);
     unsigned n_gated = 0, n_fallback = 0, n_cells = 0;
@@ -478,6 +481,28 @@ __global__ void __launch_bounds__(kSweepThreads, sweep_min_blocks<FORM>()) sweep
         // loads are issued now and complete under this iteration's arithmetic
         R vnext[NL];
         if (PREFETCH && j < s1) fetch(j + 3 - (s0 - 3), vnext);
+        // the FP32 forms also issue the stage-update operands of the cell
+        // this iteration completes (cell j - 1) here, ahead of the stencil work
+        R accp[NEQ], qkp[NEQ];
+        double qnp[NEQ];
+        if constexpr (EPI_PREFETCH) {
+            if (j > s0) {
+                const long long c = base + (long long)(j - 1) * ss;
+                if constexpr (NDIM > 1 && MODE != SW_FIRST) {
+                    const R* acc = static_cast<const R*>(a.acc);
+#pragma unroll
+                    for (int f = 0; f < NEQ; ++f) accp[f] = acc[f * nc + c];
+                }
+                if constexpr (MODE == SW_LAST_RK) {
+#pragma unroll
+                    for (int f = 0; f < NEQ; ++f) qnp[f] = __ldg(a.qn + f * nc + c);
+                    if (a.stage != 1) {
+#pragma unroll
+                        for (int f = 0; f < NEQ; ++f) qkp[f] = __ldg(qin + f * nc + c);
+                    }
+                }
+            }
+        }
         R vm[NEQ], vp[NEQ];
         bool use_weno = true;
         if constexpr (GATED) {
@@ -538,13 +563,13 @@ __global__ void __launch_bounds__(kSweepThreads, sweep_min_blocks<FORM>()) sweep
                 } else if constexpr (MODE == SW_MID) {
                     R* acc = static_cast<R*>(a.acc);
 #pragma unroll
-                    for (int f = 0; f < NEQ; ++f) acc[f * nc + c] = acc[f * nc + c] + L[f];
+                    for (int f = 0; f < NEQ; ++f) acc[f * nc + c] = (EPI_PREFETCH ? accp[f] : acc[f * nc + c]) + L[f];
                 } else if constexpr (MODE == SW_LAST_RHS) {
                     const R* acc = static_cast<const R*>(a.acc);
                     double* out = static_cast<double*>(a.qout);
 #pragma unroll
                     for (int f = 0; f < NEQ; ++f) {
-                        R tot = NDIM > 1 ? acc[f * nc + c] + L[f] : L[f];
+                        R tot = NDIM > 1 ? (EPI_PREFETCH ? accp[f] : acc[f * nc + c]) + L[f] : L[f];
                         out[f * nc + c] = double(tot);
                     }
                 } else {  // SW_LAST_RK
@@ -552,8 +577,8 @@ __global__ void __launch_bounds__(kSweepThreads, sweep_min_blocks<FORM>()) sweep
                     double qnew[NEQ];
 #pragma unroll
                     for (int f = 0; f < NEQ; ++f) {
-                        R tot = NDIM > 1 ? acc[f * nc + c] + L[f] : L[f];
-                        double qn = a.qn[f * nc + c];
+                        R tot = NDIM > 1 ? (EPI_PREFETCH ? accp[f] : acc[f * nc + c]) + L[f] : L[f];
+                        double qn = EPI_PREFETCH ? qnp[f] : a.qn[f * nc + c];
                         double totd, qkd;
                         if constexpr (MIXED) totd = f2d_bits(tot);
                         else totd = double(tot);
@@ -561,7 +586,7 @@ __global__ void __launch_bounds__(kSweepThreads, sweep_min_blocks<FORM>()) sweep
                         if (a.stage == 1) {
                             qnew[f] = qn + dL;
                         } else {
-                            if constexpr (MIXED) qkd = f2d_bits(qin[f * nc + c]);
+                            if constexpr (MIXED) qkd = f2d_bits(EPI_PREFETCH ? qkp[f] : qin[f * nc + c]);
                             else qkd = double(qin[f * nc + c]);
                             if (a.stage == 2)
                                 qnew[f] = 0.75 * qn + 0.25 * (qkd + dL);
