@@ -80,16 +80,21 @@ cudaError_t run_fma_probe(int fp64, double* tflops, cudaStream_t s);
 
 // thread-block size of every sweep launch
 constexpr int kSweepThreads = 128;
-// Resident 128-thread sweep blocks per SM requested from the register
-// allocator, per form, and for the FP32 forms separately for the last sweep
-// with its stage update (1: up to 255 registers a thread; 2: 255; 3: 168;
-// 4: 128).  The FP64 forms are bound by the FP64 pipe and lose nothing at
+// threads per block of the sweep along direction d
+__host__ __device__ constexpr int sweep_threads(int dir) { return dir == 0 ? 64 : kSweepThreads; }
+// Resident sweep blocks per SM requested from the register allocator,
+// counted in 128-thread blocks, per form, and for the FP32 forms separately
+// for the x sweep and for the last sweep with its stage update (1: up to 255
+// registers a thread; 2: 255; 3: 168; 4: 128).  The FP64 forms are bound by the FP64 pipe and lose nothing at
 // two blocks; the FP32 forms need the warps to cover their load latency.
 #ifndef MFC_MIN_BLOCKS_FP64
 #define MFC_MIN_BLOCKS_FP64 1
 #endif
 #ifndef MFC_MIN_BLOCKS_MIXED
 #define MFC_MIN_BLOCKS_MIXED 4
+#endif
+#ifndef MFC_MIN_BLOCKS_MIXED_X
+#define MFC_MIN_BLOCKS_MIXED_X 3
 #endif
 #ifndef MFC_MIN_BLOCKS_MIXED_RK
 #define MFC_MIN_BLOCKS_MIXED_RK 3

@@ -168,9 +168,25 @@ __device__ __forceinline__ R cell_wavespeed(const EosR<R>& e, const R* w, const 
 // element per row so that the 32 lanes read 32 different banks.
 template <typename R>
 struct XStage {
-    static constexpr int CH = 32 / sizeof(R);
-    static constexpr int PITCH = CH + 1;
+    static constexpr int CH = 32 / sizeof(R);   // cells per staged chunk along x (one 32-byte sector)
+    static constexpr int PITCH = CH + 1;        // padded row pitch (conflict-free reads)
 };
+
+// Asynchronous 4- or 8-byte global -> shared copies (sm_80+ cp.async), one
+// commit group per staged chunk.
+template <typename R>
+__device__ __forceinline__ void cp_async_elem(R* smem, const R* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    if constexpr (sizeof(R) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+__device__ __forceinline__ int floor_div(int j, int d) { return j >= 0 ? j / d : -((-j + d - 1) / d); }
 
 template <int FORM>
 using FormReal = typename std::conditional<FORM == FORM_MIXED || FORM == FORM_GATED, float, double>::type;
@@ -367,15 +383,22 @@ __device__ __forceinline__ bool face_ok(const EosR<float>& e, const float* w) {
     return (w[0] + w[1] > 0.f) && (a1 >= 0.f) && (a1 <= 1.f) && ((G + 1.f) * w[FL::IE] + Pi > 0.f);
 }
 
-template <int FORM, int MODE>
+// Minimum resident blocks for the register allocator, in blocks of the
+// sweep's own size (x sweeps run 64-thread blocks so that their two staging
+// buffers per warp fit the 48 KB of static shared memory of a block).
+template <int FORM, int MODE, int DIR>
 constexpr int sweep_min_blocks() {
-    return FORM == FORM_MIXED   ? (MODE == SW_LAST_RK ? MFC_MIN_BLOCKS_MIXED_RK : MFC_MIN_BLOCKS_MIXED)
-           : FORM == FORM_GATED ? (MODE == SW_LAST_RK ? MFC_MIN_BLOCKS_GATED_RK : MFC_MIN_BLOCKS_GATED)
-                                : MFC_MIN_BLOCKS_FP64;
+    constexpr int per128 = FORM == FORM_MIXED   ? (MODE == SW_LAST_RK ? MFC_MIN_BLOCKS_MIXED_RK
+                                                   : DIR == 0         ? MFC_MIN_BLOCKS_MIXED_X
+                                                                      : MFC_MIN_BLOCKS_MIXED)
+                           : FORM == FORM_GATED ? (MODE == SW_LAST_RK ? MFC_MIN_BLOCKS_GATED_RK : MFC_MIN_BLOCKS_GATED)
+                                                : MFC_MIN_BLOCKS_FP64;
+    return per128 * 128 / sweep_threads(DIR);
 }
 
 template <int NDIM, int DIR, int MODE, int FORM>
-__global__ void __launch_bounds__(kSweepThreads, sweep_min_blocks<FORM, MODE>()) sweep_kernel(const SweepArgs a) {
+__global__ void __launch_bounds__(sweep_threads(DIR), sweep_min_blocks<FORM, MODE, DIR>())
+sweep_kernel(const SweepArgs a) {
     using R = FormReal<FORM>;
     constexpr bool EXACT = FORM == FORM_FP64_EXACT;
     constexpr bool GATED = FORM == FORM_GATED;
@@ -385,8 +408,9 @@ __global__ void __launch_bounds__(kSweepThreads, sweep_min_blocks<FORM, MODE>())
     constexpr int NL = LS::N;
     constexpr bool MIXED = FORM == FORM_MIXED || FORM == FORM_GATED;
     constexpr int CH = XStage<R>::CH, PITCH = XStage<R>::PITCH;
-    constexpr int WARPS = kSweepThreads / 32;
-    __shared__ R stage[DIR == 0 ? WARPS * NL * 32 * PITCH : 1];
+    constexpr int WARPS = sweep_threads(DIR) / 32;
+    constexpr int STAGE = NL * 32 * PITCH;   // one chunk buffer of one warp
+    __shared__ R stage[DIR == 0 ? WARPS * 2 * STAGE : 1];
     __shared__ GateSmem gsm[GATED ? 1 : 0 + 1];
     __shared__ uint4 gtile[GATED ? WARPS * 64 : 1];
     if constexpr (GATED) {
@@ -423,9 +447,29 @@ __global__ void __launch_bounds__(kSweepThreads, sweep_min_blocks<FORM, MODE>())
     const R eps = R(a.eps);
     const EosR<R> er(a.eos);
     const R* __restrict__ qin = static_cast<const R*>(a.qin);
-    R* st = stage + (threadIdx.x >> 5) * (NL * 32 * PITCH);
 
-    // Values of loaded cell k (x-index s0 - 3 + k along the pencil) -> v[].
+    // Values of loaded cell k (index s0 - 3 + k along the pencil) -> v[].
+    // Along x the warp stages chunks of CH cells, aligned to multiples of CH,
+    // of its 32 rows through shared memory with cp.async, double-buffered:
+    // chunk m + 1 is requested when the pencil enters chunk m, so its copy
+    // runs under the CH cells of work on chunk m.  Calls must come in order
+    // of k (all lanes together).
+    R* st = stage + (threadIdx.x >> 5) * (2 * STAGE);
+    const int last_chunk = DIR == 0 ? floor_div(s1 + 2, CH) : 0;
+    auto stage_chunk = [&](int m) {
+        R* buf = st + (m & 1) * STAGE;
+        const int t = lane % CH;
+        const int xg = bc_index(m * CH + t, ns, a.periodic);
+#pragma unroll
+        for (int i = 0; i < CH; ++i) {
+            const int r = lane / CH + (32 / CH) * i;
+            const int row = min(chunk * 32 + r, na - 1);
+            const long long c = (long long)row * sa + (long long)b * sb + xg;
+#pragma unroll
+            for (int f = 0; f < NL; ++f) cp_async_elem(buf + (f * 32 + r) * PITCH + t, qin + LS::field(f) * nc + c);
+        }
+        cp_async_commit();
+    };
     auto fetch = [&](int k, R* v) {
         const int j = s0 - 3 + k;
         if constexpr (DIR != 0) {
@@ -433,24 +477,22 @@ __global__ void __launch_bounds__(kSweepThreads, sweep_min_blocks<FORM, MODE>())
 #pragma unroll
             for (int f = 0; f < NL; ++f) v[f] = __ldg(qin + LS::field(f) * nc + c);
         } else {
-            const int slot = k % CH;
-            if (slot == 0) {
-                // the warp stages cells j .. j+CH-1 of its 32 rows
-                __syncwarp();
-                const int t = lane % CH;
-                const int xg = bc_index(j + t, ns, a.periodic);
-#pragma unroll
-                for (int i = 0; i < CH; ++i) {
-                    const int r = lane / CH + (32 / CH) * i;
-                    const int row = min(chunk * 32 + r, na - 1);
-                    const long long c = (long long)row * sa + (long long)b * sb + xg;
-#pragma unroll
-                    for (int f = 0; f < NL; ++f) st[(f * 32 + r) * PITCH + t] = __ldg(qin + LS::field(f) * nc + c);
+            const int m = floor_div(j, CH);
+            const int slot = j - m * CH;
+            if (k == 0 || slot == 0) {
+                if (k == 0) stage_chunk(m);
+                __syncwarp();   // every lane is done with chunk m - 1 (buffer of m + 1)
+                if (m + 1 <= last_chunk) {
+                    stage_chunk(m + 1);
+                    cp_async_wait<1>();   // chunk m has landed
+                } else {
+                    cp_async_wait<0>();
                 }
                 __syncwarp();
             }
+            const R* buf = st + (m & 1) * STAGE;
 #pragma unroll
-            for (int f = 0; f < NL; ++f) v[f] = st[(f * 32 + lane) * PITCH + slot];
+            for (int f = 0; f < NL; ++f) v[f] = buf[(f * 32 + lane) * PITCH + slot];
         }
     };
 
@@ -680,26 +722,30 @@ __global__ void __launch_bounds__(kSweepThreads, sweep_min_blocks<FORM, MODE>())
 
 // Launch one sweep: the valid (direction, mode) pairs are x FIRST, y MID
 // (3-D), and LAST_RK / LAST_RHS on the last direction.
+template <int NDIM, int DIR, int MODE, int FORM>
+cudaError_t launch_one(long long warps, const SweepArgs& a, cudaStream_t s) {
+    constexpr int T = sweep_threads(DIR);
+    const long long blocks = (warps * 32 + T - 1) / T;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    sweep_kernel<NDIM, DIR, MODE, FORM><<<(unsigned)blocks, T, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
 template <int NDIM, int FORM>
 cudaError_t launch_sweep_t(int dir, int mode, const SweepArgs& a, cudaStream_t s) {
-    long long warps = sweep_warps(dir, a.n, a.seg);
-    long long blocks = (warps * 32 + kSweepThreads - 1) / kSweepThreads;
-    if (blocks <= 0) return cudaSuccess;
-    if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    dim3 grid((unsigned)blocks), block(kSweepThreads);
+    const long long warps = sweep_warps(dir, a.n, a.seg);
+    if (warps <= 0) return cudaSuccess;
     constexpr int LAST = NDIM - 1;
     if (dir == 0 && mode == SW_FIRST && NDIM > 1) {
-        if constexpr (NDIM > 1) sweep_kernel<NDIM, 0, SW_FIRST, FORM><<<grid, block, 0, s>>>(a);
+        if constexpr (NDIM > 1) return launch_one<NDIM, 0, SW_FIRST, FORM>(warps, a, s);
     } else if (dir == 1 && mode == SW_MID && NDIM == 3) {
-        if constexpr (NDIM == 3) sweep_kernel<NDIM, 1, SW_MID, FORM><<<grid, block, 0, s>>>(a);
+        if constexpr (NDIM == 3) return launch_one<NDIM, 1, SW_MID, FORM>(warps, a, s);
     } else if (dir == LAST && mode == SW_LAST_RK) {
-        sweep_kernel<NDIM, LAST, SW_LAST_RK, FORM><<<grid, block, 0, s>>>(a);
+        return launch_one<NDIM, LAST, SW_LAST_RK, FORM>(warps, a, s);
     } else if (dir == LAST && mode == SW_LAST_RHS) {
-        sweep_kernel<NDIM, LAST, SW_LAST_RHS, FORM><<<grid, block, 0, s>>>(a);
-    } else {
-        return cudaErrorInvalidValue;
+        return launch_one<NDIM, LAST, SW_LAST_RHS, FORM>(warps, a, s);
     }
-    return cudaGetLastError();
+    return cudaErrorInvalidValue;
 }
 
 template <int FORM>
