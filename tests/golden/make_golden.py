@@ -7,13 +7,15 @@ stated number of CFL-0.4 SSP-RK3 steps:
     refuse to compare if it differs),
   - the time advanced,
   - per-field max|q|, sum|q| and sum q over all cells,
-  - the full state at ~1000 sampled cells (random + domain corners/edges).
+  - the full state at ~1000 sampled cells (random + domain corners/edges),
+  - the SHA-256 of the whole final state (float64, [field][z][y][x]).
 Both the generators (only +, *, /, sqrt) and the oracle (-ffp-contract=off,
 IEEE division and square root, no libm transcendentals) are bit-reproducible
 across platforms, so these values hold on any machine.
 
   python tests/golden/make_golden.py column_1024x512   (about 6 minutes, one core)
-  python tests/golden/make_golden.py droplets_256      (about 80 minutes, one core)
+  python tests/golden/make_golden.py droplets_128      (about 13 minutes, one core)
+  python tests/golden/make_golden.py droplets_256      (about 115 minutes, one core)
 """
 import hashlib
 import json
@@ -32,6 +34,7 @@ from paper_2409_10729_gb300 import inputs as I  # noqa: E402
 
 CASES = {
     "column_1024x512": (lambda: I.shock_water_column(1024, 512), 500),
+    "droplets_128": (lambda: I.shock_droplets(128), 100),
     "droplets_256": (lambda: I.shock_droplets(256), 100),
 }
 
@@ -66,6 +69,7 @@ def make(name):
         "t_final": repr(t), "field_max_abs": [repr(float(v)) for v in np.abs(qf).max(1)],
         "field_l1": [repr(float(v)) for v in np.abs(qf).sum(1)],
         "field_sum": [repr(float(v)) for v in qf.sum(1)],
+        "state_sha256": hashlib.sha256(np.ascontiguousarray(q, dtype=np.float64).tobytes()).hexdigest(),
         "cells": cells.tolist(),
         "values": [[repr(float(v)) for v in qf[:, c]] for c in cells],
         "oracle_wall_s": round(wall, 1),

@@ -2,10 +2,11 @@
 results written by tests/golden/make_golden.py (which calls only the oracle).
 
 The 2-D shock / water-column case at 1024x512 for 500 steps and the 3-D
-shock / droplet case at 256^3 for 100 steps (CFL 0.4) are run on the GPU in
-the benchmark's launch configuration.  The FP64 form (reference operation
-order) must reproduce the time advanced, the per-field sums over all cells
-and the state at ~1000 sampled cells bit for bit.  The reorganised FP64 form
+shock / droplet case at 128^3 and 256^3 for 100 steps (CFL 0.4) are run on
+the GPU in the benchmark's launch configuration.  The FP64 form (reference
+operation order) must reproduce the time advanced, the per-field sums over
+all cells and the state at ~1000 sampled cells bit for bit, and, where the
+stored result carries it, the SHA-256 of the whole final state.  The reorganised FP64 form
 is checked against a bound set by the flows themselves: re-running the
 oracle with FMA contraction (a change of rounding only) moves the 2-D
 momentum by 6.6e-12 relative after 500 steps, so it is held to 5e-11
@@ -25,6 +26,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 TOL = 1e-12
 CASES = {
     "column_1024x512": lambda: I.shock_water_column(1024, 512),
+    "droplets_128": lambda: I.shock_droplets(128),
     "droplets_256": lambda: I.shock_droplets(256),
 }
 
@@ -65,6 +67,9 @@ def test_full_size_run_matches_stored_oracle(name, form):
     if form == "fp64":
         assert t == t_ref
         assert np.array_equal(qf[:, g["cells"]], ref)
+        if "state_sha256" in g:
+            assert hashlib.sha256(np.ascontiguousarray(q, dtype=np.float64).tobytes()).hexdigest() == \
+                g["state_sha256"], "whole final state differs from the oracle's"
         assert np.array_equal(np.abs(qf).max(1), np.array([float(v) for v in g["field_max_abs"]]))
         # numpy's summation order may differ between machines: sums to round-off
         assert np.all(np.abs(np.abs(qf).sum(1) - l1) <= 1e-14 * l1)
