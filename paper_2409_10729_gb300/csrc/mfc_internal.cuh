@@ -81,7 +81,7 @@ cudaError_t run_fma_probe(int fp64, double* tflops, cudaStream_t s);
 // thread-block size of every sweep launch
 constexpr int kSweepThreads = 128;
 // threads per block of the sweep along direction d
-__host__ __device__ constexpr int sweep_threads(int dir) { return dir == 0 ? 64 : kSweepThreads; }
+__host__ __device__ constexpr int sweep_threads(int dir) { return dir == 0 ? 32 : kSweepThreads; }
 // Resident sweep blocks per SM requested from the register allocator,
 // counted in 128-thread blocks, per form, and for the FP32 forms separately
 // for the x sweep and for the last sweep with its stage update (1: up to 255
@@ -94,7 +94,7 @@ __host__ __device__ constexpr int sweep_threads(int dir) { return dir == 0 ? 64 
 #define MFC_MIN_BLOCKS_MIXED 4
 #endif
 #ifndef MFC_MIN_BLOCKS_MIXED_X
-#define MFC_MIN_BLOCKS_MIXED_X 3
+#define MFC_MIN_BLOCKS_MIXED_X 2
 #endif
 #ifndef MFC_MIN_BLOCKS_MIXED_RK
 #define MFC_MIN_BLOCKS_MIXED_RK 3

@@ -384,8 +384,8 @@ __device__ __forceinline__ bool face_ok(const EosR<float>& e, const float* w) {
 }
 
 // Minimum resident blocks for the register allocator, in blocks of the
-// sweep's own size (x sweeps run 64-thread blocks so that their two staging
-// buffers per warp fit the 48 KB of static shared memory of a block).
+// sweep's own size (x sweeps run one-warp blocks so that the warp's two input
+// chunk buffers and its output tile fit the 48 KB of static shared memory).
 template <int FORM, int MODE, int DIR>
 constexpr int sweep_min_blocks() {
     constexpr int per128 = FORM == FORM_MIXED   ? (MODE == SW_LAST_RK ? MFC_MIN_BLOCKS_MIXED_RK
@@ -411,6 +411,11 @@ sweep_kernel(const SweepArgs a) {
     constexpr int WARPS = sweep_threads(DIR) / 32;
     constexpr int STAGE = NL * 32 * PITCH;   // one chunk buffer of one warp
     __shared__ R stage[DIR == 0 ? WARPS * 2 * STAGE : 1];
+    // x sweep writing the accumulator: the warp collects each sector's worth
+    // of cells (CH along x) of its 32 rows here and stores whole sectors
+    constexpr bool OSTAGE_ON = DIR == 0 && MODE == SW_FIRST;
+    constexpr int OSTAGE = NEQ * 32 * PITCH;
+    __shared__ R ostage[OSTAGE_ON ? WARPS * OSTAGE : 1];
     __shared__ GateSmem gsm[GATED ? 1 : 0 + 1];
     __shared__ uint4 gtile[GATED ? WARPS * 64 : 1];
     if constexpr (GATED) {
@@ -583,7 +588,7 @@ sweep_kernel(const SweepArgs a) {
             R F[NEQ], uf;
             if constexpr (EXACT) bad |= exact::hllc<NDIM, DIR>(a.eos, vmPrev, vp, F, uf);
             else bad |= hllc<NDIM, DIR, R>(er, vmPrev, vp, F, uf);
-            if (j > s0 && active) {
+            if (j > s0 && (active || OSTAGE_ON)) {
                 // cell i = j - 1 is complete: faces i-1/2 (Fprev) and i+1/2 (F)
                 R L[NEQ];
                 if constexpr (EXACT) {
@@ -598,7 +603,11 @@ sweep_kernel(const SweepArgs a) {
                     L[IA] += alphaCell * (uf - ufPrev) * inv_dx;
                 }
                 const long long c = base + (long long)(j - 1) * ss;
-                if constexpr (MODE == SW_FIRST) {
+                if constexpr (OSTAGE_ON) {
+                    R* o = ostage + (threadIdx.x >> 5) * OSTAGE + lane * PITCH + ((j - 1) & (CH - 1));
+#pragma unroll
+                    for (int f = 0; f < NEQ; ++f) o[f * 32 * PITCH] = L[f];
+                } else if constexpr (MODE == SW_FIRST) {
                     R* acc = static_cast<R*>(a.acc);
 #pragma unroll
                     for (int f = 0; f < NEQ; ++f) acc[f * nc + c] = L[f];
@@ -678,6 +687,29 @@ sweep_kernel(const SweepArgs a) {
 #pragma unroll
             for (int f = 0; f < NEQ; ++f) Fprev[f] = F[f];
             ufPrev = uf;
+            if constexpr (OSTAGE_ON) {
+                // cell i = j - 1 closes a sector (or the segment): the warp writes
+                // cells max(x0, s0) .. i of its rows, whole sectors per row
+                const int i = j - 1;
+                if (j > s0 && ((i & (CH - 1)) == CH - 1 || j == s1)) {
+                    __syncwarp();
+                    const int x0 = i & ~(CH - 1), lo = max(x0, s0);
+                    const int t = lane % CH, x = x0 + t;
+                    const R* o = ostage + (threadIdx.x >> 5) * OSTAGE;
+                    R* acc = static_cast<R*>(a.acc);
+#pragma unroll
+                    for (int k = 0; k < CH; ++k) {
+                        const int r = lane / CH + (32 / CH) * k;
+                        const int row = chunk * 32 + r;
+                        if (x >= lo && x <= i && row < na) {
+                            const long long cc = (long long)row * sa + (long long)b * sb + x;
+#pragma unroll
+                            for (int f = 0; f < NEQ; ++f) acc[f * nc + cc] = o[(f * 32 + r) * PITCH + t];
+                        }
+                    }
+                    __syncwarp();
+                }
+            }
         }
 #pragma unroll
         for (int f = 0; f < NEQ; ++f) vmPrev[f] = vm[f];
