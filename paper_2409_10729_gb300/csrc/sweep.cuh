@@ -508,6 +508,9 @@ sweep_kernel(const SweepArgs a) {
     unsigned n_gated = 0, n_fallback = 0, n_cells = 0;
     double dt = 0.0;
     if (MODE == SW_LAST_RK) dt = a.ctrl->dt;
+    // SSP-RK3 stage coefficients q^(k+1) = rk_a q^n + rk_b (q^(k) + dt L)
+    const double rk_a = a.stage == 2 ? 0.75 : (1.0 / 3.0), rk_b = a.stage == 2 ? 0.25 : (2.0 / 3.0);
+    const float bdt32 = float(a.stage == 1 ? dt : rk_b * dt);
 
     R W[5][NEQ];
 #pragma unroll
@@ -630,19 +633,27 @@ sweep_kernel(const SweepArgs a) {
                     for (int f = 0; f < NEQ; ++f) {
                         R tot = NDIM > 1 ? (EPI_PREFETCH ? accp[f] : acc[f * nc + c]) + L[f] : L[f];
                         double qn = EPI_PREFETCH ? qnp[f] : a.qn[f * nc + c];
-                        double totd, qkd;
-                        if constexpr (MIXED) totd = f2d_bits(tot);
-                        else totd = double(tot);
-                        double dL = dt * totd;
-                        if (a.stage == 1) {
-                            qnew[f] = qn + dL;
+                        if constexpr (MIXED) {
+                            // q^(k+1) = a q^n + b q^(k) + (b dt) L, accumulated in FP64
+                            // from the FP32 increment (b dt) L (L itself is FP32)
+                            const double inc = f2d_bits(bdt32 * tot);
+                            if (a.stage == 1) {
+                                qnew[f] = qn + inc;
+                            } else {
+                                const double qkd = f2d_bits(EPI_PREFETCH ? qkp[f] : qin[f * nc + c]);
+                                qnew[f] = __fma_rn(rk_a, qn, __fma_rn(rk_b, qkd, inc));
+                            }
                         } else {
-                            if constexpr (MIXED) qkd = f2d_bits(EPI_PREFETCH ? qkp[f] : qin[f * nc + c]);
-                            else qkd = double(qin[f * nc + c]);
-                            if (a.stage == 2)
-                                qnew[f] = 0.75 * qn + 0.25 * (qkd + dL);
-                            else
-                                qnew[f] = (1.0 / 3.0) * qn + (2.0 / 3.0) * (qkd + dL);
+                            double dL = dt * double(tot);
+                            if (a.stage == 1) {
+                                qnew[f] = qn + dL;
+                            } else {
+                                double qkd = double(qin[f * nc + c]);
+                                if (a.stage == 2)
+                                    qnew[f] = 0.75 * qn + 0.25 * (qkd + dL);
+                                else
+                                    qnew[f] = (1.0 / 3.0) * qn + (2.0 / 3.0) * (qkd + dL);
+                            }
                         }
                     }
                     if constexpr (!MIXED) {
