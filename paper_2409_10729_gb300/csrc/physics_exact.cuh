@@ -90,13 +90,21 @@ __device__ __forceinline__ double sound2(double G, double Pi, double rho, double
 // WENO5-JS: left-biased value at i+1/2 and right-biased value at i-1/2 from
 // v0..v4 = v_{i-2}..v_{i+2}; weights a_k = d_k/(eps+beta_k)^2, omega_k = a_k/sum(a),
 // candidate values (.)/6, face value sum omega_k p_k.
+//
+// Products by a power of two (2, 4, 1/4) are exact, so RN(RN(2 v) + x) equals
+// the single fused RN(2 v + x): those sums are written as FMAs (fma2 below),
+// which changes no result bit (barring a product in the subnormal range,
+// below 2^-1022, that a scaling by 1/4 would round).
+__device__ __forceinline__ double fma2(double k, double v, double x) { return __fma_rn(k, v, x); }
+
 __device__ __forceinline__ void weno5(double eps, double v0, double v1, double v2, double v3, double v4,
                                       double& vm, double& vp) {
     const double c13 = 13.0 / 12.0;
     const double r6 = 1.0 / 6.0;  // RN(1/6)
-    double b0 = c13 * sq(v0 - 2.0 * v1 + v2) + 0.25 * sq(v0 - 4.0 * v1 + 3.0 * v2);
-    double b1 = c13 * sq(v1 - 2.0 * v2 + v3) + 0.25 * sq(v1 - v3);
-    double b2 = c13 * sq(v2 - 2.0 * v3 + v4) + 0.25 * sq(3.0 * v2 - 4.0 * v3 + v4);
+    // b0 = c13 (v0 - 2 v1 + v2)^2 + 1/4 (v0 - 4 v1 + 3 v2)^2, and likewise b1, b2
+    double b0 = fma2(0.25, sq(fma2(-4.0, v1, v0) + 3.0 * v2), c13 * sq(fma2(-2.0, v1, v0) + v2));
+    double b1 = fma2(0.25, sq(v1 - v3), c13 * sq(fma2(-2.0, v2, v1) + v3));
+    double b2 = fma2(0.25, sq(fma2(-4.0, v3, 3.0 * v2) + v4), c13 * sq(fma2(-2.0, v3, v2) + v4));
     double s0 = sq(eps + b0), s1 = sq(eps + b1), s2 = sq(eps + b2);
     double y0 = rcp(s0), y1 = rcp(s1), y2 = rcp(s2);
 
@@ -105,9 +113,9 @@ __device__ __forceinline__ void weno5(double eps, double v0, double v1, double v
     double a2 = div_rcp(0.3, s2, y2);
     double s = a0 + a1 + a2;
     double ys = rcp(s);
-    double p0 = div_rcp(2.0 * v0 - 7.0 * v1 + 11.0 * v2, 6.0, r6);
-    double p1 = div_rcp(-v1 + 5.0 * v2 + 2.0 * v3, 6.0, r6);
-    double p2 = div_rcp(2.0 * v2 + 5.0 * v3 - v4, 6.0, r6);
+    double p0 = div_rcp(fma2(2.0, v0, -(7.0 * v1)) + 11.0 * v2, 6.0, r6);   // (2 v0 - 7 v1 + 11 v2)/6
+    double p1 = div_rcp(fma2(2.0, v3, -v1 + 5.0 * v2), 6.0, r6);             // (-v1 + 5 v2 + 2 v3)/6
+    double p2 = div_rcp(fma2(2.0, v2, 5.0 * v3) - v4, 6.0, r6);              // (2 v2 + 5 v3 - v4)/6
     vm = div_rcp(a0, s, ys) * p0 + div_rcp(a1, s, ys) * p1 + div_rcp(a2, s, ys) * p2;
 
     a0 = div_rcp(0.3, s0, y0);
@@ -115,9 +123,9 @@ __device__ __forceinline__ void weno5(double eps, double v0, double v1, double v
     a2 = div_rcp(0.1, s2, y2);
     s = a0 + a1 + a2;
     ys = rcp(s);
-    p0 = div_rcp(-v0 + 5.0 * v1 + 2.0 * v2, 6.0, r6);
-    p1 = div_rcp(2.0 * v1 + 5.0 * v2 - v3, 6.0, r6);
-    p2 = div_rcp(11.0 * v2 - 7.0 * v3 + 2.0 * v4, 6.0, r6);
+    p0 = div_rcp(fma2(2.0, v2, -v0 + 5.0 * v1), 6.0, r6);                    // (-v0 + 5 v1 + 2 v2)/6
+    p1 = div_rcp(fma2(2.0, v1, 5.0 * v2) - v3, 6.0, r6);                     // (2 v1 + 5 v2 - v3)/6
+    p2 = div_rcp(fma2(2.0, v4, 11.0 * v2 - 7.0 * v3), 6.0, r6);              // (11 v2 - 7 v3 + 2 v4)/6
     vp = div_rcp(a0, s, ys) * p0 + div_rcp(a1, s, ys) * p1 + div_rcp(a2, s, ys) * p2;
 }
 
