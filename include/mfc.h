@@ -146,6 +146,13 @@ int mfc_set_mlp_weights(mfc_ctx* ctx, const float* w, int n);
  * weights, and gated but recomputed with WENO because a face was non-physical. */
 int mfc_gate_stats(mfc_ctx* ctx, long long* gated, long long* fallback, long long* cells);
 
+/* Of the cell reconstructions counted by mfc_gate_stats, those whose warp
+ * step had exactly flat density and pressure stencils in all 32 pencils: the
+ * network input is then exactly zero and its output, the same for every
+ * lane, is taken from one evaluation at zero input instead of being
+ * recomputed (same decisions).  MFC_EINVAL on a NULL argument. */
+int mfc_gate_flat(mfc_ctx* ctx, long long* flat);
+
 /* Labelled training samples from the current state (FP64 WENO5-JS weights):
  * for every direction d and cell c, two samples (mixture-density stencil,
  * pressure stencil), index (d * ncells + c) * 2 + sensor; X[sample][5] the

@@ -327,7 +327,7 @@ static int write_ctrl_params(mfc_ctx* ctx, double cfl, double dt_fixed) {
     ctx->ctrl_h->cfl = cfl;
     ctx->ctrl_h->dt_fixed = dt_fixed;
     ctx->ctrl_h->status = 0;
-    ctx->ctrl_h->gated = ctx->ctrl_h->fallback = ctx->ctrl_h->cells = 0;
+    ctx->ctrl_h->gated = ctx->ctrl_h->fallback = ctx->ctrl_h->cells = ctx->ctrl_h->flat = 0;
     size_t off = offsetof(DevCtrl, t);
     CK(cudaMemcpyAsync((char*)ctx->ctrl + off, (char*)ctx->ctrl_h + off, sizeof(DevCtrl) - off,
                        cudaMemcpyHostToDevice, ctx->stream));
@@ -434,6 +434,12 @@ extern "C" int mfc_gate_stats(mfc_ctx* ctx, long long* gated, long long* fallbac
     if (gated) *gated = (long long)ctx->ctrl_h->gated;
     if (fallback) *fallback = (long long)ctx->ctrl_h->fallback;
     if (cells) *cells = (long long)ctx->ctrl_h->cells;
+    return MFC_OK;
+}
+
+extern "C" int mfc_gate_flat(mfc_ctx* ctx, long long* flat) {
+    if (!ctx || !flat) return MFC_EINVAL;
+    *flat = (long long)ctx->ctrl_h->flat;
     return MFC_OK;
 }
 

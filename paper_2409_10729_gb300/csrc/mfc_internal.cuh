@@ -22,6 +22,7 @@ struct DevCtrl {
     unsigned long long gated;   // gated form: cell reconstructions done with linear weights
     unsigned long long fallback;  // gated form: gated cells recomputed with WENO (non-physical faces)
     unsigned long long cells;   // gated form: cell reconstructions evaluated
+    unsigned long long flat;    // gated form: of those, in warp steps whose stencils were all flat
 };
 
 enum SweepMode {

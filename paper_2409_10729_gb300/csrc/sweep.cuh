@@ -505,7 +505,16 @@ sweep_kernel(const SweepArgs a) {
     constexpr bool EPI_PREFETCH = PREFETCH && MIXED;
     bool bad = false;
     R smax = R(0);
-    unsigned n_gated = 0, n_fallback = 0, n_cells = 0;
+    unsigned n_gated = 0, n_fallback = 0, n_cells = 0, n_flat = 0;
+    // gated form: the network's logit at zero input (tensor-core path, as for
+    // any other input), for warp steps whose stencils are all flat
+    float z_flat = 0.f;
+    if constexpr (GATED) {
+        const float x0[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+        float zr0, zp0;
+        gate_logits(gsm[0], gtile + (threadIdx.x >> 5) * 64, x0, x0, zr0, zp0);
+        z_flat = zr0;
+    }
     double dt = 0.0;
     if (MODE == SW_LAST_RK) dt = a.ctrl->dt;
     // SSP-RK3 stage coefficients q^(k+1) = rk_a q^n + rk_b (q^(k) + dt L)
@@ -559,15 +568,24 @@ sweep_kernel(const SweepArgs a) {
             // gate: linear weights when the network calls both the density and
             // the pressure stencil smooth (logit < 0) and the faces stay physical;
             // all 32 lanes take part in the tensor-core evaluation
-            float sr[5], sp[5], xr[5], xp[5], zr, zp;
+            float sr[5], sp[5], zr = z_flat, zp = z_flat;
 #pragma unroll
             for (int k = 0; k < 5; ++k) {
                 sr[k] = W[k][0] + W[k][1];
                 sp[k] = W[k][IE];
             }
-            gate_input(sr, xr);
-            gate_input(sp, xp);
-            gate_logits(gsm[0], gtile + (threadIdx.x >> 5) * 64, xr, xp, zr, zp);
+            bool flat = true;
+#pragma unroll
+            for (int k = 0; k < 5; ++k) flat = flat && sr[k] == sr[2] && sp[k] == sp[2];
+            // all 32 stencil pairs flat: every network input is exactly zero and
+            // every logit is the output at zero, evaluated once per warp below
+            const bool warp_flat = __all_sync(0xffffffffu, flat);
+            if (!warp_flat) {
+                float xr[5], xp[5];
+                gate_input(sr, xr);
+                gate_input(sp, xp);
+                gate_logits(gsm[0], gtile + (threadIdx.x >> 5) * 64, xr, xp, zr, zp);
+            }
             const bool smooth = zr < 0.f && zp < 0.f;
             if (smooth) {
 #pragma unroll
@@ -578,6 +596,7 @@ sweep_kernel(const SweepArgs a) {
                 n_fallback += smooth && use_weno;
                 n_gated += smooth && !use_weno;
                 n_cells += 1;
+                n_flat += warp_flat;
             }
         }
         if (use_weno) {
@@ -748,17 +767,19 @@ sweep_kernel(const SweepArgs a) {
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&a.ctrl->status, 1u);
     if constexpr (GATED) {
         // only cells this lane owns count (inactive lanes and segment halos excluded)
-        if (!active) n_gated = n_fallback = n_cells = 0;
+        if (!active) n_gated = n_fallback = n_cells = n_flat = 0;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             n_gated += __shfl_xor_sync(0xffffffffu, n_gated, o);
             n_fallback += __shfl_xor_sync(0xffffffffu, n_fallback, o);
             n_cells += __shfl_xor_sync(0xffffffffu, n_cells, o);
+            n_flat += __shfl_xor_sync(0xffffffffu, n_flat, o);
         }
         if (lane == 0) {
             atomicAdd(&a.ctrl->gated, (unsigned long long)n_gated);
             atomicAdd(&a.ctrl->fallback, (unsigned long long)n_fallback);
             atomicAdd(&a.ctrl->cells, (unsigned long long)n_cells);
+            atomicAdd(&a.ctrl->flat, (unsigned long long)n_flat);
         }
     }
 }

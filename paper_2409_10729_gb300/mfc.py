@@ -74,6 +74,7 @@ def lib() -> ctypes.CDLL:
             "mfc_set_mlp_weights": ([vp, ctypes.POINTER(ctypes.c_float), ip], ip),
             "mfc_gate_stats": ([vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
                                 ctypes.POINTER(ctypes.c_longlong)], ip),
+            "mfc_gate_flat": ([vp, ctypes.POINTER(ctypes.c_longlong)], ip),
             "mfc_gate_samples": ([vp, vp, vp, ctypes.c_longlong, ctypes.c_float,
                                   ctypes.POINTER(ctypes.c_longlong)], ip),
             "mfc_mlp_nparams": ([], ip),
@@ -225,6 +226,13 @@ class Solver:
         self._check(lib().mfc_gate_stats(self.ctx, ctypes.byref(g), ctypes.byref(f), ctypes.byref(c)),
                     "mfc_gate_stats")
         return g.value, f.value, c.value
+
+    def gate_flat(self) -> int:
+        """Cell reconstructions of the last rhs/step call whose warp step had
+        all-flat stencils (network output taken at zero input)."""
+        f = ctypes.c_longlong()
+        self._check(lib().mfc_gate_flat(self.ctx, ctypes.byref(f)), "mfc_gate_flat")
+        return f.value
 
     def gate_samples(self, tau: float = 0.1):
         """Labelled samples (X [n,5], Y [n]) of the current state as torch CUDA tensors."""

@@ -292,3 +292,42 @@ def test_trained_gate_gain():
     gat_l1 = np.array(out["gated"]["rel_l1"])
     assert np.all(gat_l1 <= 20 * mix_l1 + 1e-6)
     assert np.all(np.isfinite(res["gated"]["q"]))
+
+
+def test_flat_warps_take_the_logit_at_zero_input():
+    """Warp steps whose 32 density and pressure stencils are all exactly flat
+    take the network's output at zero input (their exact input) from one
+    evaluation: on a uniform state every reconstruction is such a step, the
+    trained network calls them smooth, and the RHS is exactly zero; on the
+    shock/droplet case only part of them are."""
+    import torch
+    from paper_2409_10729_gb300 import mfc
+    wpath = os.path.join(ROOT, "paper_2409_10729_gb300", "gate_weights.npy")
+    if not os.path.exists(wpath):
+        pytest.skip("no trained gate weights (python -m paper_2409_10729_gb300.train_gate)")
+    weights = np.load(wpath)
+    z0 = torch.empty(64, device="cuda")
+    mfc.mlp_forward_tc(torch.zeros(64, 5, device="cuda"), torch.from_numpy(weights).cuda(), z0)
+    p, w = I.shock_droplets(40)
+    wu = np.empty_like(w)
+    for f in range(w.shape[0]):
+        wu[f] = w[f].reshape(-1)[0]                 # the pre-shock air state everywhere
+    g = _gated(p, weights)
+    g.set_state_prim(wu)
+    L = g.rhs()
+    gated, fb, cells = g.gate_stats()
+    assert g.gate_flat() == cells == 3 * 40 ** 3
+    if float(z0[0]) < 0:
+        assert gated == cells and fb == 0
+    assert np.all(L == 0.0)
+    g.set_state_prim(w)
+    g.rhs()
+    gated, fb, cells = g.gate_stats()
+    flat = g.gate_flat()
+    assert 0 < flat < cells
+    # flatness is a property of the state: a never-firing gate sees the same
+    # flat steps on the same state, and still never fires
+    n = _gated(p, _bias_only(10.0))
+    n.set_state_prim(w)
+    n.rhs()
+    assert n.gate_stats()[0] == 0 and n.gate_flat() == flat
