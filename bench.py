@@ -120,7 +120,7 @@ def read_traffic(kernel: str):
     import hashlib
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     src = b""
-    for f in ("sweep.cuh", "physics.cuh", "physics_exact.cuh"):
+    for f in ("sweep.cuh", "physics.cuh", "physics_exact.cuh", "mfc_internal.cuh"):
         with open(os.path.join(ROOT, "paper_2409_10729_gb300", "csrc", f), "rb") as fh:
             src += fh.read()
     sha = hashlib.sha256(src).hexdigest()[:16]
@@ -168,7 +168,7 @@ def time_form(form, p, w, steps, warmup, device_index, rank, world):
         ms = float(t.item())
         torch.distributed.barrier()
     kt = s.kernel_times()
-    gate = s.gate_stats() if form == "gated" else None
+    gate = (*s.gate_stats(), s.gate_flat()) if form == "gated" else None
     launches = s.launches_per_step() * steps
     s.set_timing(False)
     ncell = p["n"][0] * p["n"][1] * p["n"][2]
@@ -353,9 +353,10 @@ def run_ours(args):
             "kernel_ms": {k: round(v[0] / max(1, v[1]), 4) for k, v in r["kernels"].items() if v[1]},
             "clocks": r["clocks"]}
         if r["gate"]:
-            g, f, c = r["gate"]
+            g, f, c, fl = r["gate"]
             out_forms[name]["fraction_gated_linear"] = round(g / max(c, 1), 4)
             out_forms[name]["fraction_fallback"] = round(f / max(c, 1), 4)
+            out_forms[name]["fraction_flat_warp_steps"] = round(fl / max(c, 1), 4)
     line = {
         "metric": METRIC, "value": round(res["grind"], 5), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(res["ms"] / args.steps, 3),
