@@ -55,6 +55,7 @@ class OrcParams(ctypes.Structure):
         ("gamma", ctypes.c_double * 2),
         ("pi_inf", ctypes.c_double * 2),
         ("weno_eps", ctypes.c_double),
+        ("weno_order", ctypes.c_int),
     ]
 
 
@@ -78,6 +79,7 @@ def lib():
             "orc_step_dt": ([pp, dp, ctypes.c_double], ctypes.c_int),
             "orc_run_cfl": ([pp, dp, ctypes.c_double, ctypes.c_int, dp], ctypes.c_int),
             "orc_weno5_cell": ([ctypes.c_double, dp, dp, dp], None),
+            "orc_weno3_cell": ([ctypes.c_double, dp, dp, dp], None),
             "orc_hllc_face": ([pp, ctypes.c_int, dp, dp, dp, dp], ctypes.c_int),
             "orc_sound_speed2": ([pp, dp, dp], ctypes.c_int),
             "orc_weno5_weights": ([ctypes.c_double, dp, dp, dp], None),
@@ -109,6 +111,7 @@ def params(p: dict) -> OrcParams:
         s.gamma[i] = float(p["gamma"][i])
         s.pi_inf[i] = float(p["pi_inf"][i])
     s.weno_eps = float(p.get("weno_eps", 1e-6))
+    s.weno_order = int(p.get("weno_order", 5))
     return s
 
 
@@ -191,6 +194,15 @@ def weno5_cell(v5, eps: float = 1e-6):
     v = np.ascontiguousarray(v5, dtype=np.float64)
     vm, vp = ctypes.c_double(), ctypes.c_double()
     lib().orc_weno5_cell(float(eps), _dptr(v), ctypes.byref(vm), ctypes.byref(vp))
+    return vm.value, vp.value
+
+
+def weno3_cell(v5, eps: float = 1e-6):
+    """WENO3-JS face values (v_{i+1/2}^-, v_{i-1/2}^+) of the middle cell of v5
+    (only v5[1:4] enter)."""
+    v = np.ascontiguousarray(v5, dtype=np.float64)
+    vm, vp = ctypes.c_double(), ctypes.c_double()
+    lib().orc_weno3_cell(float(eps), _dptr(v), ctypes.byref(vm), ctypes.byref(vp))
     return vm.value, vp.value
 
 

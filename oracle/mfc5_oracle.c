@@ -46,6 +46,7 @@ typedef struct {
     double gamma[2];   /* ratio of specific heats, fluid 1 and fluid 2 */
     double pi_inf[2];  /* stiffness, fluid 1 and fluid 2 */
     double weno_eps;   /* WENO epsilon (absolute) */
+    int weno_order;    /* 5 (WENO5-JS) or 3 (WENO3-JS); 0 means 5 */
 } orc_params;
 
 typedef struct {
@@ -58,6 +59,7 @@ typedef struct {
     double g1, g2;     /* 1/(gamma_i - 1) */
     double P1, P2;     /* gamma_i pi_i/(gamma_i - 1) */
     double eps;
+    int order;         /* WENO order, 3 or 5 */
 } grid;
 
 #define IE(g) (2 + (g)->ndim)
@@ -88,6 +90,8 @@ static int make_grid(const orc_params* p, grid* g) {
     for (int i = 0; i < 2; i++)
         if (!(p->gamma[i] > 1.0) || !(p->pi_inf[i] >= 0.0)) return ORC_EINVAL;
     if (!(p->weno_eps > 0.0)) return ORC_EINVAL;
+    if (p->weno_order != 0 && p->weno_order != 3 && p->weno_order != 5) return ORC_EINVAL;
+    g->order = p->weno_order == 3 ? 3 : 5;
     g->g1 = 1.0 / (p->gamma[0] - 1.0);
     g->g2 = 1.0 / (p->gamma[1] - 1.0);
     g->P1 = p->gamma[0] * p->pi_inf[0] / (p->gamma[0] - 1.0);
@@ -180,6 +184,41 @@ static void weno5(double eps, const double* v, double* vm, double* vp) {
     p1 = (2.0 * v[1] + 5.0 * v[2] - v[3]) / 6.0;
     p2 = (11.0 * v[2] - 7.0 * v[3] + 2.0 * v[4]) / 6.0;
     *vp = (a0 / s) * p0 + (a1 / s) * p1 + (a2 / s) * p2;
+}
+
+/* WENO3-JS (Jiang & Shu 1996, two two-cell stencils), the paper's
+ * third-order option (Sec. II-B).  v holds the same five cells as for WENO5,
+ * v_{i-2}..v_{i+2}; only v_{i-1}, v_i, v_{i+1} enter.
+ * Candidates at i+1/2: (-v_{i-1} + 3 v_i)/2 on {i-1, i}, (v_i + v_{i+1})/2 on
+ * {i, i+1}; at i-1/2: (v_{i-1} + v_i)/2 and (3 v_i - v_{i+1})/2.  Smoothness
+ * beta_0 = (v_i - v_{i-1})^2, beta_1 = (v_{i+1} - v_i)^2; linear weights
+ * (1/3, 2/3) for the left-biased value at i+1/2, (2/3, 1/3) for the
+ * right-biased value at i-1/2; a_k = d_k/(eps+beta_k)^2, omega_k = a_k/sum a. */
+static void weno3(double eps, const double* v, double* vm, double* vp) {
+    double b0 = sq(v[2] - v[1]);
+    double b1 = sq(v[3] - v[2]);
+
+    double a0 = (1.0 / 3.0) / sq(eps + b0);
+    double a1 = (2.0 / 3.0) / sq(eps + b1);
+    double s = a0 + a1;
+    double p0 = (-v[1] + 3.0 * v[2]) / 2.0;
+    double p1 = (v[2] + v[3]) / 2.0;
+    *vm = (a0 / s) * p0 + (a1 / s) * p1;
+
+    a0 = (2.0 / 3.0) / sq(eps + b0);
+    a1 = (1.0 / 3.0) / sq(eps + b1);
+    s = a0 + a1;
+    p0 = (v[1] + v[2]) / 2.0;
+    p1 = (3.0 * v[2] - v[3]) / 2.0;
+    *vp = (a0 / s) * p0 + (a1 / s) * p1;
+}
+
+/* Reconstruction of the grid's order at one cell (both faces). */
+static void weno(const grid* g, const double* v, double* vm, double* vp) {
+    if (g->order == 3)
+        weno3(g->eps, v, vm, vp);
+    else
+        weno5(g->eps, v, vm, vp);
 }
 
 /* ---- HLLC (Sec. II-B; Toro's three-wave approximate solver) -------------- */
@@ -294,7 +333,7 @@ static int cell_dir(const grid* g, int d, const double* W7, double* L) {
         for (int f = 0; f < neq; f++) {
             double v[5];
             for (int s = 0; s < 5; s++) v[s] = W7[(c + s) * neq + f];
-            weno5(g->eps, v, &vm[c][f], &vp[c][f]);
+            weno(g, v, &vm[c][f], &vp[c][f]);
         }
     }
     double Fm[7], Fp[7], ufm, ufp;
@@ -329,7 +368,7 @@ static int rhs_dir(const grid* g, int d, const double* q, double* rhs, int first
                 for (int f = 0; f < neq; f++) {
                     double v[5];
                     for (int s = 0; s < 5; s++) v[s] = W[(j + 1 + s) * neq + f];
-                    weno5(g->eps, v, &VM[(j + 1) * neq + f], &VP[(j + 1) * neq + f]);
+                    weno(g, v, &VM[(j + 1) * neq + f], &VP[(j + 1) * neq + f]);
                 }
             }
             /* HLLC at faces j+1/2, j = -1 .. nd-1 (face slot = j + 1) */
@@ -541,6 +580,8 @@ void orc_weno5_weights(double eps, const double* v, double* wm, double* wp) {
 
 
 void orc_weno5_cell(double eps, const double* v5, double* vm, double* vp) { weno5(eps, v5, vm, vp); }
+
+void orc_weno3_cell(double eps, const double* v5, double* vm, double* vp) { weno3(eps, v5, vm, vp); }
 
 int orc_hllc_face(const orc_params* p, int dir, const double* wL, const double* wR, double* F,
                   double* uf) {

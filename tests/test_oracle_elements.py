@@ -190,6 +190,111 @@ def test_weno_fifth_order_on_smooth_data():
     assert order > 4.5
 
 
+# ---------------------------------------------------------------- WENO3 ----
+
+def test_weno3_linear_weights_exact_for_quadratics():
+    """With a huge epsilon the WENO3 weights are the linear ones (1/3, 2/3) and
+    the reconstruction is the third-order upwind one: exact for cell averages
+    of any polynomial of degree <= 2 (both faces); a cubic is not reproduced."""
+    rng = np.random.default_rng(12)
+    h = 0.1
+    xc = np.arange(-2, 3) * h
+    for _ in range(20):
+        coef = rng.normal(size=3)
+        v = _cell_avgs(coef, h, xc)
+        vm, vp = O.weno3_cell(v, eps=1e100)
+        assert vm == pytest.approx(P.polyval(h / 2, coef), rel=1e-12, abs=1e-12)
+        assert vp == pytest.approx(P.polyval(-h / 2, coef), rel=1e-12, abs=1e-12)
+    v = _cell_avgs([0.0, 0.0, 0.0, 1.0], 1.0, np.arange(-2, 3) * 1.0)
+    vm, _ = O.weno3_cell(v, eps=1e100)
+    assert abs(vm - 0.125) > 1e-3
+
+
+def _weno3_independent(v, eps):
+    """WENO3-JS from its definitions (Jiang & Shu 1996, r = 2): candidate
+    values from the interpolating polynomial of the primitive function on
+    each two-cell stencil, smoothness indicator h int_cell (p_k')^2, weights
+    a_k = d_k/(eps+beta_k)^2 normalised, d = (1/3, 2/3) at i+1/2 and mirrored."""
+    h = 1.0
+    edges = np.arange(-2.5, 3.0, 1.0)
+
+    def stencil_poly(first):
+        xe = edges[first:first + 3]
+        V = np.concatenate([[0.0], np.cumsum(v[first:first + 2]) * h])
+        return np.polyder(np.polyfit(xe, V, 2))
+
+    polys = [stencil_poly(1), stencil_poly(2)]      # {i-1, i}, {i, i+1}
+    betas = []
+    for pk in polys:
+        d1 = np.polyder(pk, 1)
+        sq = np.polyint(np.polymul(d1, d1))
+        betas.append(h * (np.polyval(sq, 0.5) - np.polyval(sq, -0.5)))
+    out = []
+    for d, xf in (((1 / 3, 2 / 3), 0.5), ((2 / 3, 1 / 3), -0.5)):
+        a = np.array([d[k] / (eps + betas[k]) ** 2 for k in range(2)])
+        wts = a / a.sum()
+        out.append(sum(wts[k] * np.polyval(polys[k], xf) for k in range(2)))
+    return out
+
+
+def test_weno3_matches_definition_bruteforce():
+    """Random stencils (smooth, rough, with jumps): the oracle's WENO3 equals
+    the definition-based one; cells i-2 and i+2 do not enter."""
+    rng = np.random.default_rng(13)
+    for trial in range(300):
+        kind = trial % 3
+        if kind == 0:
+            v = rng.normal(size=5)
+        elif kind == 1:
+            v = 1.0 + 1e-3 * np.cumsum(rng.normal(size=5))
+        else:
+            v = np.where(np.arange(5) < rng.integers(1, 5), 1.0, 1e3) * (1 + 0.01 * rng.normal(size=5))
+        vm_ref, vp_ref = _weno3_independent(v, 1e-6)
+        vm, vp = O.weno3_cell(v, eps=1e-6)
+        scale = np.max(np.abs(v))
+        assert abs(vm - vm_ref) <= 1e-10 * scale
+        assert abs(vp - vp_ref) <= 1e-10 * scale
+        w = v.copy()
+        w[0], w[4] = rng.normal(size=2) * 1e6
+        assert O.weno3_cell(w, eps=1e-6) == (vm, vp)
+
+
+def test_weno3_mirror_symmetry():
+    """Reversing the stencil swaps the roles of the two faces."""
+    rng = np.random.default_rng(14)
+    for _ in range(100):
+        v = rng.normal(size=5) * 10 ** rng.uniform(-3, 3)
+        vm, vp = O.weno3_cell(v)
+        vm_r, vp_r = O.weno3_cell(v[::-1].copy())
+        s = np.max(np.abs(v))
+        assert vp_r == pytest.approx(vm, abs=8 * EPS * s)
+        assert vm_r == pytest.approx(vp, abs=8 * EPS * s)
+
+
+def test_weno3_eno_property_at_jump():
+    """A jump between cells i and i+1: both face values of cell i come from the
+    smooth stencil {i-1, i}; a jump between i-1 and i: from {i, i+1}.  The
+    leakage of the rough stencil is (beta_smooth/beta_rough)^2 relative."""
+    vm, vp = O.weno3_cell(np.array([7.0, 1.0, 1.0, 5.0, -3.0]))
+    assert vm == pytest.approx(1.0, abs=1e-10)
+    assert vp == pytest.approx(1.0, abs=1e-10)
+    vm, vp = O.weno3_cell(np.array([7.0, 1000.0, 1.0, 2.0, -3.0]))
+    assert vm == pytest.approx(1.5, abs=5e-9)        # (v_i + v_{i+1})/2
+    assert vp == pytest.approx(0.5, abs=5e-9)        # (3 v_i - v_{i+1})/2
+
+
+def test_weno3_third_order_on_smooth_data():
+    """Away from critical points, halving h divides the face error by ~8."""
+    errs = []
+    for h in (0.02, 0.01, 0.005):
+        xc = np.arange(-2, 3) * h + 0.3
+        v = (np.cos(xc + h / 2) - np.cos(xc - h / 2)) / h * -1.0   # averages of sin
+        vm, _ = O.weno3_cell(v)
+        errs.append(abs(vm - math.sin(0.3 + h / 2)))
+    order = math.log2(errs[1] / errs[2])
+    assert 2.5 < order < 3.5
+
+
 # ---------------------------------------------------------------- HLLC -----
 
 def _flux_ref(w, d, ndim, g, pi):

@@ -44,6 +44,11 @@ MUTATIONS = {
     "rk_stage3": ("(2.0 / 3.0) * (q2[i] + dt * L[i])", "(2.0 / 3.0) * (q2[i] + dt * L[i] * 0.99)"),
     "periodic_ghosts": ("if (periodic) {", "if (0) {"),
     "wavespeed_dx": ("s = s + (fabs(w[2 + d]) + cs) / g.dx[d];", "s = s + (fabs(w[2 + d]) + cs);"),
+    "weno3_linear_weight": ("double a0 = (1.0 / 3.0) / sq(eps + b0);", "double a0 = (2.0 / 3.0) / sq(eps + b0);"),
+    "weno3_candidate_index": ("double p1 = (v[2] + v[3]) / 2.0;", "double p1 = (v[2] + v[4]) / 2.0;"),
+    "weno3_beta_index": ("double b1 = sq(v[3] - v[2]);", "double b1 = sq(v[3] - v[1]);"),
+    "weno3_right_candidate": ("p1 = (3.0 * v[2] - v[3]) / 2.0;", "p1 = (3.0 * v[2] + v[3]) / 2.0;"),
+    "weno_order_ignored": ("    if (g->order == 3)\n        weno3(", "    if (0)\n        weno3("),
 }
 
 
