@@ -5,7 +5,9 @@ Metric: grind time, ns per (cell x equation x RHS evaluation), lower is better,
 and the fraction of the HBM roofline it reaches, for the FP64 form (reference
 operation order, bit-identical to the oracle; the headline value), the
 reorganised FP64 form, the mixed-precision form (512^3) and the MLP-gated
-form (256^3, trained weights from paper_2409_10729_gb300/gate_weights.npy).
+form (256^3, trained weights from paper_2409_10729_gb300/gate_weights.npy),
+plus the third-order reconstruction option (WENO3-JS) in the FP64 (256^3)
+and mixed (512^3) forms.
 
 Workload (per GPU): the 3-D shock / droplet array, 256^3 cells, 7 equations,
 FP64, SSP-RK3 at CFL 0.4 (the timed "step" is one RK3 step = 3 RHS
@@ -40,6 +42,8 @@ CFL = 0.4
 # oracle's formulas (every +, -, *, /, sqrt counts 1):
 # cons->prim 22, WENO5-JS 107 per field, HLLC 122 per face, divergence 18.
 FLOPS_CELL_DIR_3D = 22 + 107 * 7 + 122 + 18          # 911
+# with the third-order option: WENO3-JS 38 per field (beta 4, two faces x 17)
+FLOPS_CELL_DIR_3D_WENO3 = 22 + 38 * 7 + 122 + 18     # 428
 FLOPS_RK_CELL = 28                                     # stage update, mean over the 3 stages
 FLOPS_WAVESPEED_CELL = 45                              # once per step, in the last stage
 # Algorithmic bytes per cell, equation and RHS: stage 1 reads q^n and writes
@@ -184,11 +188,12 @@ def time_form(form, p, w, steps, warmup, device_index, rank, world):
 def roofline_for(form, res, peak_alu, alu_src, hbm_peak, hbm_src):
     """Roofline object for the dominant kernel of one form."""
     kt = res["kernels"]
+    base = form.replace("_weno3", "")
     name = max((k for k in kt if kt[k][1] > 0), key=lambda k: kt[k][0])
     total_ms, count = kt[name]
     avg_s = total_ms / count * 1e-3
     ncell = res["ncell"]
-    flops = FLOPS_CELL_DIR_3D
+    flops = FLOPS_CELL_DIR_3D_WENO3 if form.endswith("_weno3") else FLOPS_CELL_DIR_3D
     if name == "sweep_y":
         flops += 7
     if name == "sweep_z":
@@ -197,11 +202,11 @@ def roofline_for(form, res, peak_alu, alu_src, hbm_peak, hbm_src):
     share = total_ms / sum(v[0] for v in kt.values())
     return {"bound": "alu", "kernel": name, "achieved": round(achieved, 4), "peak": round(peak_alu, 3),
             "unit": "TFLOP/s", "frac": round(achieved / peak_alu, 4), "peak_source": alu_src,
-            "traffic": read_traffic(f"{form}:{name}"), "share_of_step": round(share, 3),
+            "traffic": read_traffic(f"{form}:{name}") if form == base else None, "share_of_step": round(share, 3),
             "avg_launch_ms": round(total_ms / count, 4),
             "algorithmic_flops_per_cell": flops,
-            "hbm": {"achieved_gbs": round(ALG_BYTES[form] / res["grind"], 1), "peak": hbm_peak,
-                    "frac": round(ALG_BYTES[form] / res["grind"] / hbm_peak, 4), "peak_source": hbm_src}}
+            "hbm": {"achieved_gbs": round(ALG_BYTES[base] / res["grind"], 1), "peak": hbm_peak,
+                    "frac": round(ALG_BYTES[base] / res["grind"] / hbm_peak, 4), "peak_source": hbm_src}}
 
 
 def cpu_baseline(target_s=15.0):
@@ -297,10 +302,15 @@ def run_ours(args):
     res = time_form("fp64", p, w, args.steps, args.warmup, local, rank, world)
     forms = {"fp64": res}
     forms["fp64_fast"] = time_form("fp64_fast", p, w, args.steps, args.warmup, local, rank, world)
+    # the third-order reconstruction option (weno_order = 3), same workload
+    forms["fp64_weno3"] = time_form("fp64", dict(p, weno_order=3), w, max(2, args.steps // 2), args.warmup,
+                                    local, rank, world)
     if not args.no_mixed:
         forms["gated"] = time_form("gated", p, w, args.steps, args.warmup, local, rank, world)
         pm, wm = I.shock_droplets(512)
         forms["mixed"] = time_form("mixed", pm, wm, max(2, args.steps // 2), args.warmup, local, rank, world)
+        forms["mixed_weno3"] = time_form("mixed", dict(pm, weno_order=3), wm, max(2, args.steps // 2),
+                                         args.warmup, local, rank, world)
         del wm
 
     # end to end through the C ABI with pinned host buffers: per step, copy
@@ -344,7 +354,7 @@ def run_ours(args):
     roof = roofline_for("fp64", res, fp64_peak, "measured (FP64 FMA-chain probe)", hbm_peak, hbm_src)
     out_forms = {}
     for name, r in forms.items():
-        peak = fp32_peak if name in ("mixed", "gated") else fp64_peak
+        peak = fp32_peak if name.startswith(("mixed", "gated")) else fp64_peak
         rf = roofline_for(name, r, peak, "measured FMA-chain probe", hbm_peak, hbm_src)
         out_forms[name] = {"grind": round(r["grind"], 5), "unit": UNIT, "ms_per_step": round(r["ms"] / r["steps"], 3),
             "cells": r["ncell"],

@@ -63,8 +63,11 @@ typedef struct {
     int bc[3][2];      /* mfc_bc per dimension and side; periodic must be set on both sides */
     double gamma[2];   /* ratio of specific heats of fluid 1 and fluid 2 (> 1) */
     double pi_inf[2];  /* stiffness pi_inf of fluid 1 and fluid 2 (>= 0), in pressure units */
-    double weno_eps;   /* WENO5-JS epsilon, absolute (1e-6 is the usual choice) */
+    double weno_eps;   /* WENO epsilon, absolute (1e-6 is the usual choice) */
     int precision;     /* mfc_precision */
+    int weno_order;    /* reconstruction (Sec. II-B): 5 = WENO5-JS, 3 = WENO3-JS (Jiang-Shu, two
+                          two-cell stencils, linear weights 1/3, 2/3); 0 means 5.  WENO3 is
+                          available in every precision except MFC_GATED (MFC_EINVAL) */
 } mfc_params;
 
 /* Creates a context: validates params (MFC_EINVAL), allocates the state,

@@ -82,6 +82,8 @@ static int validate(const mfc_params* p) {
     if (p->precision != MFC_FP64 && p->precision != MFC_MIXED && p->precision != MFC_FP64_FAST &&
         p->precision != MFC_GATED)
         return MFC_EINVAL;
+    if (p->weno_order != 0 && p->weno_order != 3 && p->weno_order != 5) return MFC_EINVAL;
+    if (p->weno_order == 3 && p->precision == MFC_GATED) return MFC_EINVAL;
     return MFC_OK;
 }
 
@@ -198,6 +200,7 @@ static SweepArgs base_args(mfc_ctx* ctx) {
     a.ncell = ctx->ncell;
     a.eos = ctx->eos;
     a.eps = ctx->p.weno_eps;
+    a.order = ctx->p.weno_order == 3 ? 3 : 5;
     a.ctrl = ctx->ctrl;
     a.acc = ctx->acc;
     a.qn = ctx->qn;

@@ -45,6 +45,7 @@ struct SweepArgs {
     double rdx[3];        // RN(1/dx) per direction (reference-order form)
     Eos eos;
     double eps;
+    int order;            // WENO order, 3 or 5
     int periodic;         // along the sweep direction
     int seg;              // cells per thread along the sweep direction
     int stage;            // 1, 2, 3

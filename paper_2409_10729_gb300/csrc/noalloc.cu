@@ -73,6 +73,7 @@ int check_params(const mfc_params* p) {
             return MFC_EINVAL;
     if (!(p->weno_eps > 0.0) || !isfinite(p->weno_eps)) return MFC_EINVAL;
     if (p->precision != MFC_FP64) return MFC_EINVAL;
+    if (p->weno_order != 0 && p->weno_order != 3 && p->weno_order != 5) return MFC_EINVAL;
     return MFC_OK;
 }
 
@@ -112,6 +113,7 @@ extern "C" int mfc_rhs_noalloc(const mfc_params* params, const double* q, double
     a.ncell = ncell;
     a.eos = Eos{g1, g2, P1, P2, g1 - g2, P1 - P2};
     a.eps = params->weno_eps;
+    a.order = params->weno_order == 3 ? 3 : 5;
     a.ctrl = ctrl;
     a.acc = scratch + kCtrlDoubles;
     a.qin = q;

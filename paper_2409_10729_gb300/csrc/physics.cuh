@@ -104,6 +104,35 @@ __device__ __forceinline__ void weno5(R v0, R v1, R v2, R v3, R v4, R eps, R& vm
     vp = v2 + Np * Dm * r;
 }
 
+// WENO3-JS (Sec. II-B's third-order option; Jiang & Shu, stencils {i-1, i}
+// and {i, i+1}, beta_k the squared first differences d1 = v_i - v_{i-1},
+// d2 = v_{i+1} - v_i).  In difference form the candidates are v_i +- d_k/2:
+//   v_{i+1/2}^- = v_i + (w0 d1 + w1 d2)/2,  linear weights (1/3, 2/3)
+//   v_{i-1/2}^+ = v_i - (w0 d1 + w1 d2)/2,  linear weights (2/3, 1/3)
+// with the same weight scaling as weno5 and one reciprocal for both faces.
+template <typename R>
+__device__ __forceinline__ void weno3(R v1, R v2, R v3, R eps, R& vm, R& vp) {
+    R d1 = v2 - v1, d2 = v3 - v2;
+    R s0 = eps + d1 * d1, s1 = eps + d2 * d2;
+    s0 = s0 * s0;
+    s1 = s1 * s1;
+    R m0, m1;
+    if constexpr (sizeof(R) == 8) {
+        m0 = s1;   // product form: weight of stencil k proportional to d_k * s_other
+        m1 = s0;
+    } else {
+        R smin = fminf(s0, s1);
+        m0 = __fdividef(smin, s0);
+        m1 = __fdividef(smin, s1);
+    }
+    R am0 = R(1.0 / 3.0) * m0, am1 = R(2.0 / 3.0) * m1;
+    R ap0 = R(2.0 / 3.0) * m0, ap1 = R(1.0 / 3.0) * m1;
+    R Dm = am0 + am1, Dp = ap0 + ap1;
+    R r = rdiv(R(1), R(2) * Dm * Dp);
+    vm = v2 + (am0 * d1 + am1 * d2) * Dp * r;
+    vp = v2 - (ap0 * d1 + ap1 * d2) * Dm * r;
+}
+
 // ---------------------------------------------------------------- HLLC
 // Flux through a face normal to DIR from reconstructed primitive states
 // (alpha1 rho1, alpha2 rho2, u_k, p, alpha1).  uf receives the velocity of the

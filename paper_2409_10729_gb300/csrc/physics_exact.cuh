@@ -129,6 +129,32 @@ __device__ __forceinline__ void weno5(double eps, double v0, double v1, double v
     vp = div_rcp(a0, s, ys) * p0 + div_rcp(a1, s, ys) * p1 + div_rcp(a2, s, ys) * p2;
 }
 
+// WENO3-JS in the reference order: v1..v3 = v_{i-1}..v_{i+1}; weights
+// a_k = d_k/(eps+beta_k)^2 with d = (1/3, 2/3) at i+1/2 and (2/3, 1/3) at
+// i-1/2, omega_k = a_k/sum(a), candidates (.)/2 (an exact halving).
+__device__ __forceinline__ void weno3(double eps, double v1, double v2, double v3, double& vm, double& vp) {
+    const double c1 = 1.0 / 3.0, c2 = 2.0 / 3.0;
+    double b0 = sq(v2 - v1), b1 = sq(v3 - v2);
+    double s0 = sq(eps + b0), s1 = sq(eps + b1);
+    double y0 = rcp(s0), y1 = rcp(s1);
+
+    double a0 = div_rcp(c1, s0, y0);
+    double a1 = div_rcp(c2, s1, y1);
+    double s = a0 + a1;
+    double ys = rcp(s);
+    double p0 = (-v1 + 3.0 * v2) * 0.5;
+    double p1 = (v2 + v3) * 0.5;
+    vm = div_rcp(a0, s, ys) * p0 + div_rcp(a1, s, ys) * p1;
+
+    a0 = div_rcp(c2, s0, y0);
+    a1 = div_rcp(c1, s1, y1);
+    s = a0 + a1;
+    ys = rcp(s);
+    p0 = (v1 + v2) * 0.5;
+    p1 = (3.0 * v2 - v3) * 0.5;
+    vp = div_rcp(a0, s, ys) * p0 + div_rcp(a1, s, ys) * p1;
+}
+
 struct Face {
     double rho, p, a1, G, Pi, E, c2;
 };

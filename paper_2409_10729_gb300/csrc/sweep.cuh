@@ -600,10 +600,20 @@ sweep_kernel(const SweepArgs a) {
             }
         }
         if (use_weno) {
+            if (GATED || a.order == 5) {
 #pragma unroll
-            for (int f = 0; f < NEQ; ++f) {
-                if constexpr (EXACT) exact::weno5(a.eps, W[0][f], W[1][f], W[2][f], W[3][f], W[4][f], vm[f], vp[f]);
-                else weno5(W[0][f], W[1][f], W[2][f], W[3][f], W[4][f], eps, vm[f], vp[f]);
+                for (int f = 0; f < NEQ; ++f) {
+                    if constexpr (EXACT)
+                        exact::weno5(a.eps, W[0][f], W[1][f], W[2][f], W[3][f], W[4][f], vm[f], vp[f]);
+                    else
+                        weno5(W[0][f], W[1][f], W[2][f], W[3][f], W[4][f], eps, vm[f], vp[f]);
+                }
+            } else {   // WENO3 (uniform over the launch): cells i-1 .. i+1 of the window
+#pragma unroll
+                for (int f = 0; f < NEQ; ++f) {
+                    if constexpr (EXACT) exact::weno3(a.eps, W[1][f], W[2][f], W[3][f], vm[f], vp[f]);
+                    else weno3(W[1][f], W[2][f], W[3][f], eps, vm[f], vp[f]);
+                }
             }
         }
         if (j >= s0) {

@@ -33,6 +33,7 @@ class MfcParams(ctypes.Structure):
         ("pi_inf", ctypes.c_double * 2),
         ("weno_eps", ctypes.c_double),
         ("precision", ctypes.c_int),
+        ("weno_order", ctypes.c_int),
     ]
 
 
@@ -121,6 +122,7 @@ def make_params(p: dict, precision="fp64") -> MfcParams:
         s.pi_inf[i] = float(p["pi_inf"][i])
     s.weno_eps = float(p.get("weno_eps", 1e-6))
     s.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    s.weno_order = int(p.get("weno_order", 5))
     return s
 
 

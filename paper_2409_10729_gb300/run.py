@@ -20,6 +20,7 @@ def main():
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=1)
     ap.add_argument("--cfl", type=float, default=0.4)
+    ap.add_argument("--weno-order", type=int, choices=[3, 5], default=5)
     args = ap.parse_args()
 
     import torch
@@ -35,6 +36,7 @@ def main():
         p, w = I.shock_water_column(2 * args.n, args.n)
     else:
         p, w = I.air_water_shock_tube(args.n)
+    p = dict(p, weno_order=args.weno_order)
     s = mfc.Solver(p, args.form)
     if args.form == "gated":
         import numpy as np

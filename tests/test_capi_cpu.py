@@ -50,14 +50,15 @@ def test_library_exports_every_declared_symbol(lib):
 def test_params_struct_layout_matches_header(tmp_path):
     src = tmp_path / "layout.c"
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "mfc.h"\n'
-                   'int main(void){printf("%zu %zu %zu %zu %zu\\n", sizeof(mfc_params),'
+                   'int main(void){printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(mfc_params),'
                    ' offsetof(mfc_params, bc), offsetof(mfc_params, gamma),'
-                   ' offsetof(mfc_params, weno_eps), offsetof(mfc_params, precision));return 0;}\n')
+                   ' offsetof(mfc_params, weno_eps), offsetof(mfc_params, precision), offsetof(mfc_params, weno_order));return 0;}\n')
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
     P = mfc.MfcParams
-    assert got == [ctypes.sizeof(P), P.bc.offset, P.gamma.offset, P.weno_eps.offset, P.precision.offset]
+    assert got == [ctypes.sizeof(P), P.bc.offset, P.gamma.offset, P.weno_eps.offset, P.precision.offset,
+                   P.weno_order.offset]
 
 
 def _params(**over):
@@ -71,10 +72,13 @@ def _params(**over):
     dict(ndim=0), dict(ndim=4), dict(n=[0, 8, 8]), dict(hi=[0.0, 1.0, 1.0]),
     dict(bc=[[0, 1], [0, 0], [0, 0]]), dict(bc=[[2, 2], [0, 0], [0, 0]]),
     dict(gamma=[1.0, 1.4]), dict(pi_inf=[-1.0, 0.0]), dict(weno_eps=0.0),
+    dict(weno_order=4), dict(weno_order=7), dict(weno_order=3, precision="gated"),
 ])
 def test_create_rejects_bad_params_before_touching_the_device(lib, bad):
     handle = ctypes.c_void_p()
-    st = lib.mfc_create(ctypes.byref(mfc.make_params(_params(**bad))), None, ctypes.byref(handle))
+    bad = dict(bad)
+    prec = bad.pop("precision", "fp64")
+    st = lib.mfc_create(ctypes.byref(mfc.make_params(_params(**bad), prec)), None, ctypes.byref(handle))
     assert st == mfc.MFC_EINVAL
     assert not handle.value
 

@@ -304,3 +304,75 @@ def test_integer_conversions_match_hardware():
     bad = ctypes.c_longlong(-1)
     assert mfc.lib().mfc_selfcheck_conversions(1 << 24, 2409, ctypes.byref(bad)) == 0
     assert bad.value == 0
+
+
+# ---------------------------------------------------------------- WENO3 ----
+# The third-order reconstruction option (Sec. II-B; weno_order = 3) to the
+# same bar: bit-identical in the FP64 form, 1e-12 in the reorganised one.
+
+W3_SMALL = [(1, [33], 1), (2, [13, 9], 1), (2, [70, 37], 0), (3, [13, 9, 7], 1), (3, [40, 11, 35], 0)]
+
+
+def _w3(p):
+    return dict(p, weno_order=3)
+
+
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("ndim,n,bc", W3_SMALL)
+def test_weno3_rhs_parity_small(ndim, n, bc, form):
+    p, w = _case(ndim, n, bc, seed=ndim + 20)
+    p = _w3(p)
+    s = solver(p, form)
+    s.set_state_prim(w)
+    L = s.rhs()
+    q = O.prim_to_cons(p, w)
+    Lo = O.rhs(p, q)
+    assert not np.array_equal(Lo, O.rhs(dict(p, weno_order=5), q))
+    check_rhs(form, p, L, Lo, q, O.max_wavespeed(p, q))
+
+
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("ndim,n,bc", W3_SMALL)
+def test_weno3_cfl_steps_parity_small(ndim, n, bc, form):
+    p, w = _case(ndim, n, bc, seed=ndim + 25)
+    p = _w3(p)
+    s = solver(p, form)
+    s.set_state_prim(w)
+    t = s.step_rk3(0.4, 5)
+    qo, to = O.run_cfl(p, O.prim_to_cons(p, w), 0.4, 5)
+    check_state(form, s.get_state(), qo)
+    assert t == to if form == "fp64" else abs(t - to) <= 1e-13 * to
+
+
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("case", ["tube_1000x200", "column_128x64x500", "droplets_32x100"])
+def test_weno3_full_runs(case, form):
+    """The three workloads at reduced size for their full step counts, WENO3."""
+    gen = {"tube_1000x200": (lambda: I.air_water_shock_tube(1000), 200),
+           "column_128x64x500": (lambda: I.shock_water_column(128, 64), 500),
+           "droplets_32x100": (lambda: I.shock_droplets(32), 100)}
+    mk, steps = gen[case]
+    p, w = mk()
+    p = _w3(p)
+    s = solver(p, form)
+    s.set_state_prim(w)
+    t = s.step_rk3(0.4, steps)
+    qo, to = oracle_run("weno3_" + case, p, w, steps)
+    check_state(form, s.get_state(), qo)
+    assert t == to if form == "fp64" else abs(t - to) <= 1e-12 * to
+
+
+def test_weno3_mixed_form_error_against_oracle():
+    """Mixed precision with WENO3 on the 2-D column (128x64, 100 steps):
+    per-field error against the oracle at the FP32 level."""
+    p, w = I.shock_water_column(128, 64)
+    p = _w3(p)
+    s = solver(p, "mixed")
+    s.set_state_prim(w)
+    s.step_rk3(0.4, 100)
+    qo, _ = O.run_cfl(p, O.prim_to_cons(p, w), 0.4, 100)
+    q = s.get_state()
+    err = rel_err(q, qo)
+    assert err.max() <= 2e-4, err
+    l1 = np.abs(q - qo).reshape(6, -1).sum(1) / np.abs(qo).reshape(6, -1).sum(1)
+    assert l1[[0, 1, 4, 5]].max() <= 1e-6, l1
