@@ -56,6 +56,7 @@ class OrcParams(ctypes.Structure):
         ("pi_inf", ctypes.c_double * 2),
         ("weno_eps", ctypes.c_double),
         ("weno_order", ctypes.c_int),
+        ("edges", ctypes.POINTER(ctypes.c_double) * 3),
     ]
 
 
@@ -80,6 +81,8 @@ def lib():
             "orc_run_cfl": ([pp, dp, ctypes.c_double, ctypes.c_int, dp], ctypes.c_int),
             "orc_weno5_cell": ([ctypes.c_double, dp, dp, dp], None),
             "orc_weno3_cell": ([ctypes.c_double, dp, dp, dp], None),
+            "orc_weno5_table": ([dp, dp], ctypes.c_int),
+            "orc_weno5_nu_cell": ([dp, ctypes.c_double, dp, dp, dp], None),
             "orc_hllc_face": ([pp, ctypes.c_int, dp, dp, dp, dp], ctypes.c_int),
             "orc_sound_speed2": ([pp, dp, dp], ctypes.c_int),
             "orc_weno5_weights": ([ctypes.c_double, dp, dp, dp], None),
@@ -112,6 +115,16 @@ def params(p: dict) -> OrcParams:
         s.pi_inf[i] = float(p["pi_inf"][i])
     s.weno_eps = float(p.get("weno_eps", 1e-6))
     s.weno_order = int(p.get("weno_order", 5))
+    edges = p.get("edges") or [None, None, None]
+    keep = []
+    for d in range(3):
+        if d < s.ndim and edges[d] is not None:
+            e = np.ascontiguousarray(edges[d], dtype=np.float64)
+            if e.shape != (s.n[d] + 1,):
+                raise ValueError(f"edges[{d}] must hold n[{d}] + 1 values")
+            keep.append(e)
+            s.edges[d] = e.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    s._keep = keep   # the edge arrays live as long as the struct
     return s
 
 
@@ -203,6 +216,30 @@ def weno3_cell(v5, eps: float = 1e-6):
     v = np.ascontiguousarray(v5, dtype=np.float64)
     vm, vp = ctypes.c_double(), ctypes.c_double()
     lib().orc_weno3_cell(float(eps), _dptr(v), ctypes.byref(vm), ctypes.byref(vp))
+    return vm.value, vp.value
+
+
+NU_TABLE = 42   # doubles per cell of a non-uniform WENO5 table
+
+
+def weno5_table(widths5):
+    """Non-uniform WENO5 table of a cell from the widths of cells i-2..i+2:
+    dict with cp, cm (3x3 face-value functionals at i+1/2, i-1/2 per stencil),
+    B, C (3x3 functionals of b = h p'(0), c = h^2 p''(0)/2), dp, dm (linear weights)."""
+    w = np.ascontiguousarray(widths5, dtype=np.float64)
+    T = np.empty(NU_TABLE)
+    if lib().orc_weno5_table(_dptr(w), _dptr(T)):
+        raise ValueError("degenerate widths")
+    return {"raw": T, "cp": T[0:9].reshape(3, 3), "cm": T[9:18].reshape(3, 3), "B": T[18:27].reshape(3, 3),
+            "C": T[27:36].reshape(3, 3), "dp": T[36:39], "dm": T[39:42]}
+
+
+def weno5_nu_cell(table, v5, eps: float = 1e-6):
+    """Non-uniform WENO5 face values (v_{i+1/2}^-, v_{i-1/2}^+) from a cell table."""
+    T = np.ascontiguousarray(table["raw"], dtype=np.float64)
+    v = np.ascontiguousarray(v5, dtype=np.float64)
+    vm, vp = ctypes.c_double(), ctypes.c_double()
+    lib().orc_weno5_nu_cell(_dptr(T), float(eps), _dptr(v), ctypes.byref(vm), ctypes.byref(vp))
     return vm.value, vp.value
 
 

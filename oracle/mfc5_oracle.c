@@ -47,6 +47,8 @@ typedef struct {
     double pi_inf[2];  /* stiffness, fluid 1 and fluid 2 */
     double weno_eps;   /* WENO epsilon (absolute) */
     int weno_order;    /* 5 (WENO5-JS) or 3 (WENO3-JS); 0 means 5 */
+    const double* edges[3];  /* optional: the n[d]+1 cell edges of direction d, strictly increasing
+                                (a non-uniform, e.g. tanh-stretched, grid; WENO5 only); NULL: uniform */
 } orc_params;
 
 typedef struct {
@@ -60,12 +62,31 @@ typedef struct {
     double P1, P2;     /* gamma_i pi_i/(gamma_i - 1) */
     double eps;
     int order;         /* WENO order, 3 or 5 */
+    int stretched[3];  /* direction d has a non-uniform grid */
+    double* h[3];      /* stretched: widths of cells -3 .. n+2 (slot j + 3), ghosts per BC */
+    double* tab[3];    /* stretched: WENO5 tables of cells -1 .. n (slot j + 1), NT each */
 } grid;
+
+#define NT 42          /* doubles per cell of a non-uniform WENO5 table (see make_tables) */
 
 #define IE(g) (2 + (g)->ndim)
 #define IA(g) (3 + (g)->ndim)
 
+static void free_grid(grid* g) {
+    for (int d = 0; d < 3; d++) {
+        free(g->h[d]);
+        free(g->tab[d]);
+        g->h[d] = g->tab[d] = NULL;
+    }
+}
+
+static int make_tables(grid* g, int d, const double* edges);
+
 static int make_grid(const orc_params* p, grid* g) {
+    for (int d = 0; d < 3; d++) {
+        g->stretched[d] = 0;
+        g->h[d] = g->tab[d] = NULL;
+    }
     if (!p || p->ndim < 1 || p->ndim > 3) return ORC_EINVAL;
     g->ndim = p->ndim;
     g->neq = p->ndim + 4;
@@ -97,6 +118,12 @@ static int make_grid(const orc_params* p, grid* g) {
     g->P1 = p->gamma[0] * p->pi_inf[0] / (p->gamma[0] - 1.0);
     g->P2 = p->gamma[1] * p->pi_inf[1] / (p->gamma[1] - 1.0);
     g->eps = p->weno_eps;
+    for (int d = 0; d < g->ndim; d++) {
+        if (!p->edges[d]) continue;
+        if (g->order != 5) { free_grid(g); return ORC_EINVAL; }
+        int st = make_tables(g, d, p->edges[d]);
+        if (st) { free_grid(g); return st; }
+    }
     return ORC_OK;
 }
 
@@ -154,6 +181,159 @@ static double sound2(double G, double Pi, double rho, double p) {
 /* ---- WENO5-JS (Sec. II-B, fifth-order reconstruction) -------------------- */
 
 static double sq(double x) { return x * x; }
+/* ---- WENO5 on a non-uniform grid (Shu's general reconstruction) ----------
+ * For cell i of width h_i, with t = (x - x_i)/h_i, each three-cell stencil k
+ * (cells i-2+k .. i+k) carries the quadratic p_k(t) = a + b t + c t^2 whose
+ * averages over its three cells are the cell values; p_k(+-1/2) are its face
+ * values, and its smoothness indicator is
+ *   beta_k = sum_{l=1,2} h_i^(2l-1) int_cell (d^l p_k/dx^l)^2 dx = b^2 + (13/3) c^2.
+ * The linear weights d_k are those for which sum_k d_k p_k(+-1/2) is the face
+ * value of the quartic with the five cell averages (the only stencil that
+ * contains cell i-2, resp. i+2, fixes d_0, resp. d_2; d_1 = 1 - d_0 - d_2).
+ * On a uniform grid these are the Jiang-Shu coefficients.  The table of a
+ * cell holds, as linear functionals of the stencil values: face values at
+ * i+1/2 (cp[3][3]) and i-1/2 (cm[3][3]), b (B[3][3]), c (C[3][3]), and the
+ * linear weights dp[3] (i+1/2) and dm[3] (i-1/2). */
+
+/* Inverse of the m x m row-major matrix A (m <= 5), Gauss-Jordan with partial
+ * pivoting; returns 1 when A is singular. */
+static int invert(int m, const double* A, double* Ainv) {
+    double a[5][10];
+    for (int r = 0; r < m; r++)
+        for (int c = 0; c < 2 * m; c++) a[r][c] = c < m ? A[r * m + c] : (c - m == r ? 1.0 : 0.0);
+    for (int col = 0; col < m; col++) {
+        int piv = col;
+        for (int r = col + 1; r < m; r++)
+            if (fabs(a[r][col]) > fabs(a[piv][col])) piv = r;
+        if (!(fabs(a[piv][col]) > 0.0)) return 1;
+        if (piv != col)
+            for (int c = 0; c < 2 * m; c++) {
+                double t = a[col][c];
+                a[col][c] = a[piv][c];
+                a[piv][c] = t;
+            }
+        double inv = 1.0 / a[col][col];
+        for (int c = 0; c < 2 * m; c++) a[col][c] = a[col][c] * inv;
+        for (int r = 0; r < m; r++) {
+            if (r == col) continue;
+            double f = a[r][col];
+            for (int c = 0; c < 2 * m; c++) a[r][c] = a[r][c] - f * a[col][c];
+        }
+    }
+    for (int r = 0; r < m; r++)
+        for (int c = 0; c < m; c++) Ainv[r * m + c] = a[r][m + c];
+    return 0;
+}
+
+/* Average of t^m over [l, u]. */
+static double avg_pow(int m, double l, double u) {
+    double lp = l, up = u;
+    for (int k = 0; k < m; k++) {
+        lp = lp * l;
+        up = up * u;
+    }
+    return (up - lp) / ((double)(m + 1) * (u - l));
+}
+
+/* Table of one cell from the widths w[0..4] of cells i-2 .. i+2. */
+static int cell_table(const double* w, double* T) {
+    double e[6];   /* cell edges in units of h_i, cell i = [-1/2, 1/2] */
+    e[2] = -0.5;
+    e[3] = 0.5;
+    e[1] = e[2] - w[1] / w[2];
+    e[0] = e[1] - w[0] / w[2];
+    e[4] = e[3] + w[3] / w[2];
+    e[5] = e[4] + w[4] / w[2];
+    double *cp = T, *cm = T + 9, *B = T + 18, *C = T + 27, *dp = T + 36, *dm = T + 39;
+    for (int k = 0; k < 3; k++) {
+        double M[9], Mi[9];
+        for (int j = 0; j < 3; j++)
+            for (int m = 0; m < 3; m++) M[3 * j + m] = avg_pow(m, e[k + j], e[k + j + 1]);
+        if (invert(3, M, Mi)) return 1;
+        for (int j = 0; j < 3; j++) {
+            /* coefficient of stencil value j in a, b, c: Mi[0][j], Mi[1][j], Mi[2][j] */
+            cp[3 * k + j] = Mi[j] + 0.5 * Mi[3 + j] + 0.25 * Mi[6 + j];
+            cm[3 * k + j] = Mi[j] - 0.5 * Mi[3 + j] + 0.25 * Mi[6 + j];
+            B[3 * k + j] = Mi[3 + j];
+            C[3 * k + j] = Mi[6 + j];
+        }
+    }
+    double M5[25], Mi5[25], Qp[5], Qm[5];
+    for (int j = 0; j < 5; j++)
+        for (int m = 0; m < 5; m++) M5[5 * j + m] = avg_pow(m, e[j], e[j + 1]);
+    if (invert(5, M5, Mi5)) return 1;
+    for (int j = 0; j < 5; j++) {
+        double sp = 0.0, sm = 0.0, xp = 1.0, xm = 1.0;
+        for (int m = 0; m < 5; m++) {
+            sp = sp + Mi5[5 * m + j] * xp;
+            sm = sm + Mi5[5 * m + j] * xm;
+            xp = xp * 0.5;
+            xm = xm * -0.5;
+        }
+        Qp[j] = sp;
+        Qm[j] = sm;
+    }
+    dp[0] = Qp[0] / cp[0];
+    dp[2] = Qp[4] / cp[3 * 2 + 2];
+    dp[1] = 1.0 - dp[0] - dp[2];
+    dm[0] = Qm[0] / cm[0];
+    dm[2] = Qm[4] / cm[3 * 2 + 2];
+    dm[1] = 1.0 - dm[0] - dm[2];
+    return 0;
+}
+
+/* Cell widths (with ghosts per BC) and WENO5 tables of stretched direction d. */
+static int make_tables(grid* g, int d, const double* edges) {
+    long n = g->n[d];
+    for (long j = 0; j < n; j++)
+        if (!(edges[j + 1] > edges[j]) || !isfinite(edges[j + 1] - edges[j])) return ORC_EINVAL;
+    g->h[d] = malloc(sizeof(double) * (n + 6));
+    g->tab[d] = malloc(sizeof(double) * (n + 2) * NT);
+    if (!g->h[d] || !g->tab[d]) return ORC_ENOMEM;
+    for (long j = -3; j < n + 3; j++) {
+        long s;
+        if (g->periodic[d]) {
+            s = j % n;
+            if (s < 0) s += n;
+        } else {
+            s = j < 0 ? 0 : (j > n - 1 ? n - 1 : j);
+        }
+        g->h[d][j + 3] = edges[s + 1] - edges[s];
+    }
+    for (long j = -1; j < n + 1; j++)
+        if (cell_table(&g->h[d][j + 1], &g->tab[d][(j + 1) * NT])) return ORC_EINVAL;
+    g->stretched[d] = 1;
+    return ORC_OK;
+}
+
+/* WENO5-JS on a non-uniform grid from the cell's table T (same weights
+ * a_k = d_k/(eps+beta_k)^2, omega_k = a_k/sum a as the uniform scheme). */
+static void weno5_nu(const double* T, double eps, const double* v, double* vm, double* vp) {
+    const double *cp = T, *cm = T + 9, *B = T + 18, *C = T + 27, *dp = T + 36, *dm = T + 39;
+    double beta[3], qp[3], qm[3];
+    for (int k = 0; k < 3; k++) {
+        double b = 0.0, c = 0.0, sp = 0.0, sm = 0.0;
+        for (int j = 0; j < 3; j++) {
+            b = b + B[3 * k + j] * v[k + j];
+            c = c + C[3 * k + j] * v[k + j];
+            sp = sp + cp[3 * k + j] * v[k + j];
+            sm = sm + cm[3 * k + j] * v[k + j];
+        }
+        beta[k] = b * b + (13.0 / 3.0) * (c * c);
+        qp[k] = sp;
+        qm[k] = sm;
+    }
+    double ap[3], am[3], sap = 0.0, sam = 0.0;
+    for (int k = 0; k < 3; k++) {
+        ap[k] = dp[k] / sq(eps + beta[k]);
+        am[k] = dm[k] / sq(eps + beta[k]);
+        sap = sap + ap[k];
+        sam = sam + am[k];
+    }
+    *vm = (ap[0] / sap) * qp[0] + (ap[1] / sap) * qp[1] + (ap[2] / sap) * qp[2];
+    *vp = (am[0] / sam) * qm[0] + (am[1] / sam) * qm[1] + (am[2] / sam) * qm[2];
+}
+
 
 /* v[0..4] = v_{i-2} .. v_{i+2} (cell averages of one primitive).
  * Returns the left-biased value at face i+1/2 (vm) and the right-biased value
@@ -321,11 +501,24 @@ static int load_prim(const grid* g, const double* q, long cell, double* w) {
     return !(qc[0] + qc[1] > 0.0);
 }
 
-/* Contribution of direction d at one cell, from the primitive pencil W
- * (7 cells, i-3..i+3).  L receives
- *   (F_{i-1/2} - F_{i+1/2})/dx_d  for every equation, plus
- *   alpha1_i (u_f,{i+1/2} - u_f,{i-1/2})/dx_d  on the alpha1 row. */
-static int cell_dir(const grid* g, int d, const double* W7, double* L) {
+/* Reconstruction of cell j (index along direction d) of the grid's order. */
+static void weno_cell(const grid* g, int d, long j, const double* v, double* vm, double* vp) {
+    if (g->stretched[d])
+        weno5_nu(&g->tab[d][(j + 1) * NT], g->eps, v, vm, vp);
+    else
+        weno(g, v, vm, vp);
+}
+
+/* Width of cell j along d (uniform: dx_d). */
+static double cell_width(const grid* g, int d, long j) {
+    return g->stretched[d] ? g->h[d][j + 3] : g->dx[d];
+}
+
+/* Contribution of direction d at cell i (index along d), from the primitive
+ * pencil W (7 cells, i-3..i+3).  L receives
+ *   (F_{i-1/2} - F_{i+1/2})/dx_i  for every equation, plus
+ *   alpha1_i (u_f,{i+1/2} - u_f,{i-1/2})/dx_i  on the alpha1 row. */
+static int cell_dir(const grid* g, int d, long i, const double* W7, double* L) {
     int neq = g->neq;
     double vm[3][7], vp[3][7];
     /* WENO at cells i-1, i, i+1 (pencil slots 2, 3, 4) */
@@ -333,13 +526,13 @@ static int cell_dir(const grid* g, int d, const double* W7, double* L) {
         for (int f = 0; f < neq; f++) {
             double v[5];
             for (int s = 0; s < 5; s++) v[s] = W7[(c + s) * neq + f];
-            weno(g, v, &vm[c][f], &vp[c][f]);
+            weno_cell(g, d, i - 1 + c, v, &vm[c][f], &vp[c][f]);
         }
     }
     double Fm[7], Fp[7], ufm, ufp;
     int bad = hllc(g, d, vm[0], vp[1], Fm, &ufm);   /* face i-1/2 */
     bad |= hllc(g, d, vm[1], vp[2], Fp, &ufp);      /* face i+1/2 */
-    double dx = g->dx[d];
+    double dx = cell_width(g, d, i);
     for (int f = 0; f < neq; f++) L[f] = (Fm[f] - Fp[f]) / dx;
     double a1 = W7[3 * neq + IA(g)];
     L[IA(g)] = L[IA(g)] + a1 * (ufp - ufm) / dx;
@@ -368,7 +561,7 @@ static int rhs_dir(const grid* g, int d, const double* q, double* rhs, int first
                 for (int f = 0; f < neq; f++) {
                     double v[5];
                     for (int s = 0; s < 5; s++) v[s] = W[(j + 1 + s) * neq + f];
-                    weno(g, v, &VM[(j + 1) * neq + f], &VP[(j + 1) * neq + f]);
+                    weno_cell(g, d, j, v, &VM[(j + 1) * neq + f], &VP[(j + 1) * neq + f]);
                 }
             }
             /* HLLC at faces j+1/2, j = -1 .. nd-1 (face slot = j + 1) */
@@ -376,9 +569,9 @@ static int rhs_dir(const grid* g, int d, const double* q, double* rhs, int first
                 bad |= hllc(g, d, &VM[(j + 1) * neq], &VP[(j + 2) * neq], &FF[(j + 1) * neq],
                             &UF[j + 1]);
             }
-            double dx = g->dx[d];
             for (long i = 0; i < nd; i++) {
                 long cell = base + i * g->stride[d];
+                double dx = cell_width(g, d, i);
                 double L[7];
                 for (int f = 0; f < neq; f++) L[f] = (FF[i * neq + f] - FF[(i + 1) * neq + f]) / dx;
                 double a1 = W[(i + 3) * neq + IA(g)];
@@ -420,7 +613,9 @@ static int rhs_all(const grid* g, const double* q, double* rhs) {
 int orc_neq(const orc_params* p) {
     grid g;
     int st = make_grid(p, &g);
-    return st ? st : g.neq;
+    if (st) return st;
+    free_grid(&g);
+    return g.neq;
 }
 
 int orc_prim_to_cons(const orc_params* p, const double* w, double* q) {
@@ -433,6 +628,7 @@ int orc_prim_to_cons(const orc_params* p, const double* w, double* q) {
         prim_to_cons(&g, wc, qc);
         for (int f = 0; f < g.neq; f++) q[(long)f * g.ncell + c] = qc[f];
     }
+    free_grid(&g);
     return ORC_OK;
 }
 
@@ -445,6 +641,7 @@ int orc_cons_to_prim(const orc_params* p, const double* q, double* w) {
         load_prim(&g, q, c, wc);
         for (int f = 0; f < g.neq; f++) w[(long)f * g.ncell + c] = wc[f];
     }
+    free_grid(&g);
     return ORC_OK;
 }
 
@@ -453,7 +650,9 @@ int orc_rhs(const orc_params* p, const double* q, double* rhs) {
     grid g;
     int st = make_grid(p, &g);
     if (st) return st;
-    return rhs_all(&g, q, rhs);
+    st = rhs_all(&g, q, rhs);
+    free_grid(&g);
+    return st;
 }
 
 /* L(q) at selected cells only (flat cell indices), out[k*neq + f].  Uses the
@@ -465,7 +664,10 @@ int orc_rhs_points(const orc_params* p, const double* q, const long* cells, long
     int neq = g.neq, bad = 0;
     for (long k = 0; k < npts; k++) {
         long cell = cells[k];
-        if (cell < 0 || cell >= g.ncell) return ORC_EINVAL;
+        if (cell < 0 || cell >= g.ncell) {
+            free_grid(&g);
+            return ORC_EINVAL;
+        }
         long idx[3];
         long rem = cell;
         for (int d = 0; d < 3; d++) { idx[d] = rem % g.n[d]; rem /= g.n[d]; }
@@ -477,7 +679,7 @@ int orc_rhs_points(const orc_params* p, const double* q, const long* cells, long
                 long src = bc_map(idx[d] + s - 3, g.n[d], g.periodic[d]);
                 bad |= load_prim(&g, q, base + src * g.stride[d], &W7[s * neq]);
             }
-            bad |= cell_dir(&g, d, W7, L);
+            bad |= cell_dir(&g, d, idx[d], W7, L);
             for (int f = 0; f < neq; f++) acc[f] = (d == 0) ? L[f] : acc[f] + L[f];
         }
         for (int f = 0; f < neq; f++) {
@@ -485,6 +687,7 @@ int orc_rhs_points(const orc_params* p, const double* q, const long* cells, long
             if (isnan(acc[f]) || isinf(acc[f])) bad = 1;
         }
     }
+    free_grid(&g);
     return bad ? ORC_ENONPHYSICAL : ORC_OK;
 }
 
@@ -505,10 +708,11 @@ int orc_max_wavespeed(const orc_params* p, const double* q, double* S_out) {
         if (!(rho > 0.0) || !(c2 > 0.0)) bad = 1;
         double cs = sqrt(c2);
         double s = 0.0;
-        for (int d = 0; d < g.ndim; d++) s = s + (fabs(w[2 + d]) + cs) / g.dx[d];
+        for (int d = 0; d < g.ndim; d++) s = s + (fabs(w[2 + d]) + cs) / cell_width(&g, d, (c / g.stride[d]) % g.n[d]);
         if (s > S) S = s;
     }
     *S_out = S;
+    free_grid(&g);
     return bad ? ORC_ENONPHYSICAL : ORC_OK;
 }
 
@@ -524,7 +728,11 @@ int orc_step_dt(const orc_params* p, double* q, double dt) {
     double* L = malloc(sizeof(double) * m);
     double* q1 = malloc(sizeof(double) * m);
     double* q2 = malloc(sizeof(double) * m);
-    if (!L || !q1 || !q2) { free(L); free(q1); free(q2); return ORC_ENOMEM; }
+    if (!L || !q1 || !q2) {
+        free(L); free(q1); free(q2);
+        free_grid(&g);
+        return ORC_ENOMEM;
+    }
     int bad = 0;
     bad |= rhs_all(&g, q, L) != ORC_OK;
     for (long i = 0; i < m; i++) q1[i] = q[i] + dt * L[i];
@@ -533,6 +741,7 @@ int orc_step_dt(const orc_params* p, double* q, double dt) {
     bad |= rhs_all(&g, q2, L) != ORC_OK;
     for (long i = 0; i < m; i++) q[i] = (1.0 / 3.0) * q[i] + (2.0 / 3.0) * (q2[i] + dt * L[i]);
     free(L); free(q1); free(q2);
+    free_grid(&g);
     return bad ? ORC_ENONPHYSICAL : ORC_OK;
 }
 
@@ -583,11 +792,21 @@ void orc_weno5_cell(double eps, const double* v5, double* vm, double* vp) { weno
 
 void orc_weno3_cell(double eps, const double* v5, double* vm, double* vp) { weno3(eps, v5, vm, vp); }
 
+/* Non-uniform WENO5 table (NT doubles, layout of cell_table) of a cell from
+ * the widths w5 of cells i-2 .. i+2; returns 1 if degenerate. */
+int orc_weno5_table(const double* w5, double* T) { return cell_table(w5, T); }
+
+/* Non-uniform WENO5 face values of a cell from its table. */
+void orc_weno5_nu_cell(const double* T, double eps, const double* v5, double* vm, double* vp) {
+    weno5_nu(T, eps, v5, vm, vp);
+}
+
 int orc_hllc_face(const orc_params* p, int dir, const double* wL, const double* wR, double* F,
                   double* uf) {
     grid g;
     int st = make_grid(p, &g);
     if (st) return st;
+    free_grid(&g);
     if (dir < 0 || dir >= g.ndim) return ORC_EINVAL;
     return hllc(&g, dir, wL, wR, F, uf) ? ORC_ENONPHYSICAL : ORC_OK;
 }
@@ -596,6 +815,7 @@ int orc_sound_speed2(const orc_params* p, const double* w, double* c2) {
     grid g;
     int st = make_grid(p, &g);
     if (st) return st;
+    free_grid(&g);
     double G, Pi;
     mixture(&g, w[IA(&g)], &G, &Pi);
     *c2 = sound2(G, Pi, w[0] + w[1], w[IE(&g)]);

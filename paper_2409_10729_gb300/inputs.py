@@ -340,3 +340,22 @@ def embed_1d(p1d: dict, w1d: np.ndarray, axis: int, m: int = 4):
     w[5] = line[3]
     w[6] = a1
     return p, w
+
+
+def tanh_edges(n: int, lo: float, hi: float, centre: float, strength: float = 10.0, refine: float = 0.5):
+    """Cell edges of a grid refined around x = centre with a hyperbolic
+    tangent (Sec. III-A's local mesh refinement): the width is proportional to
+    1 - refine sech^2(strength (xi - xi_c)) in the uniform index coordinate
+    xi, so cells near the centre are (1 - refine) times the far cells and the
+    transition is smooth.  Integrated in closed form:
+        s(xi) = xi - (refine/strength) (tanh(strength (xi - xi_c)) + tanh(strength xi_c)),
+    normalised to [lo, hi]; the end edges are exactly lo and hi."""
+    xi_c = (centre - lo) / (hi - lo)
+    xi = np.arange(n + 1) / n
+
+    def s(x):
+        return x - (refine / strength) * (np.tanh(strength * (x - xi_c)) + np.tanh(strength * xi_c))
+
+    e = lo + (hi - lo) * s(xi) / s(1.0)
+    e[0], e[-1] = lo, hi
+    return e

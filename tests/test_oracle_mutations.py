@@ -43,12 +43,20 @@ MUTATIONS = {
     "rk_stage2": ("0.75 * q[i] + 0.25 * (q1[i] + dt * L[i])", "0.75 * q[i] + 0.25 * (q1[i] + 0.5 * dt * L[i])"),
     "rk_stage3": ("(2.0 / 3.0) * (q2[i] + dt * L[i])", "(2.0 / 3.0) * (q2[i] + dt * L[i] * 0.99)"),
     "periodic_ghosts": ("if (periodic) {", "if (0) {"),
-    "wavespeed_dx": ("s = s + (fabs(w[2 + d]) + cs) / g.dx[d];", "s = s + (fabs(w[2 + d]) + cs);"),
+    "wavespeed_dx": ("(fabs(w[2 + d]) + cs) / cell_width(&g, d, (c / g.stride[d]) % g.n[d]);",
+                     "(fabs(w[2 + d]) + cs);"),
     "weno3_linear_weight": ("double a0 = (1.0 / 3.0) / sq(eps + b0);", "double a0 = (2.0 / 3.0) / sq(eps + b0);"),
     "weno3_candidate_index": ("double p1 = (v[2] + v[3]) / 2.0;", "double p1 = (v[2] + v[4]) / 2.0;"),
     "weno3_beta_index": ("double b1 = sq(v[3] - v[2]);", "double b1 = sq(v[3] - v[1]);"),
     "weno3_right_candidate": ("p1 = (3.0 * v[2] - v[3]) / 2.0;", "p1 = (3.0 * v[2] + v[3]) / 2.0;"),
     "weno_order_ignored": ("    if (g->order == 3)\n        weno3(", "    if (0)\n        weno3("),
+    "nu_beta_coefficient": ("beta[k] = b * b + (13.0 / 3.0) * (c * c);", "beta[k] = b * b + (13.0 / 12.0) * (c * c);"),
+    "nu_linear_weight": ("dp[2] = Qp[4] / cp[3 * 2 + 2];", "dp[2] = Qp[4] / cp[3 * 2 + 1];"),
+    "nu_face_value": ("cp[3 * k + j] = Mi[j] + 0.5 * Mi[3 + j] + 0.25 * Mi[6 + j];",
+                      "cp[3 * k + j] = Mi[j] + 0.5 * Mi[3 + j] + 0.5 * Mi[6 + j];"),
+    "nu_global_width": ("double dx = cell_width(g, d, i);", "double dx = g->dx[d];"),
+    "nu_wavespeed_width": ("(fabs(w[2 + d]) + cs) / cell_width(&g, d, (c / g.stride[d]) % g.n[d]);",
+                           "(fabs(w[2 + d]) + cs) / g.dx[d];"),
 }
 
 
@@ -64,7 +72,7 @@ def test_planted_mistake_is_caught(name, tmp_path):
                     str(so), str(csrc), "-lm"], check=True)
     env = dict(os.environ, MFC5_ORACLE_LIB=str(so))
     suites = [os.path.join(ROOT, "tests", f) for f in
-              ("test_oracle_elements.py", "test_oracle_physics.py")]
+              ("test_oracle_elements.py", "test_oracle_physics.py", "test_oracle_stretched.py")]
     r = subprocess.run([sys.executable, "-m", "pytest", *suites, "-x", "-q", "-p", "no:cacheprovider",
                         "-m", "not gpu"], cwd=ROOT, env=env, capture_output=True, text=True,
                        timeout=600)
