@@ -139,6 +139,20 @@ int mfc_kernel_time(mfc_ctx* ctx, int index, const char** name, double* ms, long
  * (MFC_MLP_NPARAMS floats): W1[32][5], b1[32], W2[32][32], b2[32], w3[32], b3. */
 #define MFC_MLP_NPARAMS 1281
 
+/* Makes direction `dir` (0 <= dir < ndim) non-uniform: `edges` is a host
+ * array of the n[dir] + 1 cell edges, strictly increasing (e.g. the
+ * tanh-refined grids of Sec. III-A); lo/hi of the params no longer apply to
+ * that direction.  The reconstruction becomes Shu's WENO5 for non-uniform
+ * cells (per-cell candidate coefficients, smoothness indicators and linear
+ * weights, computed here from the edges), and the flux divergence and CFL
+ * bound use each cell's own width; ghost-cell widths follow the BC (copied
+ * at transmissive, wrapped at periodic boundaries).  Only WENO5 in the FP64,
+ * FP64-fast and mixed forms: MFC_EINVAL for WENO3 or MFC_GATED contexts, a
+ * bad direction, or edges that are not strictly increasing.  Synchronises
+ * the context's stream; the wave speed of a state already set is
+ * recomputed.  The edges are copied. */
+int mfc_set_grid(mfc_ctx* ctx, int dir, const double* edges);
+
 /* Sets the gate weights of a MFC_GATED context (host array of n =
  * MFC_MLP_NPARAMS finite floats, copied).  Stepping a gated context before
  * this returns MFC_ESTATE. */

@@ -30,7 +30,7 @@ EXTRA = {"sweep_mixed.cu": FAST32, "sweep_gated.cu": FAST32,
 # needs build(force=True)
 USER_FLAGS = os.environ.get("MFC5_NVCC_FLAGS", "").split()
 UNITS = ["capi.cu", "aux.cu", "sweep_fp64.cu", "sweep_fp64x.cu", "sweep_mixed.cu", "sweep_gated.cu", "mlp.cu",
-         "noalloc.cu"]
+         "noalloc.cu", "grid.cu"]
 
 
 def nvcc() -> str:

@@ -56,10 +56,11 @@ __global__ void make_mixed_state_kernel(const double* __restrict__ qn, float* __
 // reference operation order.
 template <int NDIM>
 __global__ void wavespeed_kernel(const double* __restrict__ q, long long nc, Eos e, double dx0, double dx1,
-                                 double dx2, double rdx0, double rdx1, double rdx2, DevCtrl* ctrl) {
+                                 double dx2, double rdx0, double rdx1, double rdx2, DevCtrl* ctrl, int n0, int n1,
+                                 Geom3 g) {
     using FL = Fields<NDIM>;
-    const double dx[3] = {dx0, dx1, dx2};
-    const double rdx[3] = {rdx0, rdx1, rdx2};
+    double dx[3] = {dx0, dx1, dx2};
+    double rdx[3] = {rdx0, rdx1, rdx2};
     double smax = 0.0;
     bool bad = false;
     long long stride = (long long)gridDim.x * blockDim.x;
@@ -73,6 +74,14 @@ __global__ void wavespeed_kernel(const double* __restrict__ q, long long nc, Eos
             double v[FL::NEQ];
 #pragma unroll
             for (int f = 0; f < FL::NEQ; ++f) v[f] = __ldg(q + f * nc + c);
+            // non-uniform directions: the cell's own width
+            const long long ci[3] = {c % n0, (c / n0) % n1, c / ((long long)n0 * n1)};
+#pragma unroll
+            for (int d = 0; d < NDIM; ++d)
+                if (g.cw[d]) {
+                    dx[d] = __ldg(g.cw[d] + ci[d]);
+                    rdx[d] = __ldg(g.crw[d] + ci[d]);
+                }
             double s = exact::cell_wavespeed<NDIM>(e, v, dx, rdx, bad);
             smax = s > smax ? s : smax;
         }
@@ -118,17 +127,26 @@ cudaError_t launch_make_mixed_state(int ndim, const double* qn, float* s0, long 
     return cudaGetLastError();
 }
 
-cudaError_t launch_wavespeed(int ndim, const double* q, long long nc, const double* dx, const double* rdx,
+cudaError_t launch_wavespeed(int ndim, const double* q, const int* n, const double* const* cw,
+                             const double* const* crw, long long nc, const double* dx, const double* rdx,
                              const Eos& e, DevCtrl* ctrl, cudaStream_t s) {
     cudaError_t err = cudaMemsetAsync(&ctrl->S_bits, 0, sizeof(unsigned long long), s);
     if (err != cudaSuccess) return err;
+    Geom3 g3;
+    for (int d = 0; d < 3; ++d) {
+        g3.cw[d] = cw ? cw[d] : nullptr;
+        g3.crw[d] = crw ? crw[d] : nullptr;
+    }
     unsigned g = aux_blocks(nc);
     if (ndim == 1)
-        wavespeed_kernel<1><<<g, kAuxThreads, 0, s>>>(q, nc, e, dx[0], dx[1], dx[2], rdx[0], rdx[1], rdx[2], ctrl);
+        wavespeed_kernel<1><<<g, kAuxThreads, 0, s>>>(q, nc, e, dx[0], dx[1], dx[2], rdx[0], rdx[1], rdx[2], ctrl,
+                                                       n[0], n[1], g3);
     else if (ndim == 2)
-        wavespeed_kernel<2><<<g, kAuxThreads, 0, s>>>(q, nc, e, dx[0], dx[1], dx[2], rdx[0], rdx[1], rdx[2], ctrl);
+        wavespeed_kernel<2><<<g, kAuxThreads, 0, s>>>(q, nc, e, dx[0], dx[1], dx[2], rdx[0], rdx[1], rdx[2], ctrl,
+                                                       n[0], n[1], g3);
     else
-        wavespeed_kernel<3><<<g, kAuxThreads, 0, s>>>(q, nc, e, dx[0], dx[1], dx[2], rdx[0], rdx[1], rdx[2], ctrl);
+        wavespeed_kernel<3><<<g, kAuxThreads, 0, s>>>(q, nc, e, dx[0], dx[1], dx[2], rdx[0], rdx[1], rdx[2], ctrl,
+                                                       n[0], n[1], g3);
     return cudaGetLastError();
 }
 

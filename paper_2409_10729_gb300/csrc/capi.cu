@@ -56,6 +56,11 @@ struct mfc_ctx {
     int last_cuda;
     bool have_gate;
     float* gate_w;     // gated form: network weights (device)
+    // non-uniform directions (mfc_set_grid); null where uniform
+    void* gtab[3];     // WENO5 tables of cells -1 .. n (FP64, or FP32 for the FP32 forms)
+    double* gw[3];     // cell widths
+    double* grw[3];    // RN(1/width)
+    float* grw32[3];   // 1/width in FP32
 };
 
 #define CK(call)                                   \
@@ -105,6 +110,11 @@ static void free_all(mfc_ctx* c) {
     void* bufs[] = {c->qn, c->sa, c->sb, c->s0, c->acc, c->tmp64, c->ctrl, c->gate_w};
     for (void* b : bufs)
         if (b) cudaFree(b);
+    for (int d = 0; d < 3; ++d) {
+        void* g[] = {c->gtab[d], c->gw[d], c->grw[d], c->grw32[d]};
+        for (void* b : g)
+            if (b) cudaFree(b);
+    }
     if (c->ctrl_h) cudaFreeHost(c->ctrl_h);
     for (int i = 0; i <= kMaxTimedLaunches; ++i)
         if (c->ev[i]) cudaEventDestroy(c->ev[i]);
@@ -205,12 +215,18 @@ static SweepArgs base_args(mfc_ctx* ctx) {
     a.acc = ctx->acc;
     a.qn = ctx->qn;
     a.gate_w = ctx->gate_w;
+    for (int d = 0; d < 3; ++d) {
+        a.cw[d] = ctx->gw[d];
+        a.crw[d] = ctx->grw[d];
+        a.crw32[d] = ctx->grw32[d];
+    }
     return a;
 }
 
 static cudaError_t launch_sweep(mfc_ctx* ctx, int dir, int mode, SweepArgs a, cudaStream_t s) {
     a.periodic = ctx->periodic[dir];
     a.seg = ctx->seg[dir];
+    a.tab = ctx->gtab[dir];
     switch (ctx->form) {
         case FORM_FP64_EXACT: return launch_sweep_fp64x(ctx->ndim, dir, mode, a, s);
         case FORM_FP64_FAST: return launch_sweep_fp64(ctx->ndim, dir, mode, a, s);
@@ -280,7 +296,8 @@ static int ensure_graph(mfc_ctx* ctx) {
 static int after_state_change(mfc_ctx* ctx) {
     if (fp32_state(ctx))
         CK(launch_make_mixed_state(ctx->ndim, ctx->qn, ctx->s0, ctx->ncell, ctx->eos, ctx->stream));
-    CK(launch_wavespeed(ctx->ndim, ctx->qn, ctx->ncell, ctx->dx, ctx->rdx, ctx->eos, ctx->ctrl, ctx->stream));
+    CK(launch_wavespeed(ctx->ndim, ctx->qn, ctx->n, ctx->gw, ctx->grw, ctx->ncell, ctx->dx, ctx->rdx, ctx->eos,
+                        ctx->ctrl, ctx->stream));
     ctx->have_state = true;
     return MFC_OK;
 }
@@ -376,7 +393,8 @@ extern "C" int mfc_max_wavespeed(mfc_ctx* ctx, double* s) {
     if (!ctx->have_state) return MFC_ESTATE;
     int st = write_ctrl_params(ctx, 0.0, 0.0);
     if (st) return st;
-    CK(launch_wavespeed(ctx->ndim, ctx->qn, ctx->ncell, ctx->dx, ctx->rdx, ctx->eos, ctx->ctrl, ctx->stream));
+    CK(launch_wavespeed(ctx->ndim, ctx->qn, ctx->n, ctx->gw, ctx->grw, ctx->ncell, ctx->dx, ctx->rdx, ctx->eos,
+                        ctx->ctrl, ctx->stream));
     st = read_ctrl(ctx);
     if (st) return st;
     unsigned long long bits = ctx->ctrl_h->S_bits;
@@ -419,6 +437,52 @@ extern "C" int mfc_step_rk3(mfc_ctx* ctx, double cfl, int nsteps, double* t_adva
 extern "C" int mfc_step_rk3_dt(mfc_ctx* ctx, double dt, int nsteps) {
     if (!ctx || nsteps < 0 || !(dt > 0.0) || !isfinite(dt)) return MFC_EINVAL;
     return run_steps(ctx, 0.0, dt, nsteps, NULL);
+}
+
+extern "C" int mfc_set_grid(mfc_ctx* ctx, int dir, const double* edges) {
+    if (!ctx || !edges || dir < 0 || dir >= ctx->ndim) return MFC_EINVAL;
+    if (ctx->form == FORM_GATED || ctx->p.weno_order == 3) return MFC_EINVAL;
+    const int n = ctx->n[dir];
+    std::vector<double> tab, width;
+    if (!build_grid_tables(edges, n, ctx->periodic[dir], tab, width)) return MFC_EINVAL;
+    std::vector<double> rw(n);
+    std::vector<float> rw32(n), tab32;
+    for (int j = 0; j < n; ++j) {
+        rw[j] = 1.0 / width[j];
+        rw32[j] = (float)rw[j];
+    }
+    const bool fp32 = fp32_state(ctx);
+    if (fp32) tab32.assign(tab.begin(), tab.end());
+    CK(cudaStreamSynchronize(ctx->stream));
+    void* old[] = {ctx->gtab[dir], ctx->gw[dir], ctx->grw[dir], ctx->grw32[dir]};
+    for (void* b : old)
+        if (b) cudaFree(b);
+    ctx->gtab[dir] = ctx->gw[dir] = ctx->grw[dir] = nullptr;
+    ctx->grw32[dir] = nullptr;
+    const size_t tb = tab.size() * (fp32 ? sizeof(float) : sizeof(double));
+    if (cudaMalloc(&ctx->gtab[dir], tb) != cudaSuccess ||
+        cudaMalloc((void**)&ctx->gw[dir], n * sizeof(double)) != cudaSuccess ||
+        cudaMalloc((void**)&ctx->grw[dir], n * sizeof(double)) != cudaSuccess ||
+        cudaMalloc((void**)&ctx->grw32[dir], n * sizeof(float)) != cudaSuccess)
+        return MFC_ENOMEM;
+    CK(cudaMemcpy(ctx->gtab[dir], fp32 ? (const void*)tab32.data() : (const void*)tab.data(), tb,
+                  cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->gw[dir], width.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->grw[dir], rw.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(ctx->grw32[dir], rw32.data(), n * sizeof(float), cudaMemcpyHostToDevice));
+    // the captured step refers to the old buffers; the wave speed of the
+    // current state changes with the widths
+    if (ctx->gexec) {
+        cudaGraphExecDestroy(ctx->gexec);
+        ctx->gexec = NULL;
+    }
+    ctx->graph_ok = false;
+    if (ctx->have_state) {
+        CK(launch_wavespeed(ctx->ndim, ctx->qn, ctx->n, ctx->gw, ctx->grw, ctx->ncell, ctx->dx, ctx->rdx, ctx->eos,
+                            ctx->ctrl, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
+    return MFC_OK;
 }
 
 extern "C" int mfc_set_mlp_weights(mfc_ctx* ctx, const float* w, int n) {

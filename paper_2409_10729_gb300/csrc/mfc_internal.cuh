@@ -3,9 +3,29 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "physics.cuh"
 
 namespace mfc5 {
+
+// Non-uniform grids: doubles per cell of a WENO5 table -- face-value
+// functionals at i+1/2 (3 stencils x 3 values) and i-1/2, the functionals b
+// and c of each stencil's quadratic (smoothness b^2 + 13/3 c^2), and the
+// linear weights at i+1/2 and i-1/2.
+constexpr int kTabDoubles = 42;
+
+// Per-direction cell widths and RN(1/width) of a non-uniform grid (null where
+// the direction is uniform), by value for kernels.
+struct Geom3 {
+    const double* cw[3];
+    const double* crw[3];
+};
+
+// Tables of cells -1 .. n and widths of cells 0 .. n-1 of one direction from
+// its n + 1 cell edges (false: edges not strictly increasing, or degenerate).
+bool build_grid_tables(const double* edges, int n, int periodic, std::vector<double>& tab,
+                       std::vector<double>& width);
 
 // Step control block, resident in device memory so that consecutive steps
 // need no host round trip (dt of step n+1 comes from S(q^{n+1}), reduced by
@@ -51,6 +71,11 @@ struct SweepArgs {
     int stage;            // 1, 2, 3
     DevCtrl* ctrl;
     const float* gate_w;  // gated form: the 1281 network weights (device)
+    // non-uniform grids (null where the direction is uniform):
+    const void* tab;      // sweep direction: WENO5 tables of cells -1 .. n (FP64 or FP32 per form)
+    const double* cw[3];  // per direction: cell widths
+    const double* crw[3]; // per direction: RN(1/width)
+    const float* crw32[3];  // per direction: 1/width in FP32 (FP32 forms)
 };
 
 // Arithmetic forms of the sweep kernels:
@@ -74,7 +99,8 @@ cudaError_t launch_gate_samples(int ndim, const double* q, const int* n, const i
 cudaError_t launch_prim_to_cons(int ndim, double* q, long long ncell, const Eos& e, cudaStream_t s);
 cudaError_t launch_make_mixed_state(int ndim, const double* qn, float* s0, long long ncell,
                                     const Eos& e, cudaStream_t s);
-cudaError_t launch_wavespeed(int ndim, const double* q, long long ncell, const double* dx,
+cudaError_t launch_wavespeed(int ndim, const double* q, const int* n, const double* const* cw,
+                             const double* const* crw, long long ncell, const double* dx,
                              const double* rdx, const Eos& e, DevCtrl* ctrl, cudaStream_t s);
 cudaError_t launch_step_begin(DevCtrl* ctrl, cudaStream_t s);
 cudaError_t launch_f32_to_f64(const float* src, double* dst, long long count, cudaStream_t s);

@@ -133,6 +133,51 @@ __device__ __forceinline__ void weno3(R v1, R v2, R v3, R eps, R& vm, R& vp) {
     vp = v2 - (ap0 * d1 + ap1 * d2) * Dm * r;
 }
 
+// WENO5-JS on a non-uniform grid from the cell's table T (kTabDoubles values,
+// the same for every lane of a warp): candidates q_k^+- = cp_k.v, cm_k.v,
+// smoothness beta_k = (B_k.v)^2 + 13/3 (C_k.v)^2, linear weights dp, dm;
+// weights scaled as in weno5 (product form in FP64, relative to the smoothest
+// stencil in FP32), one reciprocal for both faces.
+template <typename R>
+__device__ __forceinline__ void weno5_tab(const R* __restrict__ T, R v0, R v1, R v2, R v3, R v4, R eps, R& vm,
+                                          R& vp) {
+    const R v[5] = {v0, v1, v2, v3, v4};
+    R qp[3], qm[3], s[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        R a = R(0), b = R(0), c = R(0), d = R(0);
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const R x = v[k + j];
+            a += __ldg(T + 3 * k + j) * x;
+            b += __ldg(T + 9 + 3 * k + j) * x;
+            c += __ldg(T + 18 + 3 * k + j) * x;
+            d += __ldg(T + 27 + 3 * k + j) * x;
+        }
+        qp[k] = a;
+        qm[k] = b;
+        const R beta = c * c + R(13.0 / 3.0) * (d * d);
+        s[k] = (eps + beta) * (eps + beta);
+    }
+    R m0, m1, m2;
+    if constexpr (sizeof(R) == 8) {
+        m0 = s[1] * s[2];
+        m1 = s[0] * s[2];
+        m2 = s[0] * s[1];
+    } else {
+        R smin = fminf(s[0], fminf(s[1], s[2]));
+        m0 = __fdividef(smin, s[0]);
+        m1 = __fdividef(smin, s[1]);
+        m2 = __fdividef(smin, s[2]);
+    }
+    const R ap0 = __ldg(T + 36) * m0, ap1 = __ldg(T + 37) * m1, ap2 = __ldg(T + 38) * m2;
+    const R am0 = __ldg(T + 39) * m0, am1 = __ldg(T + 40) * m1, am2 = __ldg(T + 41) * m2;
+    const R Dp = ap0 + ap1 + ap2, Dm = am0 + am1 + am2;
+    const R r = rdiv(R(1), Dp * Dm);
+    vm = (ap0 * qp[0] + ap1 * qp[1] + ap2 * qp[2]) * Dm * r;
+    vp = (am0 * qm[0] + am1 * qm[1] + am2 * qm[2]) * Dp * r;
+}
+
 // ---------------------------------------------------------------- HLLC
 // Flux through a face normal to DIR from reconstructed primitive states
 // (alpha1 rho1, alpha2 rho2, u_k, p, alpha1).  uf receives the velocity of the

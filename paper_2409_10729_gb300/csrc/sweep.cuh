@@ -163,6 +163,29 @@ __device__ __forceinline__ R cell_wavespeed(const EosR<R>& e, const R* w, const 
     return s;
 }
 
+// Width, RN(1/width) and 1/width of a cell in every direction (uniform, or
+// the cell's own on non-uniform directions); the cell is `i` along the sweep
+// direction DIR, `ia` along the lanes' direction and `b` along the third.
+template <int DIR>
+__device__ __forceinline__ void cell_geometry(const SweepArgs& a, int i, int ia, int b, double* dx, double* rdx,
+                                              double* idx) {
+    int c[3];
+    c[DIR] = i;
+    c[DIR == 0 ? 1 : 0] = ia;
+    c[DIR == 2 ? 1 : 2] = b;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        dx[d] = a.dx[d];
+        rdx[d] = a.rdx[d];
+        idx[d] = a.inv_dx[d];
+        if (a.cw[d]) {
+            dx[d] = __ldg(a.cw[d] + c[d]);
+            rdx[d] = __ldg(a.crw[d] + c[d]);
+            idx[d] = rdx[d];
+        }
+    }
+}
+
 // Shared-memory staging of the x-direction sweep: per warp, per loaded
 // field, 32 rows x CH cells (CH * sizeof(R) = 32 bytes), padded by one
 // element per row so that the 32 lanes read 32 different banks.
@@ -600,7 +623,11 @@ sweep_kernel(const SweepArgs a) {
             }
         }
         if (use_weno) {
-            if (GATED || a.order == 5) {
+            if (!GATED && a.tab) {   // non-uniform direction: this cell's table (uniform over the warp)
+                const R* T = static_cast<const R*>(a.tab) + (long long)(j + 1) * kTabDoubles;
+#pragma unroll
+                for (int f = 0; f < NEQ; ++f) weno5_tab<R>(T, W[0][f], W[1][f], W[2][f], W[3][f], W[4][f], eps, vm[f], vp[f]);
+            } else if (GATED || a.order == 5) {
 #pragma unroll
                 for (int f = 0; f < NEQ; ++f) {
                     if constexpr (EXACT)
@@ -625,14 +652,23 @@ sweep_kernel(const SweepArgs a) {
                 R L[NEQ];
                 if constexpr (EXACT) {
                     // (F_{i-1/2} - F_{i+1/2})/dx, then + alpha1 (u_f+ - u_f-)/dx
-                    const double dx = a.dx[DIR], rdx = a.rdx[DIR];
+                    double dx = a.dx[DIR], rdx = a.rdx[DIR];
+                    if (a.cw[DIR]) {   // non-uniform: the cell's own width
+                        dx = __ldg(a.cw[DIR] + (j - 1));
+                        rdx = __ldg(a.crw[DIR] + (j - 1));
+                    }
 #pragma unroll
                     for (int f = 0; f < NEQ; ++f) L[f] = exact::div_rcp(Fprev[f] - F[f], dx, rdx);
                     L[IA] = L[IA] + exact::div_rcp(alphaCell * (uf - ufPrev), dx, rdx);
                 } else {
+                    R idx = inv_dx;
+                    if (a.cw[DIR]) {
+                        if constexpr (sizeof(R) == 8) idx = __ldg(a.crw[DIR] + (j - 1));
+                        else idx = __ldg(a.crw32[DIR] + (j - 1));
+                    }
 #pragma unroll
-                    for (int f = 0; f < NEQ; ++f) L[f] = (Fprev[f] - F[f]) * inv_dx;
-                    L[IA] += alphaCell * (uf - ufPrev) * inv_dx;
+                    for (int f = 0; f < NEQ; ++f) L[f] = (Fprev[f] - F[f]) * idx;
+                    L[IA] += alphaCell * (uf - ufPrev) * idx;
                 }
                 const long long c = base + (long long)(j - 1) * ss;
                 if constexpr (OSTAGE_ON) {
@@ -691,12 +727,14 @@ sweep_kernel(const SweepArgs a) {
                         for (int f = 0; f < NEQ; ++f) out[f * nc + c] = qnew[f];
                         if (a.stage == 3) {
                             R s;
+                            double dx3[3], rdx3[3], idx3[3];
+                            cell_geometry<DIR>(a, j - 1, active ? ia : na - 1, b, dx3, rdx3, idx3);
                             if constexpr (EXACT) {
-                                s = exact::cell_wavespeed<NDIM>(a.eos, qnew, a.dx, a.rdx, bad);
+                                s = exact::cell_wavespeed<NDIM>(a.eos, qnew, dx3, rdx3, bad);
                             } else {
                                 double wn[NEQ];
                                 to_prim<NDIM>(er, qnew, wn);
-                                s = cell_wavespeed<NDIM, double>(er, wn, a.inv_dx, bad);
+                                s = cell_wavespeed<NDIM, double>(er, wn, idx3, bad);
                             }
                             smax = s > smax ? s : smax;
                         }
@@ -718,7 +756,9 @@ sweep_kernel(const SweepArgs a) {
                             for (int f = 0; f < NEQ; ++f) v[f] = q32[f];
                             v[IE] = pnew;
                             to_prim<NDIM>(er, v, wn);
-                            R s = cell_wavespeed<NDIM, float>(er, wn, a.inv_dx, bad);
+                            double dx3[3], rdx3[3], idx3[3];
+                            cell_geometry<DIR>(a, j - 1, active ? ia : na - 1, b, dx3, rdx3, idx3);
+                            R s = cell_wavespeed<NDIM, float>(er, wn, idx3, bad);
                             smax = s > smax ? s : smax;
                         }
                     }

@@ -76,6 +76,7 @@ def lib() -> ctypes.CDLL:
             "mfc_gate_stats": ([vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
                                 ctypes.POINTER(ctypes.c_longlong)], ip),
             "mfc_gate_flat": ([vp, ctypes.POINTER(ctypes.c_longlong)], ip),
+            "mfc_set_grid": ([vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double)], ip),
             "mfc_gate_samples": ([vp, vp, vp, ctypes.c_longlong, ctypes.c_float,
                                   ctypes.POINTER(ctypes.c_longlong)], ip),
             "mfc_mlp_nparams": ([], ip),
@@ -162,6 +163,10 @@ class Solver:
         if st != MFC_OK:
             raise MfcError(st, "mfc_create")
         self.ctx = handle
+        # non-uniform directions given as cell edges in the params dict
+        for d, e in enumerate(p.get("edges") or []):
+            if e is not None and d < int(p["ndim"]):
+                self.set_grid(d, e)
 
     def close(self):
         if getattr(self, "ctx", None):
@@ -180,6 +185,12 @@ class Solver:
         return st
 
     # -- state -------------------------------------------------------------
+    def set_grid(self, direction: int, edges):
+        """Non-uniform cell edges (n[direction] + 1, strictly increasing) for one direction."""
+        e = np.ascontiguousarray(edges, dtype=np.float64)
+        self._check(lib().mfc_set_grid(self.ctx, int(direction), e.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+                    "mfc_set_grid")
+
     def set_state(self, q):
         ptr, dev = _ptr(q, self.size)
         return self._check(lib().mfc_set_state(self.ctx, ptr, dev), "mfc_set_state")

@@ -21,6 +21,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=1)
     ap.add_argument("--cfl", type=float, default=0.4)
     ap.add_argument("--weno-order", type=int, choices=[3, 5], default=5)
+    ap.add_argument("--stretch", action="store_true",
+                    help="tanh-refined grid in every direction (cells at the centre half as wide)")
     args = ap.parse_args()
 
     import torch
@@ -37,6 +39,9 @@ def main():
     else:
         p, w = I.air_water_shock_tube(args.n)
     p = dict(p, weno_order=args.weno_order)
+    if args.stretch:
+        p["edges"] = [I.tanh_edges(p["n"][d], p["lo"][d], p["hi"][d], 0.5 * (p["lo"][d] + p["hi"][d]),
+                                   strength=8.0, refine=0.5) if d < p["ndim"] else None for d in range(3)]
     s = mfc.Solver(p, args.form)
     if args.form == "gated":
         import numpy as np

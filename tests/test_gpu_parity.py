@@ -376,3 +376,100 @@ def test_weno3_mixed_form_error_against_oracle():
     assert err.max() <= 2e-4, err
     l1 = np.abs(q - qo).reshape(6, -1).sum(1) / np.abs(qo).reshape(6, -1).sum(1)
     assert l1[[0, 1, 4, 5]].max() <= 1e-6, l1
+
+
+# ---------------------------------------------------------------- non-uniform grids
+# Directions refined with a hyperbolic tangent (Sec. III-A), set through
+# mfc_set_grid from the same edges the oracle takes.  The library computes its
+# WENO5 tables independently of the oracle (Lagrange derivatives of the
+# primitive function versus cell-average solves), so the FP64 forms are held
+# to 1e-12 rather than bit-identity; the wave speed (same widths, IEEE
+# quotients) must still match exactly.
+
+def _stretch(p, dirs, centre=0.45, strength=10.0, refine=0.6):
+    edges = [None, None, None]
+    for d in dirs:
+        edges[d] = I.tanh_edges(p["n"][d], p["lo"][d], p["hi"][d], p["lo"][d] + centre * (p["hi"][d] - p["lo"][d]),
+                                strength=strength, refine=refine)
+    return dict(p, edges=edges)
+
+
+NU_SMALL = [(1, [40], 1, (0,)), (1, [37], 0, (0,)), (2, [21, 13], 1, (0, 1)), (2, [33, 19], 0, (1,)),
+            (3, [13, 9, 11], 1, (0, 1, 2)), (3, [40, 11, 35], 0, (0, 2))]
+
+
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("ndim,n,bc,dirs", NU_SMALL)
+def test_stretched_rhs_and_wavespeed_parity(ndim, n, bc, dirs, form):
+    p, w = _case(ndim, n, bc, seed=ndim + 40)
+    p = _stretch(p, dirs)
+    s = solver(p, form)
+    s.set_state_prim(w)
+    L = s.rhs()
+    q = O.prim_to_cons(p, w)
+    Lo = O.rhs(p, q)
+    So = O.max_wavespeed(p, q)
+    assert not np.allclose(Lo, O.rhs(dict(p, edges=None), q), rtol=1e-6, atol=0)
+    assert rhs_err(p, L, Lo, q, So).max() <= TOL
+    if form == "fp64":
+        assert s.max_wavespeed() == So
+    else:
+        assert s.max_wavespeed() == pytest.approx(So, rel=1e-14)
+
+
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("ndim,n,bc,dirs", NU_SMALL)
+def test_stretched_cfl_steps_parity(ndim, n, bc, dirs, form):
+    p, w = _case(ndim, n, bc, seed=ndim + 45)
+    p = _stretch(p, dirs)
+    s = solver(p, form)
+    s.set_state_prim(w)
+    t = s.step_rk3(0.4, 5)
+    qo, to = O.run_cfl(p, O.prim_to_cons(p, w), 0.4, 5)
+    assert rel_err(s.get_state(), qo).max() <= TOL
+    assert abs(t - to) <= 1e-13 * to
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_stretched_shock_water_column(form):
+    """2-D shock / water column at 128x64, both directions refined around the
+    column, 100 steps: within 1e-11 (independent tables; rounding differences
+    of 1e-16 grow through the shock-interface interaction as on uniform grids)."""
+    p, w = I.shock_water_column(128, 64)
+    p = _stretch(p, (0, 1), centre=0.3, strength=8.0, refine=0.5)
+    s = solver(p, form)
+    s.set_state_prim(w)
+    t = s.step_rk3(0.4, 100)
+    qo, to = oracle_run("stretched_column_128x64x100", p, w, 100)
+    assert rel_err(s.get_state(), qo).max() <= 1e-11
+    assert abs(t - to) <= 1e-12 * to
+
+
+def test_stretched_mixed_form_error_against_oracle():
+    p, w = I.shock_water_column(128, 64)
+    p = _stretch(p, (0, 1), centre=0.3, strength=8.0, refine=0.5)
+    s = solver(p, "mixed")
+    s.set_state_prim(w)
+    s.step_rk3(0.4, 100)
+    qo, _ = oracle_run("stretched_column_128x64x100", p, w, 100)
+    q = s.get_state()
+    # FP32 stencils at the shock: ~2e-4 of the momentum scale (as on uniform grids)
+    assert rel_err(q, qo).max() <= 5e-4
+    l1 = np.abs(q - qo).reshape(6, -1).sum(1) / np.abs(qo).reshape(6, -1).sum(1)
+    assert l1[[0, 1, 4, 5]].max() <= 1e-6, l1
+
+
+def test_set_grid_rejections():
+    from paper_2409_10729_gb300 import mfc
+    p, w = _case(2, [16, 8], 0)
+    e = I.tanh_edges(16, 0.0, 1.0, 0.5)
+    bad = e.copy()
+    bad[5] = bad[4]
+    s = solver(p, "fp64")
+    for d, edges in ((2, e), (0, bad)):
+        with pytest.raises(mfc.MfcError):
+            s.set_grid(d, edges)
+    for kw, prec in ((dict(weno_order=3), "fp64"), ({}, "gated")):
+        g = solver(dict(p, **kw), prec)
+        with pytest.raises(mfc.MfcError):
+            g.set_grid(0, e)
