@@ -6,8 +6,8 @@ and the fraction of the HBM roofline it reaches, for the FP64 form (reference
 operation order, bit-identical to the oracle; the headline value), the
 reorganised FP64 form, the mixed-precision form (512^3) and the MLP-gated
 form (256^3, trained weights from paper_2409_10729_gb300/gate_weights.npy),
-plus the third-order reconstruction option (WENO3-JS) in the FP64 (256^3)
-and mixed (512^3) forms.
+plus the third-order reconstruction option (WENO3-JS) and a tanh-refined
+(non-uniform) grid in the FP64 (256^3) and mixed (512^3) forms.
 
 Workload (per GPU): the 3-D shock / droplet array, 256^3 cells, 7 equations,
 FP64, SSP-RK3 at CFL 0.4 (the timed "step" is one RK3 step = 3 RHS
@@ -139,6 +139,14 @@ def read_traffic(kernel: str):
     return None
 
 
+def stretched(p):
+    """The same case on a grid refined with a hyperbolic tangent about the
+    domain centre in every direction (Sec. III-A): cells there half as wide."""
+    from paper_2409_10729_gb300 import inputs as I
+    return dict(p, edges=[I.tanh_edges(p["n"][d], p["lo"][d], p["hi"][d], 0.5 * (p["lo"][d] + p["hi"][d]),
+                                       strength=8.0, refine=0.5) if d < p["ndim"] else None for d in range(3)])
+
+
 def gate_weights():
     import numpy as np
     return np.load(os.path.join(ROOT, "paper_2409_10729_gb300", "gate_weights.npy"))
@@ -188,7 +196,7 @@ def time_form(form, p, w, steps, warmup, device_index, rank, world):
 def roofline_for(form, res, peak_alu, alu_src, hbm_peak, hbm_src):
     """Roofline object for the dominant kernel of one form."""
     kt = res["kernels"]
-    base = form.replace("_weno3", "")
+    base = form.replace("_weno3", "").replace("_stretched", "")
     name = max((k for k in kt if kt[k][1] > 0), key=lambda k: kt[k][0])
     total_ms, count = kt[name]
     avg_s = total_ms / count * 1e-3
@@ -305,12 +313,17 @@ def run_ours(args):
     # the third-order reconstruction option (weno_order = 3), same workload
     forms["fp64_weno3"] = time_form("fp64", dict(p, weno_order=3), w, max(2, args.steps // 2), args.warmup,
                                     local, rank, world)
+    # a tanh-refined grid in every direction (cells at the centre half as wide)
+    forms["fp64_stretched"] = time_form("fp64", stretched(p), w, max(2, args.steps // 2), args.warmup,
+                                        local, rank, world)
     if not args.no_mixed:
         forms["gated"] = time_form("gated", p, w, args.steps, args.warmup, local, rank, world)
         pm, wm = I.shock_droplets(512)
         forms["mixed"] = time_form("mixed", pm, wm, max(2, args.steps // 2), args.warmup, local, rank, world)
         forms["mixed_weno3"] = time_form("mixed", dict(pm, weno_order=3), wm, max(2, args.steps // 2),
                                          args.warmup, local, rank, world)
+        forms["mixed_stretched"] = time_form("mixed", stretched(pm), wm, max(2, args.steps // 2), args.warmup,
+                                             local, rank, world)
         del wm
 
     # end to end through the C ABI with pinned host buffers: per step, copy
