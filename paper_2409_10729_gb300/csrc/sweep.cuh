@@ -166,7 +166,7 @@ __device__ __forceinline__ R cell_wavespeed(const EosR<R>& e, const R* w, const 
 // Width, RN(1/width) and 1/width of a cell in every direction (uniform, or
 // the cell's own on non-uniform directions); the cell is `i` along the sweep
 // direction DIR, `ia` along the lanes' direction and `b` along the third.
-template <int DIR>
+template <int DIR, bool NU>
 __device__ __forceinline__ void cell_geometry(const SweepArgs& a, int i, int ia, int b, double* dx, double* rdx,
                                               double* idx) {
     int c[3];
@@ -178,7 +178,7 @@ __device__ __forceinline__ void cell_geometry(const SweepArgs& a, int i, int ia,
         dx[d] = a.dx[d];
         rdx[d] = a.rdx[d];
         idx[d] = a.inv_dx[d];
-        if (a.cw[d]) {
+        if (NU && a.cw[d]) {
             dx[d] = __ldg(a.cw[d] + c[d]);
             rdx[d] = __ldg(a.crw[d] + c[d]);
             idx[d] = rdx[d];
@@ -419,7 +419,9 @@ constexpr int sweep_min_blocks() {
     return per128 * 128 / sweep_threads(DIR);
 }
 
-template <int NDIM, int DIR, int MODE, int FORM>
+// NU: some direction of the grid is non-uniform (tables, per-cell widths);
+// the uniform-grid kernels carry none of that code.
+template <int NDIM, int DIR, int MODE, int FORM, bool NU>
 __global__ void __launch_bounds__(sweep_threads(DIR), sweep_min_blocks<FORM, MODE, DIR>())
 sweep_kernel(const SweepArgs a) {
     using R = FormReal<FORM>;
@@ -623,7 +625,7 @@ sweep_kernel(const SweepArgs a) {
             }
         }
         if (use_weno) {
-            if (!GATED && a.tab) {   // non-uniform direction: this cell's table (uniform over the warp)
+            if (NU && a.tab) {   // non-uniform direction: this cell's table (uniform over the warp)
                 const R* T = static_cast<const R*>(a.tab) + (long long)(j + 1) * kTabDoubles;
 #pragma unroll
                 for (int f = 0; f < NEQ; ++f) weno5_tab<R>(T, W[0][f], W[1][f], W[2][f], W[3][f], W[4][f], eps, vm[f], vp[f]);
@@ -653,7 +655,7 @@ sweep_kernel(const SweepArgs a) {
                 if constexpr (EXACT) {
                     // (F_{i-1/2} - F_{i+1/2})/dx, then + alpha1 (u_f+ - u_f-)/dx
                     double dx = a.dx[DIR], rdx = a.rdx[DIR];
-                    if (a.cw[DIR]) {   // non-uniform: the cell's own width
+                    if (NU && a.cw[DIR]) {   // non-uniform: the cell's own width
                         dx = __ldg(a.cw[DIR] + (j - 1));
                         rdx = __ldg(a.crw[DIR] + (j - 1));
                     }
@@ -662,7 +664,7 @@ sweep_kernel(const SweepArgs a) {
                     L[IA] = L[IA] + exact::div_rcp(alphaCell * (uf - ufPrev), dx, rdx);
                 } else {
                     R idx = inv_dx;
-                    if (a.cw[DIR]) {
+                    if (NU && a.cw[DIR]) {
                         if constexpr (sizeof(R) == 8) idx = __ldg(a.crw[DIR] + (j - 1));
                         else idx = __ldg(a.crw32[DIR] + (j - 1));
                     }
@@ -728,7 +730,7 @@ sweep_kernel(const SweepArgs a) {
                         if (a.stage == 3) {
                             R s;
                             double dx3[3], rdx3[3], idx3[3];
-                            cell_geometry<DIR>(a, j - 1, active ? ia : na - 1, b, dx3, rdx3, idx3);
+                            cell_geometry<DIR, NU>(a, j - 1, active ? ia : na - 1, b, dx3, rdx3, idx3);
                             if constexpr (EXACT) {
                                 s = exact::cell_wavespeed<NDIM>(a.eos, qnew, dx3, rdx3, bad);
                             } else {
@@ -757,7 +759,7 @@ sweep_kernel(const SweepArgs a) {
                             v[IE] = pnew;
                             to_prim<NDIM>(er, v, wn);
                             double dx3[3], rdx3[3], idx3[3];
-                            cell_geometry<DIR>(a, j - 1, active ? ia : na - 1, b, dx3, rdx3, idx3);
+                            cell_geometry<DIR, NU>(a, j - 1, active ? ia : na - 1, b, dx3, rdx3, idx3);
                             R s = cell_wavespeed<NDIM, float>(er, wn, idx3, bad);
                             smax = s > smax ? s : smax;
                         }
@@ -841,7 +843,14 @@ cudaError_t launch_one(long long warps, const SweepArgs& a, cudaStream_t s) {
     constexpr int T = sweep_threads(DIR);
     const long long blocks = (warps * 32 + T - 1) / T;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    sweep_kernel<NDIM, DIR, MODE, FORM><<<(unsigned)blocks, T, 0, s>>>(a);
+    const bool nu = a.cw[0] || a.cw[1] || a.cw[2];
+    if constexpr (FORM != FORM_GATED) {
+        if (nu) {
+            sweep_kernel<NDIM, DIR, MODE, FORM, true><<<(unsigned)blocks, T, 0, s>>>(a);
+            return cudaGetLastError();
+        }
+    }
+    sweep_kernel<NDIM, DIR, MODE, FORM, false><<<(unsigned)blocks, T, 0, s>>>(a);
     return cudaGetLastError();
 }
 
