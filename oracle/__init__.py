@@ -52,11 +52,12 @@ class OrcParams(ctypes.Structure):
         ("lo", ctypes.c_double * 3),
         ("hi", ctypes.c_double * 3),
         ("bc", (ctypes.c_int * 2) * 3),
-        ("gamma", ctypes.c_double * 2),
-        ("pi_inf", ctypes.c_double * 2),
+        ("gamma", ctypes.c_double * 4),
+        ("pi_inf", ctypes.c_double * 4),
         ("weno_eps", ctypes.c_double),
         ("weno_order", ctypes.c_int),
         ("edges", ctypes.POINTER(ctypes.c_double) * 3),
+        ("nfluids", ctypes.c_int),
     ]
 
 
@@ -110,7 +111,11 @@ def params(p: dict) -> OrcParams:
         s.hi[d] = float(p["hi"][d])
         s.bc[d][0] = int(p["bc"][d][0])
         s.bc[d][1] = int(p["bc"][d][1])
-    for i in range(2):
+    nf = len(p["gamma"])
+    if nf < 2 or nf > 4 or len(p["pi_inf"]) != nf:
+        raise ValueError("2 to 4 fluids, one gamma and one pi_inf each")
+    s.nfluids = nf
+    for i in range(nf):
         s.gamma[i] = float(p["gamma"][i])
         s.pi_inf[i] = float(p["pi_inf"][i])
     s.weno_eps = float(p.get("weno_eps", 1e-6))

@@ -23,8 +23,10 @@
  * division and square root.
  *
  * Layout: conservative q[f][z][y][x] (x fastest), interior cells only.
- *   f = 0: alpha1 rho1, 1: alpha2 rho2, 2..2+d-1: rho u_k, 2+d: rho E,
- *   3+d: alpha1.  neq = d + 4.
+ * With N fluids (N = 2 by default, up to 4):
+ *   f = 0..N-1: alpha_i rho_i, N..N+d-1: rho u_k, N+d: rho E,
+ *   N+d+1 .. 2N+d-1: alpha_1 .. alpha_{N-1}  (alpha_N = 1 - sum).  neq = 2N + d.
+ * For two fluids: alpha1 rho1, alpha2 rho2, rho u_k, rho E, alpha1 (neq = d + 4).
  * Primitive w has the same slots with u_k in place of rho u_k and p in place
  * of rho E.
  */
@@ -43,23 +45,26 @@ typedef struct {
     double lo[3];      /* domain lower corner */
     double hi[3];      /* domain upper corner */
     int bc[3][2];      /* per dimension, per side: 0 transmissive, 1 periodic */
-    double gamma[2];   /* ratio of specific heats, fluid 1 and fluid 2 */
-    double pi_inf[2];  /* stiffness, fluid 1 and fluid 2 */
+    double gamma[4];   /* ratio of specific heats of fluids 1 .. N */
+    double pi_inf[4];  /* stiffness of fluids 1 .. N */
     double weno_eps;   /* WENO epsilon (absolute) */
     int weno_order;    /* 5 (WENO5-JS) or 3 (WENO3-JS); 0 means 5 */
     const double* edges[3];  /* optional: the n[d]+1 cell edges of direction d, strictly increasing
                                 (a non-uniform, e.g. tanh-stretched, grid; WENO5 only); NULL: uniform */
+    int nfluids;       /* N, 2 .. 4; 0 means 2 */
 } orc_params;
 
+#define NEQ_MAX 16
+
 typedef struct {
-    int ndim, neq;
+    int ndim, neq, nf;
     long n[3];
     long stride[3];
     long ncell;
     double dx[3];
     int periodic[3];
-    double g1, g2;     /* 1/(gamma_i - 1) */
-    double P1, P2;     /* gamma_i pi_i/(gamma_i - 1) */
+    double gk[4];      /* 1/(gamma_i - 1) */
+    double Pk[4];      /* gamma_i pi_i/(gamma_i - 1) */
     double eps;
     int order;         /* WENO order, 3 or 5 */
     int stretched[3];  /* direction d has a non-uniform grid */
@@ -69,8 +74,9 @@ typedef struct {
 
 #define NT 42          /* doubles per cell of a non-uniform WENO5 table (see make_tables) */
 
-#define IE(g) (2 + (g)->ndim)
-#define IA(g) (3 + (g)->ndim)
+#define IU(g) ((g)->nf)                   /* first momentum / velocity slot */
+#define IE(g) ((g)->nf + (g)->ndim)        /* energy / pressure slot */
+#define IA(g) ((g)->nf + (g)->ndim + 1)    /* alpha_1 (alpha_2 .. alpha_{N-1} follow) */
 
 static void free_grid(grid* g) {
     for (int d = 0; d < 3; d++) {
@@ -88,8 +94,10 @@ static int make_grid(const orc_params* p, grid* g) {
         g->h[d] = g->tab[d] = NULL;
     }
     if (!p || p->ndim < 1 || p->ndim > 3) return ORC_EINVAL;
+    if (p->nfluids != 0 && (p->nfluids < 2 || p->nfluids > 4)) return ORC_EINVAL;
+    g->nf = p->nfluids == 0 ? 2 : p->nfluids;
     g->ndim = p->ndim;
-    g->neq = p->ndim + 4;
+    g->neq = 2 * g->nf + p->ndim;
     g->ncell = 1;
     for (int d = 0; d < 3; d++) {
         long n = p->n[d];
@@ -108,15 +116,15 @@ static int make_grid(const orc_params* p, grid* g) {
             g->periodic[d] = (b0 == 1);
         }
     }
-    for (int i = 0; i < 2; i++)
+    for (int i = 0; i < g->nf; i++)
         if (!(p->gamma[i] > 1.0) || !(p->pi_inf[i] >= 0.0)) return ORC_EINVAL;
     if (!(p->weno_eps > 0.0)) return ORC_EINVAL;
     if (p->weno_order != 0 && p->weno_order != 3 && p->weno_order != 5) return ORC_EINVAL;
     g->order = p->weno_order == 3 ? 3 : 5;
-    g->g1 = 1.0 / (p->gamma[0] - 1.0);
-    g->g2 = 1.0 / (p->gamma[1] - 1.0);
-    g->P1 = p->gamma[0] * p->pi_inf[0] / (p->gamma[0] - 1.0);
-    g->P2 = p->gamma[1] * p->pi_inf[1] / (p->gamma[1] - 1.0);
+    for (int i = 0; i < g->nf; i++) {
+        g->gk[i] = 1.0 / (p->gamma[i] - 1.0);
+        g->Pk[i] = p->gamma[i] * p->pi_inf[i] / (p->gamma[i] - 1.0);
+    }
     g->eps = p->weno_eps;
     for (int d = 0; d < g->ndim; d++) {
         if (!p->edges[d]) continue;
@@ -130,12 +138,26 @@ static int make_grid(const orc_params* p, grid* g) {
 /* ---- equation of state (Sec. II-A) -------------------------------------- */
 
 /* Mixture rules: Gamma = sum alpha_i/(gamma_i-1), Pi = sum alpha_i gamma_i
- * pi_i/(gamma_i-1), with alpha2 = 1 - alpha1.  Then rho E = Gamma p + Pi +
- * rho|u|^2/2, the stiffened-gas relation with the kinetic energy added. */
-static void mixture(const grid* g, double a1, double* G, double* Pi) {
-    double a2 = 1.0 - a1;
-    *G = a1 * g->g1 + a2 * g->g2;
-    *Pi = a1 * g->P1 + a2 * g->P2;
+ * pi_i/(gamma_i-1), with alpha_N = 1 - alpha_1 - ... - alpha_{N-1} (the
+ * carried fractions a[0..N-2]).  Then rho E = Gamma p + Pi + rho|u|^2/2, the
+ * stiffened-gas relation with the kinetic energy added. */
+static void mixture(const grid* g, const double* a, double* G, double* Pi) {
+    double aN = 1.0 - a[0];
+    for (int i = 1; i < g->nf - 1; i++) aN = aN - a[i];
+    double sg = a[0] * g->gk[0], sp = a[0] * g->Pk[0];
+    for (int i = 1; i < g->nf - 1; i++) {
+        sg = sg + a[i] * g->gk[i];
+        sp = sp + a[i] * g->Pk[i];
+    }
+    *G = sg + aN * g->gk[g->nf - 1];
+    *Pi = sp + aN * g->Pk[g->nf - 1];
+}
+
+/* Mixture density, the sum of the partial densities. */
+static double mix_rho(const grid* g, const double* q) {
+    double rho = q[0] + q[1];
+    for (int i = 2; i < g->nf; i++) rho = rho + q[i];
+    return rho;
 }
 
 static double kinetic(const grid* g, double rho, const double* u) {
@@ -145,32 +167,30 @@ static double kinetic(const grid* g, double rho, const double* u) {
 }
 
 static void cons_to_prim(const grid* g, const double* q, double* w) {
-    double rho = q[0] + q[1];
+    double rho = mix_rho(g, q);
     double u[3] = {0.0, 0.0, 0.0};
-    for (int k = 0; k < g->ndim; k++) u[k] = q[2 + k] / rho;
+    for (int k = 0; k < g->ndim; k++) u[k] = q[IU(g) + k] / rho;
     double ke = kinetic(g, rho, u);
     double G, Pi;
-    mixture(g, q[IA(g)], &G, &Pi);
+    mixture(g, &q[IA(g)], &G, &Pi);
     double p = (q[IE(g)] - ke - Pi) / G;
-    w[0] = q[0];
-    w[1] = q[1];
-    for (int k = 0; k < g->ndim; k++) w[2 + k] = u[k];
+    for (int i = 0; i < g->nf; i++) w[i] = q[i];
+    for (int k = 0; k < g->ndim; k++) w[IU(g) + k] = u[k];
     w[IE(g)] = p;
-    w[IA(g)] = q[IA(g)];
+    for (int i = 0; i < g->nf - 1; i++) w[IA(g) + i] = q[IA(g) + i];
 }
 
 static void prim_to_cons(const grid* g, const double* w, double* q) {
-    double rho = w[0] + w[1];
+    double rho = mix_rho(g, w);
     double u[3] = {0.0, 0.0, 0.0};
-    for (int k = 0; k < g->ndim; k++) u[k] = w[2 + k];
+    for (int k = 0; k < g->ndim; k++) u[k] = w[IU(g) + k];
     double ke = kinetic(g, rho, u);
     double G, Pi;
-    mixture(g, w[IA(g)], &G, &Pi);
-    q[0] = w[0];
-    q[1] = w[1];
-    for (int k = 0; k < g->ndim; k++) q[2 + k] = rho * u[k];
+    mixture(g, &w[IA(g)], &G, &Pi);
+    for (int i = 0; i < g->nf; i++) q[i] = w[i];
+    for (int k = 0; k < g->ndim; k++) q[IU(g) + k] = rho * u[k];
     q[IE(g)] = G * w[IE(g)] + Pi + ke;
-    q[IA(g)] = w[IA(g)];
+    for (int i = 0; i < g->nf - 1; i++) q[IA(g) + i] = w[IA(g) + i];
 }
 
 /* Mixture sound speed squared, c^2 = ((Gamma+1) p + Pi)/(Gamma rho). */
@@ -404,16 +424,16 @@ static void weno(const grid* g, const double* v, double* vm, double* vp) {
 /* ---- HLLC (Sec. II-B; Toro's three-wave approximate solver) -------------- */
 
 typedef struct {
-    double rho, u[3], p, a1, G, Pi, E, c2;
+    double rho, u[3], p, a[3], G, Pi, E, c2;   /* a: the carried volume fractions */
 } face_state;
 
 static void face_from_prim(const grid* g, const double* w, face_state* s) {
-    s->rho = w[0] + w[1];
+    s->rho = mix_rho(g, w);
     s->u[0] = s->u[1] = s->u[2] = 0.0;
-    for (int k = 0; k < g->ndim; k++) s->u[k] = w[2 + k];
+    for (int k = 0; k < g->ndim; k++) s->u[k] = w[IU(g) + k];
     s->p = w[IE(g)];
-    s->a1 = w[IA(g)];
-    mixture(g, s->a1, &s->G, &s->Pi);
+    for (int i = 0; i < g->nf - 1; i++) s->a[i] = w[IA(g) + i];
+    mixture(g, s->a, &s->G, &s->Pi);
     s->E = s->G * s->p + s->Pi + kinetic(g, s->rho, s->u);
     s->c2 = sound2(s->G, s->Pi, s->rho, s->p);
 }
@@ -421,30 +441,28 @@ static void face_from_prim(const grid* g, const double* w, face_state* s) {
 /* Physical flux of the face state K in direction dir. */
 static void phys_flux(const grid* g, int dir, const double* w, const face_state* K, double* F) {
     double un = K->u[dir];
-    F[0] = w[0] * un;
-    F[1] = w[1] * un;
-    for (int k = 0; k < g->ndim; k++) F[2 + k] = K->rho * K->u[k] * un;
-    F[2 + dir] = F[2 + dir] + K->p;
+    for (int i = 0; i < g->nf; i++) F[i] = w[i] * un;
+    for (int k = 0; k < g->ndim; k++) F[IU(g) + k] = K->rho * K->u[k] * un;
+    F[IU(g) + dir] = F[IU(g) + dir] + K->p;
     F[IE(g)] = (K->E + K->p) * un;
-    F[IA(g)] = K->a1 * un;
+    for (int i = 0; i < g->nf - 1; i++) F[IA(g) + i] = K->a[i] * un;
 }
 
 /* HLLC star-region flux F*_K = F_K + S_K (q*_K - q_K); the volume-fraction
- * slot carries alpha1_K S* (advection with the contact velocity). */
+ * slots carry alpha_i,K S* (advection with the contact velocity). */
 static void star_flux(const grid* g, int dir, const double* w, const face_state* K,
                       double SK, double Ss, double* F) {
     double un = K->u[dir];
     phys_flux(g, dir, w, K, F);
     double chi = (SK - un) / (SK - Ss);
-    F[0] = F[0] + SK * (chi * w[0] - w[0]);
-    F[1] = F[1] + SK * (chi * w[1] - w[1]);
+    for (int i = 0; i < g->nf; i++) F[i] = F[i] + SK * (chi * w[i] - w[i]);
     for (int k = 0; k < g->ndim; k++) {
         double mstar = (k == dir) ? chi * K->rho * Ss : chi * K->rho * K->u[k];
-        F[2 + k] = F[2 + k] + SK * (mstar - K->rho * K->u[k]);
+        F[IU(g) + k] = F[IU(g) + k] + SK * (mstar - K->rho * K->u[k]);
     }
     double Estar = chi * (K->E + (Ss - un) * (K->rho * Ss + K->p / (SK - un)));
     F[IE(g)] = F[IE(g)] + SK * (Estar - K->E);
-    F[IA(g)] = K->a1 * Ss;
+    for (int i = 0; i < g->nf - 1; i++) F[IA(g) + i] = K->a[i] * Ss;
 }
 
 /* Flux through one face from the reconstructed primitive states wL, wR.
@@ -495,10 +513,10 @@ static long bc_map(long j, long n, int periodic) {
 /* Primitives of one cell; returns 1 when the cell's mixture density is not
  * positive (or NaN). */
 static int load_prim(const grid* g, const double* q, long cell, double* w) {
-    double qc[7];
+    double qc[NEQ_MAX];
     for (int f = 0; f < g->neq; f++) qc[f] = q[(long)f * g->ncell + cell];
     cons_to_prim(g, qc, w);
-    return !(qc[0] + qc[1] > 0.0);
+    return !(mix_rho(g, qc) > 0.0);
 }
 
 /* Reconstruction of cell j (index along direction d) of the grid's order. */
@@ -520,7 +538,7 @@ static double cell_width(const grid* g, int d, long j) {
  *   alpha1_i (u_f,{i+1/2} - u_f,{i-1/2})/dx_i  on the alpha1 row. */
 static int cell_dir(const grid* g, int d, long i, const double* W7, double* L) {
     int neq = g->neq;
-    double vm[3][7], vp[3][7];
+    double vm[3][NEQ_MAX], vp[3][NEQ_MAX];
     /* WENO at cells i-1, i, i+1 (pencil slots 2, 3, 4) */
     for (int c = 0; c < 3; c++) {
         for (int f = 0; f < neq; f++) {
@@ -529,13 +547,15 @@ static int cell_dir(const grid* g, int d, long i, const double* W7, double* L) {
             weno_cell(g, d, i - 1 + c, v, &vm[c][f], &vp[c][f]);
         }
     }
-    double Fm[7], Fp[7], ufm, ufp;
+    double Fm[NEQ_MAX], Fp[NEQ_MAX], ufm, ufp;
     int bad = hllc(g, d, vm[0], vp[1], Fm, &ufm);   /* face i-1/2 */
     bad |= hllc(g, d, vm[1], vp[2], Fp, &ufp);      /* face i+1/2 */
     double dx = cell_width(g, d, i);
     for (int f = 0; f < neq; f++) L[f] = (Fm[f] - Fp[f]) / dx;
-    double a1 = W7[3 * neq + IA(g)];
-    L[IA(g)] = L[IA(g)] + a1 * (ufp - ufm) / dx;
+    for (int i = 0; i < g->nf - 1; i++) {
+        double ai = W7[3 * neq + IA(g) + i];
+        L[IA(g) + i] = L[IA(g) + i] + ai * (ufp - ufm) / dx;
+    }
     return bad;
 }
 
@@ -572,10 +592,12 @@ static int rhs_dir(const grid* g, int d, const double* q, double* rhs, int first
             for (long i = 0; i < nd; i++) {
                 long cell = base + i * g->stride[d];
                 double dx = cell_width(g, d, i);
-                double L[7];
+                double L[NEQ_MAX];
                 for (int f = 0; f < neq; f++) L[f] = (FF[i * neq + f] - FF[(i + 1) * neq + f]) / dx;
-                double a1 = W[(i + 3) * neq + IA(g)];
-                L[IA(g)] = L[IA(g)] + a1 * (UF[i + 1] - UF[i]) / dx;
+                for (int k = 0; k < g->nf - 1; k++) {
+                    double ak = W[(i + 3) * neq + IA(g) + k];
+                    L[IA(g) + k] = L[IA(g) + k] + ak * (UF[i + 1] - UF[i]) / dx;
+                }
                 for (int f = 0; f < neq; f++) {
                     double* r = &rhs[(long)f * g->ncell + cell];
                     *r = first ? L[f] : *r + L[f];
@@ -622,7 +644,7 @@ int orc_prim_to_cons(const orc_params* p, const double* w, double* q) {
     grid g;
     int st = make_grid(p, &g);
     if (st) return st;
-    double wc[7], qc[7];
+    double wc[NEQ_MAX], qc[NEQ_MAX];
     for (long c = 0; c < g.ncell; c++) {
         for (int f = 0; f < g.neq; f++) wc[f] = w[(long)f * g.ncell + c];
         prim_to_cons(&g, wc, qc);
@@ -636,7 +658,7 @@ int orc_cons_to_prim(const orc_params* p, const double* q, double* w) {
     grid g;
     int st = make_grid(p, &g);
     if (st) return st;
-    double wc[7];
+    double wc[NEQ_MAX];
     for (long c = 0; c < g.ncell; c++) {
         load_prim(&g, q, c, wc);
         for (int f = 0; f < g.neq; f++) w[(long)f * g.ncell + c] = wc[f];
@@ -671,9 +693,9 @@ int orc_rhs_points(const orc_params* p, const double* q, const long* cells, long
         long idx[3];
         long rem = cell;
         for (int d = 0; d < 3; d++) { idx[d] = rem % g.n[d]; rem /= g.n[d]; }
-        double acc[7];
+        double acc[NEQ_MAX];
         for (int d = 0; d < g.ndim; d++) {
-            double W7[7 * 7], L[7];
+            double W7[7 * NEQ_MAX], L[NEQ_MAX];
             long base = cell - idx[d] * g.stride[d];
             for (int s = 0; s < 7; s++) {
                 long src = bc_map(idx[d] + s - 3, g.n[d], g.periodic[d]);
@@ -698,17 +720,18 @@ int orc_max_wavespeed(const orc_params* p, const double* q, double* S_out) {
     if (st) return st;
     double S = 0.0;
     int bad = 0;
-    double w[7];
+    double w[NEQ_MAX];
     for (long c = 0; c < g.ncell; c++) {
         bad |= load_prim(&g, q, c, w);
-        double rho = w[0] + w[1];
+        double rho = mix_rho(&g, w);
         double G, Pi;
-        mixture(&g, w[IA(&g)], &G, &Pi);
+        mixture(&g, &w[IA(&g)], &G, &Pi);
         double c2 = sound2(G, Pi, rho, w[IE(&g)]);
         if (!(rho > 0.0) || !(c2 > 0.0)) bad = 1;
         double cs = sqrt(c2);
         double s = 0.0;
-        for (int d = 0; d < g.ndim; d++) s = s + (fabs(w[2 + d]) + cs) / cell_width(&g, d, (c / g.stride[d]) % g.n[d]);
+        for (int d = 0; d < g.ndim; d++)
+            s = s + (fabs(w[IU(&g) + d]) + cs) / cell_width(&g, d, (c / g.stride[d]) % g.n[d]);
         if (s > S) S = s;
     }
     *S_out = S;
@@ -817,7 +840,7 @@ int orc_sound_speed2(const orc_params* p, const double* w, double* c2) {
     if (st) return st;
     free_grid(&g);
     double G, Pi;
-    mixture(&g, w[IA(&g)], &G, &Pi);
-    *c2 = sound2(G, Pi, w[0] + w[1], w[IE(&g)]);
+    mixture(&g, &w[IA(&g)], &G, &Pi);
+    *c2 = sound2(G, Pi, mix_rho(&g, w), w[IE(&g)]);
     return ORC_OK;
 }

@@ -44,8 +44,13 @@ def make_params(ndim, n, lo, hi, bc, gamma=(WATER[0], AIR[0]), pi_inf=(WATER[1],
             "pi_inf": [float(p) for p in pi_inf], "weno_eps": float(weno_eps)}
 
 
+def nfluids_of(p: dict) -> int:
+    return len(p["gamma"])
+
+
 def neq_of(p: dict) -> int:
-    return p["ndim"] + 4
+    """2N + ndim: N partial densities, ndim momenta, energy, N - 1 volume fractions."""
+    return 2 * nfluids_of(p) + p["ndim"]
 
 
 def shape_of(p: dict):
@@ -79,6 +84,27 @@ def assemble(p: dict, alpha1, rho1, rho2, vel, pres) -> np.ndarray:
         w[2 + k] = vel[k]
     w[2 + d] = pres
     w[3 + d] = a1
+    return w
+
+
+def assemble_n(p: dict, alphas, rhos, vel, pres) -> np.ndarray:
+    """Primitive array of an N-fluid state (N = len(rhos)): alphas holds the
+    volume fractions of fluids 1 .. N-1 (fluid N takes the rest), rhos the N
+    phase densities, vel the ndim velocity components, pres the pressure."""
+    shp = shape_of(p)
+    nf = nfluids_of(p)
+    assert len(rhos) == nf and len(alphas) == nf - 1
+    w = np.empty(shp, dtype=np.float64)
+    d = p["ndim"]
+    a = [np.broadcast_to(x, shp[1:]) for x in alphas]
+    rest = 1.0 - sum(a)
+    for i in range(nf):
+        w[i] = (a[i] if i < nf - 1 else rest) * rhos[i]
+    for k in range(d):
+        w[nf + k] = vel[k]
+    w[nf + d] = pres
+    for i in range(nf - 1):
+        w[nf + d + 1 + i] = a[i]
     return w
 
 

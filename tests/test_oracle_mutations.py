@@ -15,10 +15,10 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "mfc5_oracle.c")
 
 MUTATIONS = {
-    "drop_alpha_source": ("L[IA(g)] = L[IA(g)] + a1 * (UF[i + 1] - UF[i]) / dx;", "L[IA(g)] = L[IA(g)];"),
-    "source_sign": ("L[IA(g)] = L[IA(g)] + a1 * (UF[i + 1] - UF[i]) / dx;",
-                    "L[IA(g)] = L[IA(g)] - a1 * (UF[i + 1] - UF[i]) / dx;"),
-    "alpha_flux_uK": ("F[IA(g)] = K->a1 * Ss;", "F[IA(g)] = K->a1 * un;"),
+    "drop_alpha_source": ("L[IA(g) + k] = L[IA(g) + k] + ak * (UF[i + 1] - UF[i]) / dx;", "L[IA(g) + k] = L[IA(g) + k];"),
+    "source_sign": ("L[IA(g) + k] = L[IA(g) + k] + ak * (UF[i + 1] - UF[i]) / dx;",
+                    "L[IA(g) + k] = L[IA(g) + k] - ak * (UF[i + 1] - UF[i]) / dx;"),
+    "alpha_flux_uK": ("F[IA(g) + i] = K->a[i] * Ss;", "F[IA(g) + i] = K->a[i] * un;"),
     "beta0_coefficient": ("0.25 * sq(v[0] - 4.0 * v[1] + 3.0 * v[2])", "0.25 * sq(v[0] - 4.0 * v[1] + 2.0 * v[2])"),
     "linear_weight": ("double a0 = 0.1 / sq(eps + b0);", "double a0 = 0.3 / sq(eps + b0);"),
     "candidate_index": ("double p1 = (-v[1] + 5.0 * v[2] + 2.0 * v[3]) / 6.0;",
@@ -34,17 +34,17 @@ MUTATIONS = {
     "davis_right": ("double SR = (uL + cL > uR + cR) ? uL + cL : uR + cR;", "double SR = uR + cR;"),
     "face_velocity": ("        star_flux(g, dir, wL, &L, SL, Ss, F);\n        *uf = Ss;",
                       "        star_flux(g, dir, wL, &L, SL, Ss, F);\n        *uf = uL;"),
-    "momentum_pressure": ("F[2 + dir] = F[2 + dir] + K->p;", "F[2 + dir] = F[2 + dir];"),
+    "momentum_pressure": ("F[IU(g) + dir] = F[IU(g) + dir] + K->p;", "F[IU(g) + dir] = F[IU(g) + dir];"),
     "energy_flux": ("F[IE(g)] = (K->E + K->p) * un;", "F[IE(g)] = (K->E) * un;"),
     "sound_speed": ("return ((G + 1.0) * p + Pi) / (G * rho);", "return ((G + 1.0) * p + Pi) / (rho);"),
-    "mixture_Pi": ("*Pi = a1 * g->P1 + a2 * g->P2;", "*Pi = a1 * g->P1 + a1 * g->P2;"),
-    "mixture_Gamma": ("*G = a1 * g->g1 + a2 * g->g2;", "*G = a1 * g->g1 + a2 * g->g1;"),
+    "mixture_Pi": ("*Pi = sp + aN * g->Pk[g->nf - 1];", "*Pi = sp + a[0] * g->Pk[g->nf - 1];"),
+    "mixture_Gamma": ("*G = sg + aN * g->gk[g->nf - 1];", "*G = sg + aN * g->gk[0];"),
     "kinetic_half": ("return 0.5 * rho * s;", "return rho * s;"),
     "rk_stage2": ("0.75 * q[i] + 0.25 * (q1[i] + dt * L[i])", "0.75 * q[i] + 0.25 * (q1[i] + 0.5 * dt * L[i])"),
     "rk_stage3": ("(2.0 / 3.0) * (q2[i] + dt * L[i])", "(2.0 / 3.0) * (q2[i] + dt * L[i] * 0.99)"),
     "periodic_ghosts": ("if (periodic) {", "if (0) {"),
-    "wavespeed_dx": ("(fabs(w[2 + d]) + cs) / cell_width(&g, d, (c / g.stride[d]) % g.n[d]);",
-                     "(fabs(w[2 + d]) + cs);"),
+    "wavespeed_dx": ("(fabs(w[IU(&g) + d]) + cs) / cell_width(&g, d, (c / g.stride[d]) % g.n[d]);",
+                     "(fabs(w[IU(&g) + d]) + cs);"),
     "weno3_linear_weight": ("double a0 = (1.0 / 3.0) / sq(eps + b0);", "double a0 = (2.0 / 3.0) / sq(eps + b0);"),
     "weno3_candidate_index": ("double p1 = (v[2] + v[3]) / 2.0;", "double p1 = (v[2] + v[4]) / 2.0;"),
     "weno3_beta_index": ("double b1 = sq(v[3] - v[2]);", "double b1 = sq(v[3] - v[1]);"),
@@ -55,8 +55,16 @@ MUTATIONS = {
     "nu_face_value": ("cp[3 * k + j] = Mi[j] + 0.5 * Mi[3 + j] + 0.25 * Mi[6 + j];",
                       "cp[3 * k + j] = Mi[j] + 0.5 * Mi[3 + j] + 0.5 * Mi[6 + j];"),
     "nu_global_width": ("double dx = cell_width(g, d, i);", "double dx = g->dx[d];"),
-    "nu_wavespeed_width": ("(fabs(w[2 + d]) + cs) / cell_width(&g, d, (c / g.stride[d]) % g.n[d]);",
-                           "(fabs(w[2 + d]) + cs) / g.dx[d];"),
+    "nf_mixture_middle": ("sg = sg + a[i] * g->gk[i];", "sg = sg + a[i] * g->gk[0];"),
+    "nf_source_loop": ("for (int k = 0; k < g->nf - 1; k++) {\n                    double ak",
+                       "for (int k = 0; k < 1; k++) {\n                    double ak"),
+    "nf_star_density": ("for (int i = 0; i < g->nf; i++) F[i] = F[i] + SK * (chi * w[i] - w[i]);",
+                        "for (int i = 0; i < 2; i++) F[i] = F[i] + SK * (chi * w[i] - w[i]);"),
+    "nf_rho": ("for (int i = 2; i < g->nf; i++) rho = rho + q[i];", "for (int i = 3; i < g->nf; i++) rho = rho + q[i];"),
+    "nf_alpha_flux": ("for (int i = 0; i < g->nf - 1; i++) F[IA(g) + i] = K->a[i] * un;",
+                      "for (int i = 0; i < g->nf - 1; i++) F[IA(g) + i] = K->a[0] * un;"),
+    "nu_wavespeed_width": ("(fabs(w[IU(&g) + d]) + cs) / cell_width(&g, d, (c / g.stride[d]) % g.n[d]);",
+                           "(fabs(w[IU(&g) + d]) + cs) / g.dx[d];"),
 }
 
 
@@ -72,7 +80,8 @@ def test_planted_mistake_is_caught(name, tmp_path):
                     str(so), str(csrc), "-lm"], check=True)
     env = dict(os.environ, MFC5_ORACLE_LIB=str(so))
     suites = [os.path.join(ROOT, "tests", f) for f in
-              ("test_oracle_elements.py", "test_oracle_physics.py", "test_oracle_stretched.py")]
+              ("test_oracle_elements.py", "test_oracle_physics.py", "test_oracle_stretched.py",
+               "test_oracle_nfluids.py")]
     r = subprocess.run([sys.executable, "-m", "pytest", *suites, "-x", "-q", "-p", "no:cacheprovider",
                         "-m", "not gpu"], cwd=ROOT, env=env, capture_output=True, text=True,
                        timeout=600)
