@@ -54,20 +54,28 @@ typedef enum {
 
 typedef enum { MFC_BC_TRANSMISSIVE = 0, MFC_BC_PERIODIC = 1 } mfc_bc;
 
-/* Problem statement (Sec. II-A/B): a uniform grid, two stiffened gases, BCs. */
+#define MFC_MAX_FLUIDS 4
+
+/* Problem statement (Sec. II-A/B): a uniform grid, N stiffened gases, BCs.
+ * State layout with N fluids (N = nfluids): alpha_i rho_i (i = 1..N),
+ * rho u_k (k < ndim), rho E, alpha_1 .. alpha_{N-1} (alpha_N = 1 - sum):
+ * neq = 2 N + ndim fields; two fluids: alpha1 rho1, alpha2 rho2, rho u_k,
+ * rho E, alpha1 (neq = ndim + 4). */
 typedef struct {
     int ndim;          /* 1, 2 or 3 */
     int n[3];          /* cells per dimension; entries beyond ndim are ignored (treated as 1) */
     double lo[3];      /* lower corner; dx_d = (hi[d] - lo[d]) / n[d] */
     double hi[3];      /* upper corner */
     int bc[3][2];      /* mfc_bc per dimension and side; periodic must be set on both sides */
-    double gamma[2];   /* ratio of specific heats of fluid 1 and fluid 2 (> 1) */
-    double pi_inf[2];  /* stiffness pi_inf of fluid 1 and fluid 2 (>= 0), in pressure units */
+    double gamma[MFC_MAX_FLUIDS];   /* ratio of specific heats of fluids 1..N (> 1) */
+    double pi_inf[MFC_MAX_FLUIDS];  /* stiffness pi_inf of fluids 1..N (>= 0), in pressure units */
     double weno_eps;   /* WENO epsilon, absolute (1e-6 is the usual choice) */
     int precision;     /* mfc_precision */
     int weno_order;    /* reconstruction (Sec. II-B): 5 = WENO5-JS, 3 = WENO3-JS (Jiang-Shu, two
                           two-cell stencils, linear weights 1/3, 2/3); 0 means 5.  WENO3 is
                           available in every precision except MFC_GATED (MFC_EINVAL) */
+    int nfluids;       /* N, 2 .. MFC_MAX_FLUIDS; 0 means 2.  N > 2: not with MFC_GATED or
+                          mfc_set_grid (MFC_EINVAL) */
 } mfc_params;
 
 /* Creates a context: validates params (MFC_EINVAL), allocates the state,

@@ -3,6 +3,8 @@
 // wave-speed reduction, and the per-step control kernel.  Built with
 // -fmad=false: the conversion and the wave speed follow the reference
 // operation order bit for bit, so every form starts from the same state.
+#include <type_traits>
+
 #include "sweep.cuh"
 
 namespace mfc5 {
@@ -19,25 +21,25 @@ static unsigned aux_blocks(long long n) {
 // Primitive (alpha1 rho1, alpha2 rho2, u_k, p, alpha1) -> conservative, in
 // place (Sec. II-A: rho E = Gamma p + Pi + rho |u|^2 / 2), in the reference
 // operation order (this file is built with -fmad=false).
-template <int NDIM>
+template <int NDIM, int NF>
 __global__ void prim_to_cons_kernel(double* q, long long nc, Eos e) {
-    using FL = Fields<NDIM>;
+    using FL = Fields<NDIM, NF>;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < nc;
          c += (long long)gridDim.x * blockDim.x) {
         double w[FL::NEQ], v[FL::NEQ];
 #pragma unroll
         for (int f = 0; f < FL::NEQ; ++f) w[f] = q[f * nc + c];
-        exact::prim_to_cons<NDIM>(e, w, v);
+        exact::prim_to_cons<NDIM, NF>(e, w, v);
 #pragma unroll
         for (int f = 0; f < FL::NEQ; ++f) q[f * nc + c] = v[f];
     }
 }
 
 // FP32 working copy (conservatives + pressure) of an FP64 state, mixed form.
-template <int NDIM>
+template <int NDIM, int NF>
 __global__ void make_mixed_state_kernel(const double* __restrict__ qn, float* __restrict__ s0,
                                         long long nc, Eos e) {
-    using FL = Fields<NDIM>;
+    using FL = Fields<NDIM, NF>;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < nc;
          c += (long long)gridDim.x * blockDim.x) {
         double q[FL::NEQ];
@@ -48,17 +50,17 @@ __global__ void make_mixed_state_kernel(const double* __restrict__ qn, float* __
             q32[f] = d2f_bits(q[f]);
             s0[f * nc + c] = q32[f];
         }
-        s0[FL::NEQ * nc + c] = mixed_pressure<NDIM>(e, q, q32);
+        s0[FL::NEQ * nc + c] = mixed_pressure<NDIM, NF>(e, q, q32);
     }
 }
 
 // S = max over cells of sum_d (|u_d| + c)/dx_d of an FP64 state, in the
 // reference operation order.
-template <int NDIM>
+template <int NDIM, int NF>
 __global__ void wavespeed_kernel(const double* __restrict__ q, long long nc, Eos e, double dx0, double dx1,
                                  double dx2, double rdx0, double rdx1, double rdx2, DevCtrl* ctrl, int n0, int n1,
                                  Geom3 g) {
-    using FL = Fields<NDIM>;
+    using FL = Fields<NDIM, NF>;
     double dx[3] = {dx0, dx1, dx2};
     double rdx[3] = {rdx0, rdx1, rdx2};
     double smax = 0.0;
@@ -82,7 +84,7 @@ __global__ void wavespeed_kernel(const double* __restrict__ q, long long nc, Eos
                     dx[d] = __ldg(g.cw[d] + ci[d]);
                     rdx[d] = __ldg(g.crw[d] + ci[d]);
                 }
-            double s = exact::cell_wavespeed<NDIM>(e, v, dx, rdx, bad);
+            double s = exact::cell_wavespeed<NDIM, NF>(e, v, dx, rdx, bad);
             smax = s > smax ? s : smax;
         }
     }
@@ -110,21 +112,41 @@ __global__ void f32_to_f64_kernel(const float* __restrict__ src, double* __restr
         dst[i] = double(src[i]);
 }
 
+// Calls f.template operator()<NDIM, NF>() for the runtime ndim and fluid count.
+template <typename Fn>
+cudaError_t dispatch_nd_nf(int ndim, int nf, Fn&& f) {
+    auto by_nf = [&](auto nd) -> cudaError_t {
+        constexpr int ND = decltype(nd)::value;
+        switch (nf) {
+            case 2: return f.template operator()<ND, 2>();
+            case 3: return f.template operator()<ND, 3>();
+            case 4: return f.template operator()<ND, 4>();
+            default: return cudaErrorInvalidValue;
+        }
+    };
+    switch (ndim) {
+        case 1: return by_nf(std::integral_constant<int, 1>());
+        case 2: return by_nf(std::integral_constant<int, 2>());
+        case 3: return by_nf(std::integral_constant<int, 3>());
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 cudaError_t launch_prim_to_cons(int ndim, double* q, long long nc, const Eos& e, cudaStream_t s) {
     unsigned g = aux_blocks(nc);
-    if (ndim == 1) prim_to_cons_kernel<1><<<g, kAuxThreads, 0, s>>>(q, nc, e);
-    else if (ndim == 2) prim_to_cons_kernel<2><<<g, kAuxThreads, 0, s>>>(q, nc, e);
-    else prim_to_cons_kernel<3><<<g, kAuxThreads, 0, s>>>(q, nc, e);
-    return cudaGetLastError();
+    return dispatch_nd_nf(ndim, e.nf, [&]<int ND, int NF>() {
+        prim_to_cons_kernel<ND, NF><<<g, kAuxThreads, 0, s>>>(q, nc, e);
+        return cudaGetLastError();
+    });
 }
 
 cudaError_t launch_make_mixed_state(int ndim, const double* qn, float* s0, long long nc, const Eos& e,
                                     cudaStream_t s) {
     unsigned g = aux_blocks(nc);
-    if (ndim == 1) make_mixed_state_kernel<1><<<g, kAuxThreads, 0, s>>>(qn, s0, nc, e);
-    else if (ndim == 2) make_mixed_state_kernel<2><<<g, kAuxThreads, 0, s>>>(qn, s0, nc, e);
-    else make_mixed_state_kernel<3><<<g, kAuxThreads, 0, s>>>(qn, s0, nc, e);
-    return cudaGetLastError();
+    return dispatch_nd_nf(ndim, e.nf, [&]<int ND, int NF>() {
+        make_mixed_state_kernel<ND, NF><<<g, kAuxThreads, 0, s>>>(qn, s0, nc, e);
+        return cudaGetLastError();
+    });
 }
 
 cudaError_t launch_wavespeed(int ndim, const double* q, const int* n, const double* const* cw,
@@ -138,16 +160,11 @@ cudaError_t launch_wavespeed(int ndim, const double* q, const int* n, const doub
         g3.crw[d] = crw ? crw[d] : nullptr;
     }
     unsigned g = aux_blocks(nc);
-    if (ndim == 1)
-        wavespeed_kernel<1><<<g, kAuxThreads, 0, s>>>(q, nc, e, dx[0], dx[1], dx[2], rdx[0], rdx[1], rdx[2], ctrl,
-                                                       n[0], n[1], g3);
-    else if (ndim == 2)
-        wavespeed_kernel<2><<<g, kAuxThreads, 0, s>>>(q, nc, e, dx[0], dx[1], dx[2], rdx[0], rdx[1], rdx[2], ctrl,
-                                                       n[0], n[1], g3);
-    else
-        wavespeed_kernel<3><<<g, kAuxThreads, 0, s>>>(q, nc, e, dx[0], dx[1], dx[2], rdx[0], rdx[1], rdx[2], ctrl,
-                                                       n[0], n[1], g3);
-    return cudaGetLastError();
+    return dispatch_nd_nf(ndim, e.nf, [&]<int ND, int NF>() {
+        wavespeed_kernel<ND, NF><<<g, kAuxThreads, 0, s>>>(q, nc, e, dx[0], dx[1], dx[2], rdx[0], rdx[1], rdx[2],
+                                                          ctrl, n[0], n[1], g3);
+        return cudaGetLastError();
+    });
 }
 
 cudaError_t launch_step_begin(DevCtrl* ctrl, cudaStream_t s) {

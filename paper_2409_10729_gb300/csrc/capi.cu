@@ -80,9 +80,12 @@ static int validate(const mfc_params* p) {
         int b0 = p->bc[d][0], b1 = p->bc[d][1];
         if (b0 < 0 || b0 > 1 || b1 < 0 || b1 > 1 || b0 != b1) return MFC_EINVAL;
     }
-    for (int i = 0; i < 2; ++i)
+    if (p->nfluids != 0 && (p->nfluids < 2 || p->nfluids > MFC_MAX_FLUIDS)) return MFC_EINVAL;
+    const int nf = params_nfluids(p->nfluids);
+    for (int i = 0; i < nf; ++i)
         if (!(p->gamma[i] > 1.0) || !isfinite(p->gamma[i]) || !(p->pi_inf[i] >= 0.0) || !isfinite(p->pi_inf[i]))
             return MFC_EINVAL;
+    if (nf > 2 && p->precision == MFC_GATED) return MFC_EINVAL;
     if (!(p->weno_eps > 0.0) || !isfinite(p->weno_eps)) return MFC_EINVAL;
     if (p->precision != MFC_FP64 && p->precision != MFC_MIXED && p->precision != MFC_FP64_FAST &&
         p->precision != MFC_GATED)
@@ -130,7 +133,7 @@ extern "C" int mfc_create(const mfc_params* params, void* cuda_stream, mfc_ctx**
     if (!ctx) return MFC_ENOMEM;
     ctx->p = *params;
     ctx->ndim = params->ndim;
-    ctx->neq = params->ndim + 4;
+    ctx->neq = 2 * params_nfluids(params->nfluids) + params->ndim;
     switch (params->precision) {
         case MFC_FP64: ctx->form = FORM_FP64_EXACT; break;
         case MFC_FP64_FAST: ctx->form = FORM_FP64_FAST; break;
@@ -147,10 +150,7 @@ extern "C" int mfc_create(const mfc_params* params, void* cuda_stream, mfc_ctx**
         ctx->periodic[d] = d < ctx->ndim ? params->bc[d][0] == MFC_BC_PERIODIC : 0;
     }
     for (int d = 0; d < ctx->ndim; ++d) ctx->seg[d] = pick_seg(d, ctx->n);
-    double g1 = 1.0 / (params->gamma[0] - 1.0), g2 = 1.0 / (params->gamma[1] - 1.0);
-    double P1 = params->gamma[0] * params->pi_inf[0] / (params->gamma[0] - 1.0);
-    double P2 = params->gamma[1] * params->pi_inf[1] / (params->gamma[1] - 1.0);
-    ctx->eos = Eos{g1, g2, P1, P2, g1 - g2, P1 - P2};
+    ctx->eos = make_eos(params->gamma, params->pi_inf, params_nfluids(params->nfluids));
     ctx->stream = (cudaStream_t)cuda_stream;
 
     if (cudaGetDevice(&ctx->device) != cudaSuccess ||
@@ -441,7 +441,7 @@ extern "C" int mfc_step_rk3_dt(mfc_ctx* ctx, double dt, int nsteps) {
 
 extern "C" int mfc_set_grid(mfc_ctx* ctx, int dir, const double* edges) {
     if (!ctx || !edges || dir < 0 || dir >= ctx->ndim) return MFC_EINVAL;
-    if (ctx->form == FORM_GATED || ctx->p.weno_order == 3) return MFC_EINVAL;
+    if (ctx->form == FORM_GATED || ctx->p.weno_order == 3 || ctx->eos.nf != 2) return MFC_EINVAL;
     const int n = ctx->n[dir];
     std::vector<double> tab, width;
     if (!build_grid_tables(edges, n, ctx->periodic[dir], tab, width)) return MFC_EINVAL;
@@ -511,7 +511,7 @@ extern "C" int mfc_gate_flat(mfc_ctx* ctx, long long* flat) {
 }
 
 extern "C" int mfc_gate_samples(mfc_ctx* ctx, float* X, float* Y, long long capacity, float tau, long long* count) {
-    if (!ctx || !X || !Y || !(tau > 0.f)) return MFC_EINVAL;
+    if (!ctx || !X || !Y || !(tau > 0.f) || ctx->eos.nf != 2) return MFC_EINVAL;
     if (!ctx->have_state) return MFC_ESTATE;
     long long need = 2LL * ctx->ndim * ctx->ncell;
     if (capacity < need) return MFC_EINVAL;

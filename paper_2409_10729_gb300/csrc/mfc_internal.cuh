@@ -15,6 +15,24 @@ namespace mfc5 {
 // linear weights at i+1/2 and i-1/2.
 constexpr int kTabDoubles = 42;
 
+// Number of fluids of a params struct (0 means 2).
+inline int params_nfluids(int nfluids) { return nfluids == 0 ? 2 : nfluids; }
+
+// Mixture constants of nf fluids from their gamma and pi_inf.
+inline Eos make_eos(const double* gamma, const double* pi_inf, int nf) {
+    Eos e{};
+    e.nf = nf;
+    for (int i = 0; i < nf; ++i) {
+        e.g[i] = 1.0 / (gamma[i] - 1.0);
+        e.P[i] = gamma[i] * pi_inf[i] / (gamma[i] - 1.0);
+    }
+    for (int i = 0; i < nf - 1; ++i) {
+        e.dg[i] = e.g[i] - e.g[nf - 1];
+        e.dP[i] = e.P[i] - e.P[nf - 1];
+    }
+    return e;
+}
+
 // Per-direction cell widths and RN(1/width) of a non-uniform grid (null where
 // the direction is uniform), by value for kernels.
 struct Geom3 {

@@ -68,7 +68,8 @@ int check_params(const mfc_params* p) {
         int b0 = p->bc[d][0], b1 = p->bc[d][1];
         if (b0 < 0 || b0 > 1 || b1 < 0 || b1 > 1 || b0 != b1) return MFC_EINVAL;
     }
-    for (int i = 0; i < 2; ++i)
+    if (p->nfluids != 0 && (p->nfluids < 2 || p->nfluids > MFC_MAX_FLUIDS)) return MFC_EINVAL;
+    for (int i = 0; i < params_nfluids(p->nfluids); ++i)
         if (!(p->gamma[i] > 1.0) || !isfinite(p->gamma[i]) || !(p->pi_inf[i] >= 0.0) || !isfinite(p->pi_inf[i]))
             return MFC_EINVAL;
     if (!(p->weno_eps > 0.0) || !isfinite(p->weno_eps)) return MFC_EINVAL;
@@ -89,7 +90,7 @@ extern "C" int mfc_rhs_noalloc(const mfc_params* params, const double* q, double
         n[d] = d < params->ndim ? params->n[d] : 1;
         ncell *= n[d];
     }
-    const int ndim = params->ndim, neq = ndim + 4;
+    const int ndim = params->ndim, neq = 2 * params_nfluids(params->nfluids) + ndim;
     if ((long long)neq * ncell > (long long)MFC_NOALLOC_MAX_DOUBLES - kCtrlDoubles) return MFC_ETOOBIG;
 
     double* scratch = nullptr;
@@ -99,9 +100,7 @@ extern "C" int mfc_rhs_noalloc(const mfc_params* params, const double* q, double
     DevCtrl* ctrl = reinterpret_cast<DevCtrl*>(scratch);
     if (cudaMemsetAsync(ctrl, 0, sizeof(DevCtrl), s) != cudaSuccess) return MFC_ECUDA;
 
-    double g1 = 1.0 / (params->gamma[0] - 1.0), g2 = 1.0 / (params->gamma[1] - 1.0);
-    double P1 = params->gamma[0] * params->pi_inf[0] / (params->gamma[0] - 1.0);
-    double P2 = params->gamma[1] * params->pi_inf[1] / (params->gamma[1] - 1.0);
+
     SweepArgs a;
     memset(&a, 0, sizeof(a));
     for (int d = 0; d < 3; ++d) {
@@ -111,7 +110,7 @@ extern "C" int mfc_rhs_noalloc(const mfc_params* params, const double* q, double
         a.rdx[d] = 1.0 / a.dx[d];
     }
     a.ncell = ncell;
-    a.eos = Eos{g1, g2, P1, P2, g1 - g2, P1 - P2};
+    a.eos = make_eos(params->gamma, params->pi_inf, params_nfluids(params->nfluids));
     a.eps = params->weno_eps;
     a.order = params->weno_order == 3 ? 3 : 5;
     a.ctrl = ctrl;

@@ -18,20 +18,38 @@
 
 namespace mfc5 {
 
-// Stiffened-gas mixture constants: Gamma = g2 + alpha1 (g1 - g2),
-// Pi = P2 + alpha1 (P1 - P2), with g_i = 1/(gamma_i - 1) and
-// P_i = gamma_i pi_i / (gamma_i - 1).
+// Stiffened-gas mixture constants of N fluids (N <= kMaxFluids), with
+// g_i = 1/(gamma_i - 1) and P_i = gamma_i pi_i / (gamma_i - 1):
+//   Gamma = sum_i alpha_i g_i = g_N + sum_{i<N} alpha_i (g_i - g_N),
+//   Pi    = sum_i alpha_i P_i = P_N + sum_{i<N} alpha_i (P_i - P_N),
+// alpha_N = 1 - sum_{i<N} alpha_i.  dg/dP hold g_i - g_N, P_i - P_N (i < N).
+constexpr int kMaxFluids = 4;
 struct Eos {
-    double g1, g2, P1, P2;
-    double dg, dP;
+    double g[kMaxFluids], P[kMaxFluids];
+    double dg[kMaxFluids - 1], dP[kMaxFluids - 1];
+    int nf;
 };
 
-template <int NDIM>
+// Field layout of an N-fluid state: alpha_i rho_i (i < N), rho u_k, rho E,
+// alpha_1 .. alpha_{N-1}.  For two fluids: alpha1 rho1, alpha2 rho2, rho u_k,
+// rho E, alpha1 (NEQ = NDIM + 4).
+template <int NDIM, int NF = 2>
 struct Fields {
-    static constexpr int NEQ = NDIM + 4;  // alpha1 rho1, alpha2 rho2, rho u_k, rho E, alpha1
-    static constexpr int IE = 2 + NDIM;
-    static constexpr int IA = 3 + NDIM;
+    static constexpr int NEQ = 2 * NF + NDIM;
+    static constexpr int IU = NF;             // first momentum / velocity
+    static constexpr int IE = NF + NDIM;      // energy / pressure
+    static constexpr int IA = NF + NDIM + 1;  // alpha_1 (alpha_2 .. alpha_{N-1} follow)
+    static constexpr int NA = NF - 1;         // carried volume fractions
 };
+
+// Mixture density of the partial densities w[0..NF-1].
+template <int NF, typename R>
+__device__ __forceinline__ R mix_rho(const R* w) {
+    R rho = w[0] + w[1];
+#pragma unroll
+    for (int i = 2; i < NF; ++i) rho = rho + w[i];
+    return rho;
+}
 
 template <typename R>
 __device__ __forceinline__ R rdiv(R a, R b) { return a / b; }
@@ -41,17 +59,28 @@ __device__ __forceinline__ R sqrt_pos(R x) { return sqrt(x); }
 
 // EOS constants in the working precision R (converted once per thread, so the
 // FP32 path issues no FP64 conversions per face).
-template <typename R>
+template <typename R, int NF = 2>
 struct EosR {
-    R dg, g2, dP, P2;
-    __device__ __forceinline__ explicit EosR(const Eos& e) : dg(R(e.dg)), g2(R(e.g2)), dP(R(e.dP)), P2(R(e.P2)) {}
+    R dg[NF - 1], gN, dP[NF - 1], PN;
+    __device__ __forceinline__ explicit EosR(const Eos& e) : gN(R(e.g[NF - 1])), PN(R(e.P[NF - 1])) {
+#pragma unroll
+        for (int i = 0; i < NF - 1; ++i) {
+            dg[i] = R(e.dg[i]);
+            dP[i] = R(e.dP[i]);
+        }
+    }
 };
 
-// Mixture Gamma and Pi at volume fraction a1.
-template <typename R>
-__device__ __forceinline__ void mixture(const EosR<R>& e, R a1, R& G, R& Pi) {
-    G = a1 * e.dg + e.g2;
-    Pi = a1 * e.dP + e.P2;
+// Mixture Gamma and Pi at the carried volume fractions a[0..NF-2].
+template <typename R, int NF>
+__device__ __forceinline__ void mixture(const EosR<R, NF>& e, const R* a, R& G, R& Pi) {
+    G = a[0] * e.dg[0] + e.gN;
+    Pi = a[0] * e.dP[0] + e.PN;
+#pragma unroll
+    for (int i = 1; i < NF - 1; ++i) {
+        G = G + a[i] * e.dg[i];
+        Pi = Pi + a[i] * e.dP[i];
+    }
 }
 
 // ---------------------------------------------------------------- WENO5-JS
@@ -185,21 +214,21 @@ __device__ __forceinline__ void weno5_tab(const R* __restrict__ T, R v0, R v1, R
 // alpha1 slot: F_alpha = alpha1_K * uf.  Region choice follows
 // 0<=S_L: F_L; S_L<0<=S*: F*_L; S*<0<=S_R: F*_R; else F_R.
 // Returns true when a face state is non-physical (rho<=0, c^2<=0, NaN).
-template <int NDIM, int DIR, typename R>
-__device__ __forceinline__ bool hllc(const EosR<R>& e, const R* wL, const R* wR, R* F, R& uf) {
-    using FL = Fields<NDIM>;
-    const int IE = FL::IE, IA = FL::IA;
-    R rhoL = wL[0] + wL[1];
-    R rhoR = wR[0] + wR[1];
+template <int NDIM, int DIR, typename R, int NF = 2>
+__device__ __forceinline__ bool hllc(const EosR<R, NF>& e, const R* wL, const R* wR, R* F, R& uf) {
+    using FL = Fields<NDIM, NF>;
+    const int IE = FL::IE, IA = FL::IA, IU = FL::IU;
+    R rhoL = mix_rho<NF>(wL);
+    R rhoR = mix_rho<NF>(wR);
     R GL, PiL, GR, PiR;
-    mixture(e, wL[IA], GL, PiL);
-    mixture(e, wR[IA], GR, PiR);
+    mixture(e, wL + IA, GL, PiL);
+    mixture(e, wR + IA, GR, PiR);
     R pL = wL[IE], pR = wR[IE];
     R c2L = rdiv((GL + R(1)) * pL + PiL, GL * rhoL);
     R c2R = rdiv((GR + R(1)) * pR + PiR, GR * rhoR);
     bool bad = !(rhoL > R(0)) || !(rhoR > R(0)) || !(c2L > R(0)) || !(c2R > R(0));
     R cL = sqrt_pos(c2L), cR = sqrt_pos(c2R);
-    R uL = wL[2 + DIR], uR = wR[2 + DIR];
+    R uL = wL[IU + DIR], uR = wR[IU + DIR];
     R SL = (uL - cL < uR - cR) ? uL - cL : uR - cR;
     R SR = (uL + cL > uR + cR) ? uL + cL : uR + cR;
     R mL = rhoL * (SL - uL), mR = rhoR * (SR - uR);
@@ -215,36 +244,37 @@ __device__ __forceinline__ bool hllc(const EosR<R>& e, const R* wL, const R* wR,
     R Pi = left ? PiL : PiR;
     R SK = left ? SL : SR;
     R p = w[IE];
-    R un = w[2 + DIR];
+    R un = w[IU + DIR];
     R ke = R(0);
 #pragma unroll
-    for (int k = 0; k < NDIM; ++k) ke += w[2 + k] * w[2 + k];
+    for (int k = 0; k < NDIM; ++k) ke += w[IU + k] * w[IU + k];
     ke = R(0.5) * rho * ke;
     R E = G * p + Pi + ke;
-    F[0] = w[0] * un;
-    F[1] = w[1] * un;
 #pragma unroll
-    for (int k = 0; k < NDIM; ++k) F[2 + k] = rho * w[2 + k] * un;
-    F[2 + DIR] += p;
+    for (int i = 0; i < NF; ++i) F[i] = w[i] * un;
+#pragma unroll
+    for (int k = 0; k < NDIM; ++k) F[IU + k] = rho * w[IU + k] * un;
+    F[IU + DIR] += p;
     F[IE] = (E + p) * un;
     uf = un;
     if (star) {
         R inv = rdiv(R(1), SK - Ss);
         R chi = (SK - un) * inv;
         R dchi = chi - R(1);
-        F[0] += SK * (dchi * w[0]);
-        F[1] += SK * (dchi * w[1]);
+#pragma unroll
+        for (int i = 0; i < NF; ++i) F[i] += SK * (dchi * w[i]);
 #pragma unroll
         for (int k = 0; k < NDIM; ++k) {
-            R ms = (k == DIR) ? chi * rho * Ss : chi * rho * w[2 + k];
-            F[2 + k] += SK * (ms - rho * w[2 + k]);
+            R ms = (k == DIR) ? chi * rho * Ss : chi * rho * w[IU + k];
+            F[IU + k] += SK * (ms - rho * w[IU + k]);
         }
         R dS = Ss - un;
         R Es = chi * (E + dS * rho * Ss) + dS * p * inv;
         F[IE] += SK * (Es - E);
         uf = Ss;
     }
-    F[IA] = w[IA] * uf;
+#pragma unroll
+    for (int i = 0; i < FL::NA; ++i) F[IA + i] = w[IA + i] * uf;
     return bad;
 }
 

@@ -28,11 +28,30 @@ __device__ __forceinline__ double rcp(double b) { return __drcp_rn(b); }
 
 __device__ __forceinline__ double sq(double x) { return x * x; }
 
-// Gamma = a1 g1 + (1 - a1) g2, Pi = a1 P1 + (1 - a1) P2.
-__device__ __forceinline__ void mixture(const Eos& e, double a1, double& G, double& Pi) {
-    double a2 = 1.0 - a1;
-    G = a1 * e.g1 + a2 * e.g2;
-    Pi = a1 * e.P1 + a2 * e.P2;
+// Gamma = sum_i alpha_i g_i, Pi = sum_i alpha_i P_i over the NF fluids, the
+// carried fractions a[0..NF-2] first and alpha_N = 1 - a[0] - ... - a[NF-2]
+// last (two fluids: a1 g1 + (1 - a1) g2).
+template <int NF>
+__device__ __forceinline__ void mixture(const Eos& e, const double* a, double& G, double& Pi) {
+    double aN = 1.0 - a[0];
+#pragma unroll
+    for (int i = 1; i < NF - 1; ++i) aN = aN - a[i];
+    double sg = a[0] * e.g[0], sp = a[0] * e.P[0];
+#pragma unroll
+    for (int i = 1; i < NF - 1; ++i) {
+        sg = sg + a[i] * e.g[i];
+        sp = sp + a[i] * e.P[i];
+    }
+    G = sg + aN * e.g[NF - 1];
+    Pi = sp + aN * e.P[NF - 1];
+}
+
+template <int NF>
+__device__ __forceinline__ double mix_rho(const double* q) {
+    double rho = q[0] + q[1];
+#pragma unroll
+    for (int i = 2; i < NF; ++i) rho = rho + q[i];
+    return rho;
 }
 
 template <int NDIM>
@@ -44,43 +63,45 @@ __device__ __forceinline__ double kinetic(double rho, const double* u) {
 }
 
 // Conservative -> primitive (u_k = rho u_k / rho, p = (rho E - ke - Pi)/Gamma).
-template <int NDIM>
+template <int NDIM, int NF = 2>
 __device__ __forceinline__ void cons_to_prim(const Eos& e, const double* q, double* w) {
-    using FL = Fields<NDIM>;
-    double rho = q[0] + q[1];
+    using FL = Fields<NDIM, NF>;
+    double rho = mix_rho<NF>(q);
     double y = rcp(rho);
     double u[NDIM];
 #pragma unroll
-    for (int k = 0; k < NDIM; ++k) u[k] = div_rcp(q[2 + k], rho, y);
+    for (int k = 0; k < NDIM; ++k) u[k] = div_rcp(q[FL::IU + k], rho, y);
     double ke = kinetic<NDIM>(rho, u);
     double G, Pi;
-    mixture(e, q[FL::IA], G, Pi);
+    mixture<NF>(e, q + FL::IA, G, Pi);
     double p = (q[FL::IE] - ke - Pi) / G;
-    w[0] = q[0];
-    w[1] = q[1];
 #pragma unroll
-    for (int k = 0; k < NDIM; ++k) w[2 + k] = u[k];
+    for (int i = 0; i < NF; ++i) w[i] = q[i];
+#pragma unroll
+    for (int k = 0; k < NDIM; ++k) w[FL::IU + k] = u[k];
     w[FL::IE] = p;
-    w[FL::IA] = q[FL::IA];
+#pragma unroll
+    for (int i = 0; i < FL::NA; ++i) w[FL::IA + i] = q[FL::IA + i];
 }
 
 // Primitive -> conservative (rho E = Gamma p + Pi + ke).
-template <int NDIM>
+template <int NDIM, int NF = 2>
 __device__ __forceinline__ void prim_to_cons(const Eos& e, const double* w, double* q) {
-    using FL = Fields<NDIM>;
-    double rho = w[0] + w[1];
+    using FL = Fields<NDIM, NF>;
+    double rho = mix_rho<NF>(w);
     double u[NDIM];
 #pragma unroll
-    for (int k = 0; k < NDIM; ++k) u[k] = w[2 + k];
+    for (int k = 0; k < NDIM; ++k) u[k] = w[FL::IU + k];
     double ke = kinetic<NDIM>(rho, u);
     double G, Pi;
-    mixture(e, w[FL::IA], G, Pi);
-    q[0] = w[0];
-    q[1] = w[1];
+    mixture<NF>(e, w + FL::IA, G, Pi);
 #pragma unroll
-    for (int k = 0; k < NDIM; ++k) q[2 + k] = rho * u[k];
+    for (int i = 0; i < NF; ++i) q[i] = w[i];
+#pragma unroll
+    for (int k = 0; k < NDIM; ++k) q[FL::IU + k] = rho * u[k];
     q[FL::IE] = G * w[FL::IE] + Pi + ke;
-    q[FL::IA] = w[FL::IA];
+#pragma unroll
+    for (int i = 0; i < FL::NA; ++i) q[FL::IA + i] = w[FL::IA + i];
 }
 
 __device__ __forceinline__ double sound2(double G, double Pi, double rho, double p) {
@@ -156,46 +177,47 @@ __device__ __forceinline__ void weno3(double eps, double v1, double v2, double v
 }
 
 struct Face {
-    double rho, p, a1, G, Pi, E, c2;
+    double rho, p, G, Pi, E, c2;
 };
 
-template <int NDIM>
+template <int NDIM, int NF = 2>
 __device__ __forceinline__ void face_from_prim(const Eos& e, const double* w, Face& s) {
-    using FL = Fields<NDIM>;
-    s.rho = w[0] + w[1];
+    using FL = Fields<NDIM, NF>;
+    s.rho = mix_rho<NF>(w);
     s.p = w[FL::IE];
-    s.a1 = w[FL::IA];
-    mixture(e, s.a1, s.G, s.Pi);
-    s.E = s.G * s.p + s.Pi + kinetic<NDIM>(s.rho, w + 2);
+    mixture<NF>(e, w + FL::IA, s.G, s.Pi);
+    s.E = s.G * s.p + s.Pi + kinetic<NDIM>(s.rho, w + FL::IU);
     s.c2 = sound2(s.G, s.Pi, s.rho, s.p);
 }
 
-// Physical flux of side K (primitives w, face state K) normal to DIR.
-template <int NDIM, int DIR>
+// Physical flux of side K (primitives w, face state K) normal to DIR; the
+// volume-fraction slots carry alpha_i,K u_n.
+template <int NDIM, int DIR, int NF = 2>
 __device__ __forceinline__ void phys_flux(const double* w, const Face& K, double* F) {
-    using FL = Fields<NDIM>;
-    double un = w[2 + DIR];
-    F[0] = w[0] * un;
-    F[1] = w[1] * un;
+    using FL = Fields<NDIM, NF>;
+    double un = w[FL::IU + DIR];
 #pragma unroll
-    for (int k = 0; k < NDIM; ++k) F[2 + k] = K.rho * w[2 + k] * un;
-    F[2 + DIR] = F[2 + DIR] + K.p;
+    for (int i = 0; i < NF; ++i) F[i] = w[i] * un;
+#pragma unroll
+    for (int k = 0; k < NDIM; ++k) F[FL::IU + k] = K.rho * w[FL::IU + k] * un;
+    F[FL::IU + DIR] = F[FL::IU + DIR] + K.p;
     F[FL::IE] = (K.E + K.p) * un;
-    F[FL::IA] = K.a1 * un;
+#pragma unroll
+    for (int i = 0; i < FL::NA; ++i) F[FL::IA + i] = w[FL::IA + i] * un;
 }
 
 // HLLC flux through a face normal to DIR; regions 0<=S_L: F_L, S_L<0<=S*: F*_L,
 // S*<0<=S_R: F*_R, else F_R; the alpha1 slot carries alpha1_K times the
 // region velocity, returned in uf.  Returns true for a non-physical face state.
-template <int NDIM, int DIR>
+template <int NDIM, int DIR, int NF = 2>
 __device__ __forceinline__ bool hllc(const Eos& e, const double* wL, const double* wR, double* F, double& uf) {
-    using FL = Fields<NDIM>;
+    using FL = Fields<NDIM, NF>;
     Face L, R;
-    face_from_prim<NDIM>(e, wL, L);
-    face_from_prim<NDIM>(e, wR, R);
+    face_from_prim<NDIM, NF>(e, wL, L);
+    face_from_prim<NDIM, NF>(e, wR, R);
     bool bad = !(L.rho > 0.0) || !(R.rho > 0.0) || !(L.c2 > 0.0) || !(R.c2 > 0.0);
     double cL = sqrt(L.c2), cR = sqrt(R.c2);
-    double uL = wL[2 + DIR], uR = wR[2 + DIR];
+    double uL = wL[FL::IU + DIR], uR = wR[FL::IU + DIR];
     double SL = (uL - cL < uR - cR) ? uL - cL : uR - cR;
     double SR = (uL + cL > uR + cR) ? uL + cL : uR + cR;
     double num = R.p - L.p + L.rho * uL * (SL - uL) - R.rho * uR * (SR - uR);
@@ -209,47 +231,47 @@ __device__ __forceinline__ bool hllc(const Eos& e, const double* wL, const doubl
     Face K;
     K.rho = left ? L.rho : R.rho;
     K.p = left ? L.p : R.p;
-    K.a1 = left ? L.a1 : R.a1;
     K.G = left ? L.G : R.G;
     K.Pi = left ? L.Pi : R.Pi;
     K.E = left ? L.E : R.E;
     double SK = left ? SL : SR;
-    double un = w[2 + DIR];
-    phys_flux<NDIM, DIR>(w, K, F);
+    double un = w[FL::IU + DIR];
+    phys_flux<NDIM, DIR, NF>(w, K, F);
     uf = un;
     if (star) {
         double chi = (SK - un) / (SK - Ss);
-        F[0] = F[0] + SK * (chi * w[0] - w[0]);
-        F[1] = F[1] + SK * (chi * w[1] - w[1]);
+#pragma unroll
+        for (int i = 0; i < NF; ++i) F[i] = F[i] + SK * (chi * w[i] - w[i]);
 #pragma unroll
         for (int k = 0; k < NDIM; ++k) {
-            double mstar = (k == DIR) ? chi * K.rho * Ss : chi * K.rho * w[2 + k];
-            F[2 + k] = F[2 + k] + SK * (mstar - K.rho * w[2 + k]);
+            double mstar = (k == DIR) ? chi * K.rho * Ss : chi * K.rho * w[FL::IU + k];
+            F[FL::IU + k] = F[FL::IU + k] + SK * (mstar - K.rho * w[FL::IU + k]);
         }
         double Estar = chi * (K.E + (Ss - un) * (K.rho * Ss + K.p / (SK - un)));
         F[FL::IE] = F[FL::IE] + SK * (Estar - K.E);
-        F[FL::IA] = K.a1 * Ss;
+#pragma unroll
+        for (int i = 0; i < FL::NA; ++i) F[FL::IA + i] = w[FL::IA + i] * Ss;
         uf = Ss;
     }
     return bad;
 }
 
 // S contribution of one cell: sum_d (|u_d| + c)/dx_d, from the conservative state.
-template <int NDIM>
+template <int NDIM, int NF = 2>
 __device__ __forceinline__ double cell_wavespeed(const Eos& e, const double* q, const double* dx,
                                                  const double* rdx, bool& bad) {
-    using FL = Fields<NDIM>;
+    using FL = Fields<NDIM, NF>;
     double w[FL::NEQ];
-    cons_to_prim<NDIM>(e, q, w);
-    double rho = w[0] + w[1];
+    cons_to_prim<NDIM, NF>(e, q, w);
+    double rho = mix_rho<NF>(w);
     double G, Pi;
-    mixture(e, w[FL::IA], G, Pi);
+    mixture<NF>(e, w + FL::IA, G, Pi);
     double c2 = sound2(G, Pi, rho, w[FL::IE]);
-    bad |= !(q[0] + q[1] > 0.0) || !(rho > 0.0) || !(c2 > 0.0);
+    bad |= !(mix_rho<NF>(q) > 0.0) || !(rho > 0.0) || !(c2 > 0.0);
     double cs = sqrt(c2);
     double s = 0.0;
 #pragma unroll
-    for (int d = 0; d < NDIM; ++d) s = s + div_rcp(fabs(w[2 + d]) + cs, dx[d], rdx[d]);
+    for (int d = 0; d < NDIM; ++d) s = s + div_rcp(fabs(w[FL::IU + d]) + cs, dx[d], rdx[d]);
     bad |= !(s < INFINITY);
     return s;
 }

@@ -42,44 +42,46 @@ __device__ __forceinline__ int bc_index(int j, int n, int periodic) {
 // Fields a sweep reads per cell, in load order.  FP64: the conservative
 // state.  Mixed: the FP32 state with the pressure stored as field NEQ (formed
 // in FP64 when the state was written) read in place of rho E.
-template <int NDIM, typename R>
+template <int NDIM, typename R, int NF = 2>
 struct LoadSet {
-    static constexpr int N = NDIM + 4;
+    static constexpr int N = Fields<NDIM, NF>::NEQ;
     __device__ static constexpr int field(int k) {
-        return (sizeof(R) == 8 || k != 2 + NDIM) ? k : NDIM + 4;
+        return (sizeof(R) == 8 || k != Fields<NDIM, NF>::IE) ? k : N;
     }
 };
 
 // Primitives from the loaded values v[] (see LoadSet).
-template <int NDIM>
-__device__ __forceinline__ void to_prim(const EosR<double>& e, const double* v, double* w) {
-    using FL = Fields<NDIM>;
-    double r = 1.0 / (v[0] + v[1]);
+template <int NDIM, int NF = 2>
+__device__ __forceinline__ void to_prim(const EosR<double, NF>& e, const double* v, double* w) {
+    using FL = Fields<NDIM, NF>;
+    double r = 1.0 / mix_rho<NF>(v);
     double ke2 = 0.0;
-    w[0] = v[0];
-    w[1] = v[1];
+#pragma unroll
+    for (int i = 0; i < NF; ++i) w[i] = v[i];
 #pragma unroll
     for (int k = 0; k < NDIM; ++k) {
-        double u = v[2 + k] * r;
-        w[2 + k] = u;
-        ke2 += v[2 + k] * u;
+        double u = v[FL::IU + k] * r;
+        w[FL::IU + k] = u;
+        ke2 += v[FL::IU + k] * u;
     }
     double G, Pi;
-    mixture(e, v[FL::IA], G, Pi);
+    mixture(e, v + FL::IA, G, Pi);
     w[FL::IE] = (v[FL::IE] - 0.5 * ke2 - Pi) / G;
-    w[FL::IA] = v[FL::IA];
+#pragma unroll
+    for (int i = 0; i < FL::NA; ++i) w[FL::IA + i] = v[FL::IA + i];
 }
 
-template <int NDIM>
-__device__ __forceinline__ void to_prim(const EosR<float>& e, const float* v, float* w) {
-    using FL = Fields<NDIM>;
-    float r = __fdividef(1.0f, v[0] + v[1]);
-    w[0] = v[0];
-    w[1] = v[1];
+template <int NDIM, int NF = 2>
+__device__ __forceinline__ void to_prim(const EosR<float, NF>& e, const float* v, float* w) {
+    using FL = Fields<NDIM, NF>;
+    float r = __fdividef(1.0f, mix_rho<NF>(v));
 #pragma unroll
-    for (int k = 0; k < NDIM; ++k) w[2 + k] = v[2 + k] * r;
+    for (int i = 0; i < NF; ++i) w[i] = v[i];
+#pragma unroll
+    for (int k = 0; k < NDIM; ++k) w[FL::IU + k] = v[FL::IU + k] * r;
     w[FL::IE] = v[FL::IE];  // stored pressure
-    w[FL::IA] = v[FL::IA];
+#pragma unroll
+    for (int i = 0; i < FL::NA; ++i) w[FL::IA + i] = v[FL::IA + i];
 }
 
 // Exact float -> double and round-to-nearest-even double -> float conversions
@@ -112,28 +114,22 @@ __device__ __forceinline__ float d2f_bits(double x) {
 
 // Pressure from an FP64 conservative state, mixed form: the cancelling part
 // rho E - Pi is formed in FP64, the rest in FP32.
-template <int NDIM>
+template <int NDIM, int NF = 2>
 __device__ __forceinline__ float mixed_pressure(const Eos& e, const double* q, const float* q32) {
-    using FL = Fields<NDIM>;
-    float rho = q32[0] + q32[1];
+    using FL = Fields<NDIM, NF>;
+    float rho = mix_rho<NF>(q32);
     float r = __fdividef(1.0f, rho);
     float ke2 = 0.0f;
 #pragma unroll
-    for (int k = 0; k < NDIM; ++k) ke2 += q32[2 + k] * (q32[2 + k] * r);
-    double a1 = q[FL::IA];
-    double num = (q[FL::IE] - (a1 * e.dP + e.P2)) - f2d_bits(0.5f * ke2);
-    float G = q32[FL::IA] * float(e.dg) + float(e.g2);
-    return __fdividef(d2f_bits(num), G);
-}
-
-// FP64 primitives of one cell of an FP64 conservative state (standalone use).
-template <int NDIM>
-__device__ __forceinline__ void load_prim(const double* __restrict__ q, long long c, long long nc,
-                                          const EosR<double>& e, double* w) {
-    double v[NDIM + 4];
+    for (int k = 0; k < NDIM; ++k) ke2 += q32[FL::IU + k] * (q32[FL::IU + k] * r);
+    double Pi = q[FL::IA] * e.dP[0] + e.P[NF - 1];
 #pragma unroll
-    for (int f = 0; f < NDIM + 4; ++f) v[f] = __ldg(q + f * nc + c);
-    to_prim<NDIM>(e, v, w);
+    for (int i = 1; i < FL::NA; ++i) Pi = Pi + q[FL::IA + i] * e.dP[i];
+    double num = (q[FL::IE] - Pi) - f2d_bits(0.5f * ke2);
+    float G = q32[FL::IA] * float(e.dg[0]) + float(e.g[NF - 1]);
+#pragma unroll
+    for (int i = 1; i < FL::NA; ++i) G = G + q32[FL::IA + i] * float(e.dg[i]);
+    return __fdividef(d2f_bits(num), G);
 }
 
 template <typename R>
@@ -147,18 +143,18 @@ __device__ __forceinline__ R warp_max(R v) {
 }
 
 // Per-cell wave speed sum_d (|u_d| + c) / dx_d from primitives.
-template <int NDIM, typename R>
-__device__ __forceinline__ R cell_wavespeed(const EosR<R>& e, const R* w, const double* inv_dx, bool& bad) {
-    using FL = Fields<NDIM>;
-    R rho = w[0] + w[1];
+template <int NDIM, typename R, int NF = 2>
+__device__ __forceinline__ R cell_wavespeed(const EosR<R, NF>& e, const R* w, const double* inv_dx, bool& bad) {
+    using FL = Fields<NDIM, NF>;
+    R rho = mix_rho<NF>(w);
     R G, Pi;
-    mixture(e, w[FL::IA], G, Pi);
+    mixture(e, w + FL::IA, G, Pi);
     R c2 = rdiv((G + R(1)) * w[FL::IE] + Pi, G * rho);
     bad |= !(rho > R(0)) || !(c2 > R(0));
     R c = sqrt_pos(c2);
     R s = R(0);
 #pragma unroll
-    for (int d = 0; d < NDIM; ++d) s += (fabs(w[2 + d]) + c) * R(inv_dx[d]);
+    for (int d = 0; d < NDIM; ++d) s += (fabs(w[FL::IU + d]) + c) * R(inv_dx[d]);
     bad |= !(s < R(INFINITY));
     return s;
 }
@@ -398,19 +394,20 @@ __device__ __forceinline__ void linear5(float v0, float v1, float v2, float v3, 
 // A reconstructed face state is usable when rho > 0, 0 <= alpha1 <= 1 and
 // p + pi_inf of the mixture is positive ((Gamma + 1) p + Pi > 0).
 template <int NDIM>
-__device__ __forceinline__ bool face_ok(const EosR<float>& e, const float* w) {
+__device__ __forceinline__ bool face_ok(const EosR<float, 2>& e, const float* w) {
     using FL = Fields<NDIM>;
     float a1 = w[FL::IA];
     float G, Pi;
-    mixture(e, a1, G, Pi);
+    mixture(e, w + FL::IA, G, Pi);
     return (w[0] + w[1] > 0.f) && (a1 >= 0.f) && (a1 <= 1.f) && ((G + 1.f) * w[FL::IE] + Pi > 0.f);
 }
 
 // Minimum resident blocks for the register allocator, in blocks of the
 // sweep's own size (x sweeps run one-warp blocks so that the warp's two input
 // chunk buffers and its output tile fit the 48 KB of static shared memory).
-template <int FORM, int MODE, int DIR>
+template <int FORM, int MODE, int DIR, int NF = 2>
 constexpr int sweep_min_blocks() {
+    if (NF > 2) return 1;   // more fields per cell: no register cap (the two-fluid caps spill)
     constexpr int per128 = FORM == FORM_MIXED   ? (MODE == SW_LAST_RK ? MFC_MIN_BLOCKS_MIXED_RK
                                                    : DIR == 0         ? MFC_MIN_BLOCKS_MIXED_X
                                                                       : MFC_MIN_BLOCKS_MIXED)
@@ -421,15 +418,15 @@ constexpr int sweep_min_blocks() {
 
 // NU: some direction of the grid is non-uniform (tables, per-cell widths);
 // the uniform-grid kernels carry none of that code.
-template <int NDIM, int DIR, int MODE, int FORM, bool NU>
-__global__ void __launch_bounds__(sweep_threads(DIR), sweep_min_blocks<FORM, MODE, DIR>())
+template <int NDIM, int DIR, int MODE, int FORM, bool NU, int NF>
+__global__ void __launch_bounds__(sweep_threads(DIR), sweep_min_blocks<FORM, MODE, DIR, NF>())
 sweep_kernel(const SweepArgs a) {
     using R = FormReal<FORM>;
     constexpr bool EXACT = FORM == FORM_FP64_EXACT;
     constexpr bool GATED = FORM == FORM_GATED;
-    using FL = Fields<NDIM>;
-    using LS = LoadSet<NDIM, R>;
-    constexpr int NEQ = FL::NEQ, IE = FL::IE, IA = FL::IA;
+    using FL = Fields<NDIM, NF>;
+    using LS = LoadSet<NDIM, R, NF>;
+    constexpr int NEQ = FL::NEQ, IE = FL::IE, IA = FL::IA, NA = FL::NA;
     constexpr int NL = LS::N;
     constexpr bool MIXED = FORM == FORM_MIXED || FORM == FORM_GATED;
     constexpr int CH = XStage<R>::CH, PITCH = XStage<R>::PITCH;
@@ -475,7 +472,7 @@ sweep_kernel(const SweepArgs a) {
     const long long nc = a.ncell;
     const R inv_dx = R(a.inv_dx[DIR]);
     const R eps = R(a.eps);
-    const EosR<R> er(a.eos);
+    const EosR<R, NF> er(a.eos);
     const R* __restrict__ qin = static_cast<const R*>(a.qin);
 
     // Values of loaded cell k (index s0 - 3 + k along the pencil) -> v[].
@@ -551,12 +548,14 @@ sweep_kernel(const SweepArgs a) {
     for (int k = 0; k < 5; ++k) {
         R v[NL];
         fetch(k, v);
-        if constexpr (EXACT) exact::cons_to_prim<NDIM>(a.eos, v, W[k]);
-        else to_prim<NDIM>(er, v, W[k]);
-        bad |= !(W[k][0] + W[k][1] > R(0));
+        if constexpr (EXACT) exact::cons_to_prim<NDIM, NF>(a.eos, v, W[k]);
+        else to_prim<NDIM, NF>(er, v, W[k]);
+        bad |= !(mix_rho<NF>(W[k]) > R(0));
     }
     R vmPrev[NEQ], Fprev[NEQ];
-    R ufPrev = R(0), alphaCell = R(0);
+    R ufPrev = R(0), alphaCell[NA];
+#pragma unroll
+    for (int i = 0; i < NA; ++i) alphaCell[i] = R(0);
 #pragma unroll
     for (int f = 0; f < NEQ; ++f) vmPrev[f] = Fprev[f] = R(0);
 
@@ -647,8 +646,8 @@ sweep_kernel(const SweepArgs a) {
         }
         if (j >= s0) {
             R F[NEQ], uf;
-            if constexpr (EXACT) bad |= exact::hllc<NDIM, DIR>(a.eos, vmPrev, vp, F, uf);
-            else bad |= hllc<NDIM, DIR, R>(er, vmPrev, vp, F, uf);
+            if constexpr (EXACT) bad |= exact::hllc<NDIM, DIR, NF>(a.eos, vmPrev, vp, F, uf);
+            else bad |= hllc<NDIM, DIR, R, NF>(er, vmPrev, vp, F, uf);
             if (j > s0 && (active || OSTAGE_ON)) {
                 // cell i = j - 1 is complete: faces i-1/2 (Fprev) and i+1/2 (F)
                 R L[NEQ];
@@ -661,7 +660,9 @@ sweep_kernel(const SweepArgs a) {
                     }
 #pragma unroll
                     for (int f = 0; f < NEQ; ++f) L[f] = exact::div_rcp(Fprev[f] - F[f], dx, rdx);
-                    L[IA] = L[IA] + exact::div_rcp(alphaCell * (uf - ufPrev), dx, rdx);
+#pragma unroll
+                    for (int i = 0; i < NA; ++i)
+                        L[IA + i] = L[IA + i] + exact::div_rcp(alphaCell[i] * (uf - ufPrev), dx, rdx);
                 } else {
                     R idx = inv_dx;
                     if (NU && a.cw[DIR]) {
@@ -670,7 +671,8 @@ sweep_kernel(const SweepArgs a) {
                     }
 #pragma unroll
                     for (int f = 0; f < NEQ; ++f) L[f] = (Fprev[f] - F[f]) * idx;
-                    L[IA] += alphaCell * (uf - ufPrev) * idx;
+#pragma unroll
+                    for (int i = 0; i < NA; ++i) L[IA + i] += alphaCell[i] * (uf - ufPrev) * idx;
                 }
                 const long long c = base + (long long)(j - 1) * ss;
                 if constexpr (OSTAGE_ON) {
@@ -732,11 +734,11 @@ sweep_kernel(const SweepArgs a) {
                             double dx3[3], rdx3[3], idx3[3];
                             cell_geometry<DIR, NU>(a, j - 1, active ? ia : na - 1, b, dx3, rdx3, idx3);
                             if constexpr (EXACT) {
-                                s = exact::cell_wavespeed<NDIM>(a.eos, qnew, dx3, rdx3, bad);
+                                s = exact::cell_wavespeed<NDIM, NF>(a.eos, qnew, dx3, rdx3, bad);
                             } else {
                                 double wn[NEQ];
-                                to_prim<NDIM>(er, qnew, wn);
-                                s = cell_wavespeed<NDIM, double>(er, wn, idx3, bad);
+                                to_prim<NDIM, NF>(er, qnew, wn);
+                                s = cell_wavespeed<NDIM, double, NF>(er, wn, idx3, bad);
                             }
                             smax = s > smax ? s : smax;
                         }
@@ -744,7 +746,7 @@ sweep_kernel(const SweepArgs a) {
                         float q32[NEQ];
 #pragma unroll
                         for (int f = 0; f < NEQ; ++f) q32[f] = d2f_bits(qnew[f]);
-                        float pnew = mixed_pressure<NDIM>(a.eos, qnew, q32);
+                        float pnew = mixed_pressure<NDIM, NF>(a.eos, qnew, q32);
                         float* o32 = static_cast<float*>(a.stage == 3 ? a.qout2 : a.qout);
 #pragma unroll
                         for (int f = 0; f < NEQ; ++f) o32[f * nc + c] = q32[f];
@@ -757,10 +759,10 @@ sweep_kernel(const SweepArgs a) {
 #pragma unroll
                             for (int f = 0; f < NEQ; ++f) v[f] = q32[f];
                             v[IE] = pnew;
-                            to_prim<NDIM>(er, v, wn);
+                            to_prim<NDIM, NF>(er, v, wn);
                             double dx3[3], rdx3[3], idx3[3];
                             cell_geometry<DIR, NU>(a, j - 1, active ? ia : na - 1, b, dx3, rdx3, idx3);
-                            R s = cell_wavespeed<NDIM, float>(er, wn, idx3, bad);
+                            R s = cell_wavespeed<NDIM, float, NF>(er, wn, idx3, bad);
                             smax = s > smax ? s : smax;
                         }
                     }
@@ -795,16 +797,17 @@ sweep_kernel(const SweepArgs a) {
         }
 #pragma unroll
         for (int f = 0; f < NEQ; ++f) vmPrev[f] = vm[f];
-        alphaCell = W[2][IA];
+#pragma unroll
+        for (int i = 0; i < NA; ++i) alphaCell[i] = W[2][IA + i];
         if (j < s1) {
 #pragma unroll
             for (int k = 0; k < 4; ++k)
 #pragma unroll
                 for (int f = 0; f < NEQ; ++f) W[k][f] = W[k + 1][f];
             if (!PREFETCH) fetch(j + 3 - (s0 - 3), vnext);
-            if constexpr (EXACT) exact::cons_to_prim<NDIM>(a.eos, vnext, W[4]);
-            else to_prim<NDIM>(er, vnext, W[4]);
-            bad |= !(W[4][0] + W[4][1] > R(0));
+            if constexpr (EXACT) exact::cons_to_prim<NDIM, NF>(a.eos, vnext, W[4]);
+            else to_prim<NDIM, NF>(er, vnext, W[4]);
+            bad |= !(mix_rho<NF>(W[4]) > R(0));
         }
     }
     bad = bad && active;
@@ -838,47 +841,60 @@ sweep_kernel(const SweepArgs a) {
 
 // Launch one sweep: the valid (direction, mode) pairs are x FIRST, y MID
 // (3-D), and LAST_RK / LAST_RHS on the last direction.
-template <int NDIM, int DIR, int MODE, int FORM>
+template <int NDIM, int DIR, int MODE, int FORM, int NF>
 cudaError_t launch_one(long long warps, const SweepArgs& a, cudaStream_t s) {
     constexpr int T = sweep_threads(DIR);
     const long long blocks = (warps * 32 + T - 1) / T;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     const bool nu = a.cw[0] || a.cw[1] || a.cw[2];
-    if constexpr (FORM != FORM_GATED) {
+    if constexpr (FORM != FORM_GATED && NF == 2) {
         if (nu) {
-            sweep_kernel<NDIM, DIR, MODE, FORM, true><<<(unsigned)blocks, T, 0, s>>>(a);
+            sweep_kernel<NDIM, DIR, MODE, FORM, true, NF><<<(unsigned)blocks, T, 0, s>>>(a);
             return cudaGetLastError();
         }
     }
-    sweep_kernel<NDIM, DIR, MODE, FORM, false><<<(unsigned)blocks, T, 0, s>>>(a);
+    if (nu) return cudaErrorInvalidValue;   // non-uniform grids: two fluids, non-gated forms
+    sweep_kernel<NDIM, DIR, MODE, FORM, false, NF><<<(unsigned)blocks, T, 0, s>>>(a);
     return cudaGetLastError();
 }
 
-template <int NDIM, int FORM>
+template <int NDIM, int FORM, int NF>
 cudaError_t launch_sweep_t(int dir, int mode, const SweepArgs& a, cudaStream_t s) {
     const long long warps = sweep_warps(dir, a.n, a.seg);
     if (warps <= 0) return cudaSuccess;
     constexpr int LAST = NDIM - 1;
     if (dir == 0 && mode == SW_FIRST && NDIM > 1) {
-        if constexpr (NDIM > 1) return launch_one<NDIM, 0, SW_FIRST, FORM>(warps, a, s);
+        if constexpr (NDIM > 1) return launch_one<NDIM, 0, SW_FIRST, FORM, NF>(warps, a, s);
     } else if (dir == 1 && mode == SW_MID && NDIM == 3) {
-        if constexpr (NDIM == 3) return launch_one<NDIM, 1, SW_MID, FORM>(warps, a, s);
+        if constexpr (NDIM == 3) return launch_one<NDIM, 1, SW_MID, FORM, NF>(warps, a, s);
     } else if (dir == LAST && mode == SW_LAST_RK) {
-        return launch_one<NDIM, LAST, SW_LAST_RK, FORM>(warps, a, s);
+        return launch_one<NDIM, LAST, SW_LAST_RK, FORM, NF>(warps, a, s);
     } else if (dir == LAST && mode == SW_LAST_RHS) {
-        return launch_one<NDIM, LAST, SW_LAST_RHS, FORM>(warps, a, s);
+        return launch_one<NDIM, LAST, SW_LAST_RHS, FORM, NF>(warps, a, s);
     }
     return cudaErrorInvalidValue;
 }
 
-template <int FORM>
-cudaError_t launch_sweep_any(int ndim, int dir, int mode, const SweepArgs& a, cudaStream_t s) {
+template <int FORM, int NF>
+cudaError_t launch_sweep_nf(int ndim, int dir, int mode, const SweepArgs& a, cudaStream_t s) {
     switch (ndim) {
-        case 1: return launch_sweep_t<1, FORM>(dir, mode, a, s);
-        case 2: return launch_sweep_t<2, FORM>(dir, mode, a, s);
-        case 3: return launch_sweep_t<3, FORM>(dir, mode, a, s);
+        case 1: return launch_sweep_t<1, FORM, NF>(dir, mode, a, s);
+        case 2: return launch_sweep_t<2, FORM, NF>(dir, mode, a, s);
+        case 3: return launch_sweep_t<3, FORM, NF>(dir, mode, a, s);
         default: return cudaErrorInvalidValue;
     }
+}
+
+// Dispatch on the number of dimensions and of fluids (a.eos.nf): 2 in every
+// form, 3 and 4 in the non-gated forms.
+template <int FORM>
+cudaError_t launch_sweep_any(int ndim, int dir, int mode, const SweepArgs& a, cudaStream_t s) {
+    if (a.eos.nf == 2) return launch_sweep_nf<FORM, 2>(ndim, dir, mode, a, s);
+    if constexpr (FORM != FORM_GATED) {
+        if (a.eos.nf == 3) return launch_sweep_nf<FORM, 3>(ndim, dir, mode, a, s);
+        if (a.eos.nf == 4) return launch_sweep_nf<FORM, 4>(ndim, dir, mode, a, s);
+    }
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace mfc5

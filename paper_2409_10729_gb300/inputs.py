@@ -339,6 +339,76 @@ def shock_droplets(n: int = 256, seed: int = 2409, mach: float = 2.0, gap: float
     return p, assemble(p, a1, 1000.0, rho_air, [u, 0.0, 0.0], pres)
 
 
+OIL = (2.35, 1.0e9)   # a third stiffened gas (a generic liquid) for the N-fluid cases
+GLYCOL = (1.8, 2.0e8)
+
+
+def random_periodic_n(ndim: int, n, nfluids: int = 3, seed: int = 0):
+    """N-fluid counterpart of random_periodic: smooth random fields and N - 1
+    liquid blobs (water, oil, glycol-like) in air on a periodic box; every
+    volume fraction stays within [ALPHA_EPS, 1]."""
+    rng = np.random.default_rng(seed)
+    ns = [n] * ndim if np.isscalar(n) else list(n)
+    fl = [WATER, OIL, GLYCOL][:nfluids - 1] + [AIR]
+    p = make_params(ndim, ns, [0.0] * ndim, [1.0] * ndim, PERIODIC, gamma=[f[0] for f in fl],
+                    pi_inf=[f[1] for f in fl])
+    c = cell_centres(p)
+    grids = np.meshgrid(*c[:ndim][::-1], indexing="ij")[::-1]
+    shp = shape_of(p)[1:]
+    grids = [g.reshape(shp) for g in grids]
+
+    def modes(scale):
+        f = np.zeros(shp)
+        for _ in range(3):
+            k = rng.integers(1, 3, size=ndim)
+            ph = rng.uniform(0, 2 * math.pi)
+            arg = sum(2 * math.pi * k[d] * grids[d] for d in range(ndim)) + ph
+            f = f + scale * rng.uniform(0.3, 1.0) * np.sin(arg)
+        return f
+
+    width = 1.5 / min(ns)
+    raw = []
+    for i in range(nfluids - 1):
+        centre = rng.uniform(0.25, 0.75, size=ndim)
+        r = np.sqrt(sum((grids[d] - centre[d]) ** 2 for d in range(ndim)))
+        raw.append(np.clip(0.5 * (1.0 + np.tanh((0.18 - r) / width)), ALPHA_EPS, 1.0))
+    raw.append(np.full(shp, 0.3))          # air everywhere, diluted where liquids are
+    tot = sum(raw)
+    alphas = [np.maximum(a / tot, ALPHA_EPS) for a in raw[:-1]]
+    rhos = [1000.0 * (1.0 + 0.01 * modes(1.0)), 900.0 * (1.0 + 0.01 * modes(1.0)),
+            1100.0 * (1.0 + 0.01 * modes(1.0))][:nfluids - 1] + [1.2 * (1.0 + 0.2 * modes(1.0))]
+    vel = [20.0 * modes(1.0) for _ in range(ndim)]
+    pres = 1.0e7 * (1.0 + 0.2 * modes(1.0))
+    return p, assemble_n(p, alphas, rhos, vel, pres)
+
+
+def shock_droplets_3fluid(n: int = 256, seed: int = 2409, mach: float = 2.0, gap: float = 0.01,
+                          count: int = 8, smear: float = 1.5):
+    """The shock-droplet array with three fluids: droplets alternate between
+    water (fluid 1) and oil (fluid 2), in air (fluid 3)."""
+    drops = droplet_layout(seed, count)
+    p = make_params(3, [n, n, n], [0.0] * 3, [1.0] * 3, TRANSMISSIVE, gamma=[WATER[0], OIL[0], AIR[0]],
+                    pi_inf=[WATER[1], OIL[1], AIR[1]])
+    x, y, z = cell_centres(p)
+    a = [np.full((n, n, n), ALPHA_EPS), np.full((n, n, n), ALPHA_EPS)]
+    h = 1.0 / n
+    for k, (cx, cy, cz, r) in enumerate(drops):
+        lo = [max(0, int((c - r) / h) - 8) for c in (cx, cy, cz)]
+        hi = [min(n, int((c + r) / h) + 9) for c in (cx, cy, cz)]
+        sl = (slice(lo[2], hi[2]), slice(lo[1], hi[1]), slice(lo[0], hi[0]))
+        d2 = (x[None, None, lo[0]:hi[0]] - cx) ** 2 + (y[None, lo[1]:hi[1], None] - cy) ** 2
+        d2 = d2 + (z[lo[2]:hi[2], None, None] - cz) ** 2
+        prof = diffuse_alpha(np.sqrt(d2) - r, smear * h)
+        a[k % 2][sl] = np.maximum(a[k % 2][sl], np.minimum(prof, 1.0 - 2 * ALPHA_EPS))
+    xs = float(np.min(drops[:, 0] - drops[:, 3])) - gap
+    rho2, u2, p2, _ = normal_shock(AIR[0], 1.2, 1.0e5, mach)
+    post = (x < xs)[None, None, :]
+    rho_air = np.where(post, rho2, 1.2)
+    u = np.where(post, u2, 0.0)
+    pres = np.where(post, p2, 1.0e5)
+    return p, assemble_n(p, a, [1000.0, 900.0, rho_air], [u, 0.0, 0.0], pres)
+
+
 def embed_1d(p1d: dict, w1d: np.ndarray, axis: int, m: int = 4):
     """Lay a 1-D case along `axis` of a 3-D box with m cells in the other two
     directions (transmissive there).  Velocity goes to component `axis`."""

@@ -29,11 +29,12 @@ class MfcParams(ctypes.Structure):
         ("lo", ctypes.c_double * 3),
         ("hi", ctypes.c_double * 3),
         ("bc", (ctypes.c_int * 2) * 3),
-        ("gamma", ctypes.c_double * 2),
-        ("pi_inf", ctypes.c_double * 2),
+        ("gamma", ctypes.c_double * 4),
+        ("pi_inf", ctypes.c_double * 4),
         ("weno_eps", ctypes.c_double),
         ("precision", ctypes.c_int),
         ("weno_order", ctypes.c_int),
+        ("nfluids", ctypes.c_int),
     ]
 
 
@@ -118,7 +119,9 @@ def make_params(p: dict, precision="fp64") -> MfcParams:
         s.hi[d] = float(p["hi"][d])
         s.bc[d][0] = int(p["bc"][d][0])
         s.bc[d][1] = int(p["bc"][d][1])
-    for i in range(2):
+    nf = len(p["gamma"])
+    s.nfluids = nf
+    for i in range(nf):
         s.gamma[i] = float(p["gamma"][i])
         s.pi_inf[i] = float(p["pi_inf"][i])
     s.weno_eps = float(p.get("weno_eps", 1e-6))
@@ -150,7 +153,7 @@ class Solver:
     def __init__(self, p: dict, precision="fp64", stream=None):
         import torch
         self.p = p
-        self.neq = int(p["ndim"]) + 4
+        self.neq = 2 * len(p["gamma"]) + int(p["ndim"])
         self.shape = (self.neq, int(p["n"][2]) if p["ndim"] > 2 else 1,
                       int(p["n"][1]) if p["ndim"] > 1 else 1, int(p["n"][0]))
         self.size = int(np.prod(self.shape))

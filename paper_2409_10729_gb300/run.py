@@ -14,7 +14,7 @@ import time
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--case", choices=["droplets", "column", "tube"], default="droplets")
+    ap.add_argument("--case", choices=["droplets", "droplets3", "column", "tube"], default="droplets")
     ap.add_argument("--n", type=int, default=128, help="cells per dimension (column: ny, nx = 2 ny)")
     ap.add_argument("--form", choices=["fp64", "fp64_fast", "mixed", "gated"], default="fp64")
     ap.add_argument("--steps", type=int, default=2)
@@ -34,6 +34,8 @@ def main():
     B.build()
     if args.case == "droplets":
         p, w = I.shock_droplets(args.n)
+    elif args.case == "droplets3":
+        p, w = I.shock_droplets_3fluid(args.n)
     elif args.case == "column":
         p, w = I.shock_water_column(2 * args.n, args.n)
     else:
@@ -58,7 +60,7 @@ def main():
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     ncell = p["n"][0] * p["n"][1] * p["n"][2]
-    neq = p["ndim"] + 4
+    neq = I.neq_of(p)
     grind = ms * 1e6 / (args.steps * 3 * ncell * neq)
     print(f"case={args.case} n={args.n} form={args.form} steps={args.steps} ms/step={ms / args.steps:.3f} "
           f"grind_ns={grind:.5f} t={t:.6e} wall={time.perf_counter() - t0:.2f}s")

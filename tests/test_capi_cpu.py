@@ -73,6 +73,8 @@ def _params(**over):
     dict(bc=[[0, 1], [0, 0], [0, 0]]), dict(bc=[[2, 2], [0, 0], [0, 0]]),
     dict(gamma=[1.0, 1.4]), dict(pi_inf=[-1.0, 0.0]), dict(weno_eps=0.0),
     dict(weno_order=4), dict(weno_order=7), dict(weno_order=3, precision="gated"),
+    dict(gamma=[4.4, 1.4, 2.35], pi_inf=[6e8, 0.0, 1e9], precision="gated"),
+    dict(gamma=[4.4, 1.4, 2.35], pi_inf=[6e8, 0.0, -1.0]),
 ])
 def test_create_rejects_bad_params_before_touching_the_device(lib, bad):
     handle = ctypes.c_void_p()

@@ -67,18 +67,18 @@ def solver(p, precision="fp64"):
     return mfc.Solver(p, precision)
 
 
-def rel_err(a, b):
+def rel_err(a, b, nf=2):
     """Per-field relative L-infinity error of a against reference b.  The
     momentum components are rows of one vector field and share its scale,
     max over cells of |rho u| (otherwise a component that is ~0 in a given
     orientation, e.g. rho v in a flow along x, would be judged against its own
-    round-off-sized values)."""
-    ndim = a.shape[0] - 4
+    round-off-sized values).  nf: number of fluids (momenta at rows nf ..)."""
+    ndim = a.shape[0] - 2 * nf
     a = a.reshape(a.shape[0], -1)
     b = b.reshape(b.shape[0], -1)
     scale = np.abs(b).max(1)
-    mom = np.sqrt((b[2:2 + ndim] ** 2).sum(0)).max()
-    scale[2:2 + ndim] = mom
+    mom = np.sqrt((b[nf:nf + ndim] ** 2).sum(0)).max()
+    scale[nf:nf + ndim] = mom
     return np.abs(a - b).max(1) / np.maximum(scale, 1e-300)
 
 
@@ -86,13 +86,14 @@ def rhs_scale(p, q, Lo, S):
     """Per-field size of the fluxes a RHS is formed from, per unit length:
     max(max|L_f|, max|q_f| S), plus max(p) max(1/dx_d) on the momentum rows
     (their normal flux carries the pressure)."""
-    nf = q.shape[0]
-    qf = q.reshape(nf, -1)
+    nq = q.shape[0]
+    qf = q.reshape(nq, -1)
     scale = np.maximum(np.abs(Lo.reshape(Lo.shape[0], -1)).max(1), np.abs(qf).max(1) * S)
     ndim = p["ndim"]
-    pmax = np.abs(O.cons_to_prim(p, q)[2 + ndim]).max()
+    nfl = len(p["gamma"])
+    pmax = np.abs(O.cons_to_prim(p, q)[nfl + ndim]).max()
     inv_dx = max(p["n"][d] / (p["hi"][d] - p["lo"][d]) for d in range(ndim))
-    scale[2:2 + ndim] = np.maximum(scale[2:2 + ndim], pmax * inv_dx)
+    scale[nfl:nfl + ndim] = np.maximum(scale[nfl:nfl + ndim], pmax * inv_dx)
     return scale
 
 
@@ -473,3 +474,78 @@ def test_set_grid_rejections():
         g = solver(dict(p, **kw), prec)
         with pytest.raises(mfc.MfcError):
             g.set_grid(0, e)
+
+
+# ---------------------------------------------------------------- N fluids
+# The N-fluid model (N = 3, 4; the oracle's N-fluid pins fix the model) to
+# the same bar: bit-identical in the FP64 form, 1e-12 in the reorganised one.
+
+NF_SMALL = [(1, [33], 3), (2, [13, 9], 3), (3, [9, 7, 6], 3), (2, [14, 11], 4), (3, [8, 7, 5], 4)]
+
+
+def check_state_n(form, got, ref, nf):
+    if form == "fp64":
+        assert np.array_equal(got, ref), f"not bit-identical, rel err {rel_err(got, ref, nf)}"
+    else:
+        assert rel_err(got, ref, nf).max() <= TOL
+
+
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("ndim,n,nf", NF_SMALL)
+def test_nfluid_rhs_parity(ndim, n, nf, form):
+    p, w = I.random_periodic_n(ndim, n, nf, seed=70 + ndim + nf)
+    s = solver(p, form)
+    s.set_state_prim(w)
+    L = s.rhs()
+    q = O.prim_to_cons(p, w)
+    assert np.array_equal(s.get_state(), q)
+    Lo = O.rhs(p, q)
+    check_rhs(form, p, L, Lo, q, O.max_wavespeed(p, q))
+    if form == "fp64":
+        assert s.max_wavespeed() == O.max_wavespeed(p, q)
+
+
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("ndim,n,nf", NF_SMALL)
+def test_nfluid_cfl_steps_parity(ndim, n, nf, form):
+    p, w = I.random_periodic_n(ndim, n, nf, seed=80 + ndim + nf)
+    s = solver(p, form)
+    s.set_state_prim(w)
+    t = s.step_rk3(0.4, 5)
+    qo, to = O.run_cfl(p, O.prim_to_cons(p, w), 0.4, 5)
+    check_state_n(form, s.get_state(), qo, nf)
+    assert t == to if form == "fp64" else abs(t - to) <= 1e-13 * to
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_three_fluid_droplets_full_run(form):
+    """Water and oil droplets in air (32^3), Mach-2 shock, 60 steps."""
+    p, w = I.shock_droplets_3fluid(32)
+    s = solver(p, form)
+    s.set_state_prim(w)
+    t = s.step_rk3(0.4, 60)
+    qo, to = oracle_run("droplets3_32x60", p, w, 60)
+    check_state_n(form, s.get_state(), qo, 3)
+    assert t == to if form == "fp64" else abs(t - to) <= 1e-12 * to
+
+
+def test_three_fluid_mixed_form_error_against_oracle():
+    p, w = I.shock_droplets_3fluid(32)
+    s = solver(p, "mixed")
+    s.set_state_prim(w)
+    s.step_rk3(0.4, 60)
+    qo, _ = oracle_run("droplets3_32x60", p, w, 60)
+    q = s.get_state()
+    assert rel_err(q, qo, 3).max() <= 1e-3
+    l1 = np.abs(q - qo).reshape(9, -1).sum(1) / np.abs(qo).reshape(9, -1).sum(1)
+    assert l1[[0, 1, 2, 6, 7, 8]].max() <= 1e-5, l1
+
+
+def test_nfluid_rejections():
+    from paper_2409_10729_gb300 import mfc
+    p, w = I.random_periodic_n(2, [16, 8], 3, seed=1)
+    with pytest.raises(mfc.MfcError):
+        solver(p, "gated")
+    s = solver(p, "fp64")
+    with pytest.raises(mfc.MfcError):
+        s.set_grid(0, I.tanh_edges(16, 0.0, 1.0, 0.5))
