@@ -7,7 +7,8 @@ operation order, bit-identical to the oracle; the headline value), the
 reorganised FP64 form, the mixed-precision form (512^3) and the MLP-gated
 form (256^3, trained weights from paper_2409_10729_gb300/gate_weights.npy),
 plus the third-order reconstruction option (WENO3-JS) and a tanh-refined
-(non-uniform) grid in the FP64 (256^3) and mixed (512^3) forms.
+(non-uniform) grid in the FP64 (256^3) and mixed (512^3) forms, and a
+three-fluid droplet case (256^3, 9 equations) in both.
 
 Workload (per GPU): the 3-D shock / droplet array, 256^3 cells, 7 equations,
 FP64, SSP-RK3 at CFL 0.4 (the timed "step" is one RK3 step = 3 RHS
@@ -184,7 +185,7 @@ def time_form(form, p, w, steps, warmup, device_index, rank, world):
     launches = s.launches_per_step() * steps
     s.set_timing(False)
     ncell = p["n"][0] * p["n"][1] * p["n"][2]
-    neq = p["ndim"] + 4
+    neq = 2 * len(p["gamma"]) + p["ndim"]
     grind = ms * 1e6 / (steps * 3 * ncell * neq * world)
     s.close()
     del s
@@ -196,7 +197,7 @@ def time_form(form, p, w, steps, warmup, device_index, rank, world):
 def roofline_for(form, res, peak_alu, alu_src, hbm_peak, hbm_src):
     """Roofline object for the dominant kernel of one form."""
     kt = res["kernels"]
-    base = form.replace("_weno3", "").replace("_stretched", "")
+    base = form.replace("_weno3", "").replace("_stretched", "").replace("_3fluid", "")
     name = max((k for k in kt if kt[k][1] > 0), key=lambda k: kt[k][0])
     total_ms, count = kt[name]
     avg_s = total_ms / count * 1e-3
@@ -316,6 +317,9 @@ def run_ours(args):
     # a tanh-refined grid in every direction (cells at the centre half as wide)
     forms["fp64_stretched"] = time_form("fp64", stretched(p), w, max(2, args.steps // 2), args.warmup,
                                         local, rank, world)
+    # three fluids: water and oil droplets in air (9 equations)
+    p3, w3 = I.shock_droplets_3fluid(256)
+    forms["fp64_3fluid"] = time_form("fp64", p3, w3, max(2, args.steps // 2), args.warmup, local, rank, world)
     if not args.no_mixed:
         forms["gated"] = time_form("gated", p, w, args.steps, args.warmup, local, rank, world)
         pm, wm = I.shock_droplets(512)
@@ -324,6 +328,7 @@ def run_ours(args):
                                          args.warmup, local, rank, world)
         forms["mixed_stretched"] = time_form("mixed", stretched(pm), wm, max(2, args.steps // 2), args.warmup,
                                              local, rank, world)
+        forms["mixed_3fluid"] = time_form("mixed", p3, w3, max(2, args.steps // 2), args.warmup, local, rank, world)
         del wm
 
     # end to end through the C ABI with pinned host buffers: per step, copy
