@@ -255,6 +255,32 @@ def test_full_size_sampled(case):
     _check_sampled(p, s, qf, 2)
 
 
+def test_largest_size_sampled():
+    """The largest configuration (3-D droplets at 512^3, 134M cells, the mixed
+    form's benchmark size): FP64 RHS at 4096+ sampled cells and the wave speed
+    bit for bit, before and after two steps; the mixed form's RHS at the same
+    cells within FP32 accuracy of the flux scale."""
+    p, w = I.shock_droplets(512)
+    q0 = O.prim_to_cons(p, w)
+    s = solver(p)
+    s.set_state(q0)
+    _check_sampled(p, s, q0, 3)
+    m = solver(p, "mixed")
+    m.set_state(q0)
+    cells = _sample_cells(p, 4096, 3)
+    Lm = m.rhs().reshape(q0.shape[0], -1)[:, cells]
+    m.close()
+    Lo = O.rhs_points(p, q0, cells).T
+    S = O.max_wavespeed(p, q0)
+    # flux scale as in rhs_scale, from the whole state
+    scale = np.maximum(np.abs(Lo).max(1), np.abs(q0.reshape(q0.shape[0], -1)).max(1) * S)
+    pmax = np.abs(O.cons_to_prim(p, q0)[5]).max()
+    scale[2:5] = np.maximum(scale[2:5], pmax * 512.0)
+    assert (np.abs(Lm - Lo).max(1) / scale).max() <= 1e-5
+    s.step_rk3(0.4, 2)
+    _check_sampled(p, s, s.get_state(), 4)
+
+
 @pytest.mark.parametrize("where", ["interior", "edge"])
 def test_nonphysical_state_is_reported(where):
     """A cell with negative density: both sides report it (MFC_ENONPHYSICAL /
@@ -549,3 +575,32 @@ def test_nfluid_rejections():
     s = solver(p, "fp64")
     with pytest.raises(mfc.MfcError):
         s.set_grid(0, I.tanh_edges(16, 0.0, 1.0, 0.5))
+
+
+# ---------------------------------------------------------------- degenerate grids
+# Directions with fewer cells than the five-cell stencil (1 or 2 cells: every
+# ghost is a copy or a wrap of them), single cells, and segments of one cell.
+
+DEGENERATE = [(1, [1], 0), (1, [1], 1), (1, [2], 0), (1, [3], 1), (2, [1, 9], 0), (2, [9, 1], 1),
+              (2, [2, 2], 1), (3, [1, 1, 1], 0), (3, [5, 1, 3], 1), (3, [1, 33, 2], 0)]
+
+
+@pytest.mark.parametrize("form", FORMS + ["mixed"])
+@pytest.mark.parametrize("ndim,n,bc", DEGENERATE)
+def test_degenerate_grids(ndim, n, bc, form):
+    p, w = _case(ndim, n, bc, seed=90 + ndim)
+    s = solver(p, form)
+    s.set_state_prim(w)
+    L = s.rhs()
+    q = O.prim_to_cons(p, w)
+    Lo = O.rhs(p, q)
+    S = O.max_wavespeed(p, q)
+    t = s.step_rk3(0.4, 3)
+    qo, to = O.run_cfl(p, q, 0.4, 3)
+    if form == "mixed":
+        assert rhs_err(p, L, Lo, q, S).max() <= 1e-5
+        assert rel_err(s.get_state(), qo).max() <= 1e-5
+    else:
+        check_rhs(form, p, L, Lo, q, S)
+        check_state(form, s.get_state(), qo)
+        assert t == to if form == "fp64" else abs(t - to) <= 1e-13 * to
