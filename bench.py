@@ -53,6 +53,26 @@ ALG_BYTES = {"fp64": 8.0 / 3.0 * 8.0, "fp64_fast": 8.0 / 3.0 * 8.0, "mixed": (12
              "gated": (12.0 + 16.0 + 20.0) / 3.0}
 
 
+def max_over_ranks(value: float, world: int) -> float:
+    """The largest of the ranks' values (the slowest rank's time); the
+    process group's own device (CUDA under NCCL, CPU under gloo)."""
+    if world == 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_grind(seconds: float, steps: int, ncell: int, neq: int, world: int) -> float:
+    """Whole-job grind time in ns per (cell x equation x RHS evaluation): the
+    slowest rank's time over the cells of all ranks (each rank runs its own
+    replica: weak scaling), 3 RHS evaluations per SSP-RK3 step."""
+    return seconds * 1e9 / (steps * 3 * ncell * neq * world)
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -174,11 +194,8 @@ def time_form(form, p, w, steps, warmup, device_index, rank, world):
     ev1.record(stream)
     torch.cuda.synchronize()
     clocks = sampler.stop()
-    ms = ev0.elapsed_time(ev1)
+    ms = max_over_ranks(ev0.elapsed_time(ev1), world)
     if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
         torch.distributed.barrier()
     kt = s.kernel_times()
     gate = (*s.gate_stats(), s.gate_flat()) if form == "gated" else None
@@ -186,7 +203,7 @@ def time_form(form, p, w, steps, warmup, device_index, rank, world):
     s.set_timing(False)
     ncell = p["n"][0] * p["n"][1] * p["n"][2]
     neq = 2 * len(p["gamma"]) + p["ndim"]
-    grind = ms * 1e6 / (steps * 3 * ncell * neq * world)
+    grind = aggregate_grind(ms * 1e-3, steps, ncell, neq, world)
     s.close()
     del s
     torch.cuda.empty_cache()
@@ -351,13 +368,9 @@ def run_ours(args):
         s.step_rk3(CFL, 1)
         s.get_state(q_out)
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
     ncell, neq = res["ncell"], res["neq"]
-    e2e_grind = e2e_s * 1e9 / (e2e_steps * 3 * ncell * neq * world)
+    e2e_grind = aggregate_grind(e2e_s, e2e_steps, ncell, neq, world)
     s.close()
 
     if rank != 0:
