@@ -243,6 +243,14 @@ int mfc_rhs_noalloc(const mfc_params* params, const double* q, double* rhs, void
  * memory and synchronises the legacy default stream. */
 int mfc_selfcheck_conversions(long long n, unsigned long long seed, long long* mismatches);
 
+/* Instrumentation, no counterpart in the paper: checks the FP64 form's
+ * integer-pipe WENO5 operations (products by 3, 5, 7 and 11, quotients by 6)
+ * against the FP64 instructions on n pseudo-random patterns (all exponents,
+ * zeros, subnormals, infinities, NaNs); *mismatches receives the number of
+ * differing results (0 expected).  Allocates 4 bytes of device memory and
+ * synchronises the legacy default stream. */
+int mfc_selfcheck_exact_ops(long long n, unsigned long long seed, long long* mismatches);
+
 /* Message for a status code (static storage). */
 const char* mfc_strerror(int status);
 

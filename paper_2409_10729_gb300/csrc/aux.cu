@@ -261,6 +261,38 @@ __global__ void conversion_check_kernel(long long n, unsigned long long seed, un
     if (bad) atomicAdd(mismatches, bad);
 }
 
+// Self-check of the FP64 form's integer-pipe products K v and quotients x/6
+// against the FP64 instructions: pseudo-random patterns over every exponent,
+// with a share of zeros, subnormals, infinities, NaNs and exponents at the
+// ends of the range where the integer path hands over to the FP64 one.
+__global__ void exact_ops_check_kernel(long long n, unsigned long long seed, unsigned* mismatches) {
+    unsigned bad = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        unsigned long long z = seed + (unsigned long long)i * 0x9e3779b97f4a7c15ULL;
+        z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+        z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+        z ^= z >> 31;
+        unsigned long long bits = z;
+        const unsigned sel = (unsigned)(i & 15);
+        if (sel == 0) bits &= 0x8000000000000000ULL;                              // +-0
+        else if (sel == 1) bits &= 0x800fffffffffffffULL;                         // subnormal
+        else if (sel == 2) bits = (bits & 0x800fffffffffffffULL) | ((unsigned long long)((z >> 11) % 10) << 52);
+        else if (sel == 3) bits = (bits & 0x800fffffffffffffULL) | ((unsigned long long)(2047 - (z >> 11) % 10) << 52);
+        else if (sel == 4) bits = (bits & 0x800fffffffffffffULL) | ((unsigned long long)(1018 + (z >> 11) % 12) << 52);
+        const double x = __longlong_as_double((long long)bits);
+        const double r[5] = {exact::mul_small<3>(x), exact::mul_small<5>(x), exact::mul_small<7>(x),
+                             exact::mul_small<11>(x), exact::div6(x)};
+        const double h[5] = {__dmul_rn(3.0, x), __dmul_rn(5.0, x), __dmul_rn(7.0, x), __dmul_rn(11.0, x),
+                             __ddiv_rn(x, 6.0)};
+#pragma unroll
+        for (int k = 0; k < 5; ++k)
+            if (__double_as_longlong(r[k]) != __double_as_longlong(h[k]) && !(r[k] != r[k] && h[k] != h[k]))
+                ++bad;
+    }
+    if (bad) atomicAdd(mismatches, bad);
+}
+
 }  // namespace mfc5
 
 extern "C" int mfc_selfcheck_conversions(long long n, unsigned long long seed, long long* mismatches) {
@@ -269,6 +301,20 @@ extern "C" int mfc_selfcheck_conversions(long long n, unsigned long long seed, l
     if (cudaMalloc(&d, sizeof(unsigned)) != cudaSuccess) return -3;
     cudaMemset(d, 0, sizeof(unsigned));
     mfc5::conversion_check_kernel<<<152 * 8, 256>>>(n, seed, d);
+    unsigned h = 0;
+    cudaError_t err = cudaMemcpy(&h, d, sizeof(unsigned), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (err != cudaSuccess) return -3;
+    *mismatches = (long long)h;
+    return 0;
+}
+
+extern "C" int mfc_selfcheck_exact_ops(long long n, unsigned long long seed, long long* mismatches) {
+    if (n <= 0 || !mismatches) return -1;
+    unsigned* d = nullptr;
+    if (cudaMalloc(&d, sizeof(unsigned)) != cudaSuccess) return -3;
+    cudaMemset(d, 0, sizeof(unsigned));
+    mfc5::exact_ops_check_kernel<<<152 * 8, 256>>>(n, seed, d);
     unsigned h = 0;
     cudaError_t err = cudaMemcpy(&h, d, sizeof(unsigned), cudaMemcpyDeviceToHost);
     cudaFree(d);

@@ -33,7 +33,6 @@ struct mfc_ctx {
     double inv_dx[3];
     double dx[3], rdx[3];
     int periodic[3];
-    int seg[3];
     Eos eos;
     int device;
     cudaStream_t stream;
@@ -95,15 +94,6 @@ static int validate(const mfc_params* p) {
     return MFC_OK;
 }
 
-static int pick_seg(int dir, const int* n) {
-    // longest segment (fewest duplicated halo cells) that still gives every
-    // SM a few warps
-    const long long want_threads = 152LL * 256;
-    int seg = 32;
-    while (seg > 4 && sweep_warps(dir, n, seg) * 32 < want_threads) seg >>= 1;
-    return seg;
-}
-
 static bool fp32_state(const mfc_ctx* c) { return c->form == FORM_MIXED || c->form == FORM_GATED; }
 static size_t state_elem(const mfc_ctx* c) { return fp32_state(c) ? sizeof(float) : sizeof(double); }
 static int state_fields(const mfc_ctx* c) { return fp32_state(c) ? c->neq + 1 : c->neq; }
@@ -149,7 +139,6 @@ extern "C" int mfc_create(const mfc_params* params, void* cuda_stream, mfc_ctx**
         ctx->rdx[d] = 1.0 / ctx->dx[d];
         ctx->periodic[d] = d < ctx->ndim ? params->bc[d][0] == MFC_BC_PERIODIC : 0;
     }
-    for (int d = 0; d < ctx->ndim; ++d) ctx->seg[d] = pick_seg(d, ctx->n);
     ctx->eos = make_eos(params->gamma, params->pi_inf, params_nfluids(params->nfluids));
     ctx->stream = (cudaStream_t)cuda_stream;
 
@@ -225,7 +214,6 @@ static SweepArgs base_args(mfc_ctx* ctx) {
 
 static cudaError_t launch_sweep(mfc_ctx* ctx, int dir, int mode, SweepArgs a, cudaStream_t s) {
     a.periodic = ctx->periodic[dir];
-    a.seg = ctx->seg[dir];
     a.tab = ctx->gtab[dir];
     switch (ctx->form) {
         case FORM_FP64_EXACT: return launch_sweep_fp64x(ctx->ndim, dir, mode, a, s);
@@ -273,6 +261,12 @@ static cudaError_t enqueue_step(mfc_ctx* ctx, cudaStream_t s, bool timed, int* k
 
 static int ensure_graph(mfc_ctx* ctx) {
     if (ctx->graph_ok) return MFC_OK;
+    // the sweeps' launch shapes come from occupancy queries, made here once
+    // rather than inside the capture
+    SweepArgs dry = base_args(ctx);
+    dry.dry = 1;
+    for (int d = 0; d < ctx->ndim; ++d)
+        CK(launch_sweep(ctx, d, d == ctx->ndim - 1 ? SW_LAST_RK : (d == 0 ? SW_FIRST : SW_MID), dry, ctx->stream));
     cudaGraph_t g = NULL;
     CK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = enqueue_step(ctx, ctx->cap_stream, false, NULL, NULL);

@@ -85,7 +85,8 @@ struct SweepArgs {
     double eps;
     int order;            // WENO order, 3 or 5
     int periodic;         // along the sweep direction
-    int seg;              // cells per thread along the sweep direction
+    int seg;              // cells per thread along the sweep direction (set at launch)
+    int dry;              // 1: only pick the launch shape (fills the occupancy caches), launch nothing
     int stage;            // 1, 2, 3
     DevCtrl* ctrl;
     const float* gate_w;  // gated form: the 1281 network weights (device)
@@ -133,6 +134,16 @@ __host__ __device__ constexpr int sweep_threads(int dir) { return dir == 0 ? 32 
 // for the x sweep and for the last sweep with its stage update (1: up to 255
 // registers a thread; 2: 255; 3: 168; 4: 128).  The FP64 forms are bound by the FP64 pipe and lose nothing at
 // two blocks; the FP32 forms need the warps to cover their load latency.
+// Pencil segments per warp (cells along the sweep direction) are lengthened
+// up to MFC_MAX_SEG cells while the grid still fills the device's resident
+// blocks MFC_MIN_WAVES times (measured best at 256^3: FP64 64 cells, mixed
+// 32; at 512^3: mixed 128).
+#ifndef MFC_MAX_SEG
+#define MFC_MAX_SEG 128
+#endif
+#ifndef MFC_MIN_WAVES
+#define MFC_MIN_WAVES 6
+#endif
 #ifndef MFC_MIN_BLOCKS_FP64
 #define MFC_MIN_BLOCKS_FP64 1
 #endif

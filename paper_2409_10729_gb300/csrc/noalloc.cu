@@ -119,10 +119,6 @@ extern "C" int mfc_rhs_noalloc(const mfc_params* params, const double* q, double
     a.qout = rhs;
     for (int d = 0; d < ndim; ++d) {
         a.periodic = params->bc[d][0] == MFC_BC_PERIODIC;
-        // same segment rule as the context path
-        int seg = 32;
-        while (seg > 4 && sweep_warps(d, n, seg) * 32 < 152LL * 256) seg >>= 1;
-        a.seg = seg;
         int mode = d == ndim - 1 ? SW_LAST_RHS : (d == 0 ? SW_FIRST : SW_MID);
         if (launch_sweep_fp64x(ndim, d, mode, a, s) != cudaSuccess) return MFC_ECUDA;
     }

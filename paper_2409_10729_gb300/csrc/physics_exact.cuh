@@ -118,14 +118,56 @@ __device__ __forceinline__ double sound2(double G, double Pi, double rho, double
 // below 2^-1022, that a scaling by 1/4 would round).
 __device__ __forceinline__ double fma2(double k, double v, double x) { return __fma_rn(k, v, x); }
 
+// Two correctly rounded operations of WENO5 computed from the IEEE 754
+// binary64 fields on the integer pipes (GB300's FP64 pipe retires two
+// operations per SM and clock): the product of v by a small odd integer K and
+// the quotient x/6.  Same bits as the FP64 operation for every input: zeros
+// are returned directly, and subnormal, infinite or NaN operands and results
+// near the exponent limits take the FP64 instruction.
+//
+// K v: with v = +-M 2^(e-1075), M in [2^52, 2^53), the product M K has 54 to
+// 57 bits; it is rounded to 53 bits (ties to even) by adding 2^(s-1) - 1 plus
+// the lowest kept bit before the shift by s.  The rounded significand (up to
+// 2^53) is added onto the shifted exponent field, so a carry out of the
+// significand raises the exponent.
+template <unsigned K>
+__device__ __forceinline__ double mul_small(double v) {
+    static_assert(K % 2 == 1 && K >= 3 && K <= 15, "odd factor 3..15");
+    constexpr int S0 = K < 4 ? 1 : (K < 8 ? 2 : 3);   // M K in [2^(52+S0), 2^(54+S0))
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const unsigned e = (unsigned)(b >> 52) & 0x7ffu;
+    if (__builtin_expect(e > 2041u || (e == 0u && (b << 1) != 0ull), 0)) return (double)K * v;
+    const unsigned long long m = (b & 0x000fffffffffffffull) | 0x0010000000000000ull;
+    const unsigned long long P = m * K;
+    const unsigned s = S0 + (P >= (1ull << (53 + S0)) ? 1u : 0u);
+    const unsigned long long R = (P + ((1ull << (s - 1)) - 1ull) + ((P >> s) & 1ull)) >> s;
+    const unsigned long long out = (b & 0x8000000000000000ull) + ((unsigned long long)(e + s - 1u) << 52) + R;
+    return e == 0u ? v : __longlong_as_double((long long)out);
+}
+
+// x/6: with x = +-M 2^(e-1075), x/6 = +-(M 2^k / 3) 2^(e-1076-k), where k = 2
+// for M < 3 2^51 and k = 1 otherwise puts M 2^k / 3 in [2^52, 2^53).  A third
+// of an integer is never halfway between two integers, so the round-to-nearest
+// significand is floor((M 2^k + 1) / 3) and never reaches 2^53.
+__device__ __forceinline__ double div6(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned e = (unsigned)(b >> 52) & 0x7ffu;
+    if (__builtin_expect(e == 2047u || (e < 4u && (b << 1) != 0ull), 0)) return x / 6.0;
+    const unsigned long long m = (b & 0x000fffffffffffffull) | 0x0010000000000000ull;
+    const unsigned k = m < 0x0018000000000000ull ? 2u : 1u;
+    const unsigned long long Q = ((m << k) + 1ull) / 3ull;
+    const unsigned long long out = (b & 0x8000000000000000ull) + ((unsigned long long)(e - 2u - k) << 52) + Q;
+    return e == 0u ? x : __longlong_as_double((long long)out);
+}
+
 __device__ __forceinline__ void weno5(double eps, double v0, double v1, double v2, double v3, double v4,
                                       double& vm, double& vp) {
     const double c13 = 13.0 / 12.0;
-    const double r6 = 1.0 / 6.0;  // RN(1/6)
     // b0 = c13 (v0 - 2 v1 + v2)^2 + 1/4 (v0 - 4 v1 + 3 v2)^2, and likewise b1, b2
-    double b0 = fma2(0.25, sq(fma2(-4.0, v1, v0) + 3.0 * v2), c13 * sq(fma2(-2.0, v1, v0) + v2));
+    const double v2x3 = mul_small<3>(v2);
+    double b0 = fma2(0.25, sq(fma2(-4.0, v1, v0) + v2x3), c13 * sq(fma2(-2.0, v1, v0) + v2));
     double b1 = fma2(0.25, sq(v1 - v3), c13 * sq(fma2(-2.0, v2, v1) + v3));
-    double b2 = fma2(0.25, sq(fma2(-4.0, v3, 3.0 * v2) + v4), c13 * sq(fma2(-2.0, v3, v2) + v4));
+    double b2 = fma2(0.25, sq(fma2(-4.0, v3, v2x3) + v4), c13 * sq(fma2(-2.0, v3, v2) + v4));
     double s0 = sq(eps + b0), s1 = sq(eps + b1), s2 = sq(eps + b2);
     double y0 = rcp(s0), y1 = rcp(s1), y2 = rcp(s2);
 
@@ -134,9 +176,10 @@ __device__ __forceinline__ void weno5(double eps, double v0, double v1, double v
     double a2 = div_rcp(0.3, s2, y2);
     double s = a0 + a1 + a2;
     double ys = rcp(s);
-    double p0 = div_rcp(fma2(2.0, v0, -(7.0 * v1)) + 11.0 * v2, 6.0, r6);   // (2 v0 - 7 v1 + 11 v2)/6
-    double p1 = div_rcp(fma2(2.0, v3, -v1 + 5.0 * v2), 6.0, r6);             // (-v1 + 5 v2 + 2 v3)/6
-    double p2 = div_rcp(fma2(2.0, v2, 5.0 * v3) - v4, 6.0, r6);              // (2 v2 + 5 v3 - v4)/6
+    const double v2x5 = mul_small<5>(v2), v2x11 = mul_small<11>(v2);
+    double p0 = div6(fma2(2.0, v0, -mul_small<7>(v1)) + v2x11);     // (2 v0 - 7 v1 + 11 v2)/6
+    double p1 = div6(fma2(2.0, v3, -v1 + v2x5));                    // (-v1 + 5 v2 + 2 v3)/6
+    double p2 = div6(fma2(2.0, v2, mul_small<5>(v3)) - v4);         // (2 v2 + 5 v3 - v4)/6
     vm = div_rcp(a0, s, ys) * p0 + div_rcp(a1, s, ys) * p1 + div_rcp(a2, s, ys) * p2;
 
     a0 = div_rcp(0.3, s0, y0);
@@ -144,9 +187,9 @@ __device__ __forceinline__ void weno5(double eps, double v0, double v1, double v
     a2 = div_rcp(0.1, s2, y2);
     s = a0 + a1 + a2;
     ys = rcp(s);
-    p0 = div_rcp(fma2(2.0, v2, -v0 + 5.0 * v1), 6.0, r6);                    // (-v0 + 5 v1 + 2 v2)/6
-    p1 = div_rcp(fma2(2.0, v1, 5.0 * v2) - v3, 6.0, r6);                     // (2 v1 + 5 v2 - v3)/6
-    p2 = div_rcp(fma2(2.0, v4, 11.0 * v2 - 7.0 * v3), 6.0, r6);              // (11 v2 - 7 v3 + 2 v4)/6
+    p0 = div6(fma2(2.0, v2, -v0 + mul_small<5>(v1)));               // (-v0 + 5 v1 + 2 v2)/6
+    p1 = div6(fma2(2.0, v1, v2x5) - v3);                            // (2 v1 + 5 v2 - v3)/6
+    p2 = div6(fma2(2.0, v4, v2x11 - mul_small<7>(v3)));             // (11 v2 - 7 v3 + 2 v4)/6
     vp = div_rcp(a0, s, ys) * p0 + div_rcp(a1, s, ys) * p1 + div_rcp(a2, s, ys) * p2;
 }
 

@@ -839,38 +839,74 @@ sweep_kernel(const SweepArgs a) {
     }
 }
 
-// Launch one sweep: the valid (direction, mode) pairs are x FIRST, y MID
-// (3-D), and LAST_RK / LAST_RHS on the last direction.
-template <int NDIM, int DIR, int MODE, int FORM, int NF>
-cudaError_t launch_one(long long warps, const SweepArgs& a, cudaStream_t s) {
-    constexpr int T = sweep_threads(DIR);
-    const long long blocks = (warps * 32 + T - 1) / T;
-    if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    const bool nu = a.cw[0] || a.cw[1] || a.cw[2];
-    if constexpr (FORM != FORM_GATED && NF == 2) {
-        if (nu) {
-            sweep_kernel<NDIM, DIR, MODE, FORM, true, NF><<<(unsigned)blocks, T, 0, s>>>(a);
-            return cudaGetLastError();
+// Resident blocks of one sweep kernel on the whole device (occupancy x SMs),
+// looked up once per kernel.
+template <int NDIM, int DIR, int MODE, int FORM, bool NU, int NF>
+long long sweep_slots() {
+    static const long long slots = [] {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel<NDIM, DIR, MODE, FORM, NU, NF>,
+                                                          sweep_threads(DIR), 0) != cudaSuccess) {
+            cudaGetLastError();
+            per_sm = 1;
         }
-    }
-    if (nu) return cudaErrorInvalidValue;   // non-uniform grids: two fluids, non-gated forms
-    sweep_kernel<NDIM, DIR, MODE, FORM, false, NF><<<(unsigned)blocks, T, 0, s>>>(a);
+        return (long long)(sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+    }();
+    return slots;
+}
+
+// Cells per warp along the pencil.  Short segments duplicate halo work (two
+// extra reconstructions and one extra Riemann solve per segment), long ones
+// leave fewer blocks to spread over the SMs.  Start from the longest power of
+// two up to 32 that still gives 152 x 256 threads (4 where none does), then
+// double while the grid still fills the resident blocks MFC_MIN_WAVES times
+// over, up to MFC_MAX_SEG.
+inline int pick_seg(int dir, const int* n, int threads, long long slots) {
+    int seg = 32;
+    while (seg > 4 && sweep_warps(dir, n, seg) * 32 < 152LL * 256) seg >>= 1;
+    while (seg < MFC_MAX_SEG &&
+           (sweep_warps(dir, n, 2 * seg) * 32 + threads - 1) / threads >= MFC_MIN_WAVES * slots)
+        seg <<= 1;
+    return seg;
+}
+
+template <int NDIM, int DIR, int MODE, int FORM, bool NU, int NF>
+cudaError_t launch_kernel(const SweepArgs& a0, cudaStream_t s) {
+    constexpr int T = sweep_threads(DIR);
+    SweepArgs a = a0;
+    a.seg = pick_seg(DIR, a.n, T, sweep_slots<NDIM, DIR, MODE, FORM, NU, NF>());
+    const long long blocks = (sweep_warps(DIR, a.n, a.seg) * 32 + T - 1) / T;
+    if (blocks <= 0 || a.dry) return cudaSuccess;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    sweep_kernel<NDIM, DIR, MODE, FORM, NU, NF><<<(unsigned)blocks, T, 0, s>>>(a);
     return cudaGetLastError();
 }
 
+template <int NDIM, int DIR, int MODE, int FORM, int NF>
+cudaError_t launch_one(const SweepArgs& a, cudaStream_t s) {
+    const bool nu = a.cw[0] || a.cw[1] || a.cw[2];
+    if constexpr (FORM != FORM_GATED && NF == 2) {
+        if (nu) return launch_kernel<NDIM, DIR, MODE, FORM, true, NF>(a, s);
+    }
+    if (nu) return cudaErrorInvalidValue;   // non-uniform grids: two fluids, non-gated forms
+    return launch_kernel<NDIM, DIR, MODE, FORM, false, NF>(a, s);
+}
+
+// Launch one sweep: the valid (direction, mode) pairs are x FIRST, y MID
+// (3-D), and LAST_RK / LAST_RHS on the last direction.
 template <int NDIM, int FORM, int NF>
 cudaError_t launch_sweep_t(int dir, int mode, const SweepArgs& a, cudaStream_t s) {
-    const long long warps = sweep_warps(dir, a.n, a.seg);
-    if (warps <= 0) return cudaSuccess;
     constexpr int LAST = NDIM - 1;
     if (dir == 0 && mode == SW_FIRST && NDIM > 1) {
-        if constexpr (NDIM > 1) return launch_one<NDIM, 0, SW_FIRST, FORM, NF>(warps, a, s);
+        if constexpr (NDIM > 1) return launch_one<NDIM, 0, SW_FIRST, FORM, NF>(a, s);
     } else if (dir == 1 && mode == SW_MID && NDIM == 3) {
-        if constexpr (NDIM == 3) return launch_one<NDIM, 1, SW_MID, FORM, NF>(warps, a, s);
+        if constexpr (NDIM == 3) return launch_one<NDIM, 1, SW_MID, FORM, NF>(a, s);
     } else if (dir == LAST && mode == SW_LAST_RK) {
-        return launch_one<NDIM, LAST, SW_LAST_RK, FORM, NF>(warps, a, s);
+        return launch_one<NDIM, LAST, SW_LAST_RK, FORM, NF>(a, s);
     } else if (dir == LAST && mode == SW_LAST_RHS) {
-        return launch_one<NDIM, LAST, SW_LAST_RHS, FORM, NF>(warps, a, s);
+        return launch_one<NDIM, LAST, SW_LAST_RHS, FORM, NF>(a, s);
     }
     return cudaErrorInvalidValue;
 }

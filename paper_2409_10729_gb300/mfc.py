@@ -72,6 +72,8 @@ def lib() -> ctypes.CDLL:
             "mfc_alu_peak": ([ip, dp], ip),
             "mfc_selfcheck_conversions": ([ctypes.c_longlong, ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_longlong)],
                                           ip),
+            "mfc_selfcheck_exact_ops": ([ctypes.c_longlong, ctypes.c_ulonglong, ctypes.POINTER(ctypes.c_longlong)],
+                                        ip),
             "mfc_rhs_noalloc": ([ctypes.POINTER(MfcParams), vp, vp, vp], ip),
             "mfc_set_mlp_weights": ([vp, ctypes.POINTER(ctypes.c_float), ip], ip),
             "mfc_gate_stats": ([vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),

@@ -333,6 +333,17 @@ def test_integer_conversions_match_hardware():
     assert bad.value == 0
 
 
+def test_integer_weno_operations_match_hardware():
+    """The FP64 form's integer-pipe products K v (K = 3, 5, 7, 11) and
+    quotients x/6 return the FP64 instructions' bits on 64M patterns, zeros,
+    subnormals, infinities, NaNs and the ends of the exponent range among them."""
+    import ctypes
+    from paper_2409_10729_gb300 import mfc
+    bad = ctypes.c_longlong(-1)
+    assert mfc.lib().mfc_selfcheck_exact_ops(1 << 26, 1729, ctypes.byref(bad)) == 0
+    assert bad.value == 0
+
+
 # ---------------------------------------------------------------- WENO3 ----
 # The third-order reconstruction option (Sec. II-B; weno_order = 3) to the
 # same bar: bit-identical in the FP64 form, 1e-12 in the reorganised one.
