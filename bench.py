@@ -160,6 +160,16 @@ def read_traffic(kernel: str):
     return None
 
 
+def pipe_busy(form, name):
+    """Busy fraction of the FP64 (FP64 forms) or FP32 FMA (FP32 forms) pipe of
+    the dominant kernel, from the committed ncu summary of the same kernel
+    source (None if the kernels changed since)."""
+    pipe = "fp64" if form.startswith("fp64") else "fma"
+    v = read_traffic(f"{form}:{name}:pipe_{pipe}")
+    return None if v is None else {"pipe": pipe, "frac": v, "source": "ncu sm__inst_executed_pipe_" + pipe +
+                                   " at 160^3, profiles/traffic.txt"}
+
+
 def stretched(p):
     """The same case on a grid refined with a hyperbolic tangent about the
     domain centre in every direction (Sec. III-A): cells there half as wide."""
@@ -231,6 +241,7 @@ def roofline_for(form, res, peak_alu, alu_src, hbm_peak, hbm_src):
             "traffic": read_traffic(f"{form}:{name}") if form == base else None, "share_of_step": round(share, 3),
             "avg_launch_ms": round(total_ms / count, 4),
             "algorithmic_flops_per_cell": flops,
+            "pipe_busy_ncu": pipe_busy(form, name) if form == base else None,
             "hbm": {"achieved_gbs": round(ALG_BYTES[base] / res["grind"], 1), "peak": hbm_peak,
                     "frac": round(ALG_BYTES[base] / res["grind"] / hbm_peak, 4), "peak_source": hbm_src}}
 
