@@ -11,10 +11,10 @@
 //
 // Thread mapping.  A warp owns 32 adjacent pencils along d and a segment of
 // `seg` cells of each.  For d = y, z the 32 lanes run along x, so every load
-// is one coalesced row.  For d = x the lanes run along y; their cells are
-// staged through shared memory in chunks of 32 bytes along x per row (one
-// full DRAM sector), loaded cooperatively by the warp so that every global
-// load touches whole sectors.  Each thread slides a five-cell window of
+// is one coalesced row.  For d = x the lanes run along y: each lane loads
+// its own row, whose 32-byte sector stays in L1 for the lane's next cells,
+// and the RHS goes out through a shared-memory tile as whole sectors.  Each
+// thread slides a five-cell window of
 // primitives along its pencil in registers: per cell it takes one new cell,
 // runs WENO once (both faces) and HLLC once (the face between the previous
 // cell and this one), so no face is computed twice except at the two ends of
@@ -182,30 +182,14 @@ __device__ __forceinline__ void cell_geometry(const SweepArgs& a, int i, int ia,
     }
 }
 
-// Shared-memory staging of the x-direction sweep: per warp, per loaded
-// field, 32 rows x CH cells (CH * sizeof(R) = 32 bytes), padded by one
-// element per row so that the 32 lanes read 32 different banks.
+// Output tile of the x-direction sweep: per warp, per field, 32 rows x CH
+// cells (CH * sizeof(R) = 32 bytes, one DRAM sector), padded by one element
+// per row so that the 32 lanes write 32 different banks.
 template <typename R>
 struct XStage {
-    static constexpr int CH = 32 / sizeof(R);   // cells per staged chunk along x (one 32-byte sector)
-    static constexpr int PITCH = CH + 1;        // padded row pitch (conflict-free reads)
+    static constexpr int CH = 32 / sizeof(R);   // cells per row and sector along x
+    static constexpr int PITCH = CH + 1;        // padded row pitch (conflict-free accesses)
 };
-
-// Asynchronous 4- or 8-byte global -> shared copies (sm_80+ cp.async), one
-// commit group per staged chunk.
-template <typename R>
-__device__ __forceinline__ void cp_async_elem(R* smem, const R* gmem) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    if constexpr (sizeof(R) == 4)
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
-    else
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
-
-__device__ __forceinline__ int floor_div(int j, int d) { return j >= 0 ? j / d : -((-j + d - 1) / d); }
 
 template <int FORM>
 using FormReal = typename std::conditional<FORM == FORM_MIXED || FORM == FORM_GATED, float, double>::type;
@@ -403,8 +387,8 @@ __device__ __forceinline__ bool face_ok(const EosR<float, 2>& e, const float* w)
 }
 
 // Minimum resident blocks for the register allocator, in blocks of the
-// sweep's own size (x sweeps run one-warp blocks so that the warp's two input
-// chunk buffers and its output tile fit the 48 KB of static shared memory).
+// sweep's own size (x sweeps run one-warp blocks, each with its own output
+// tile in static shared memory).
 template <int FORM, int MODE, int DIR, int NF = 2>
 constexpr int sweep_min_blocks() {
     if (NF > 2) return 1;   // more fields per cell: no register cap (the two-fluid caps spill)
@@ -431,8 +415,6 @@ sweep_kernel(const SweepArgs a) {
     constexpr bool MIXED = FORM == FORM_MIXED || FORM == FORM_GATED;
     constexpr int CH = XStage<R>::CH, PITCH = XStage<R>::PITCH;
     constexpr int WARPS = sweep_threads(DIR) / 32;
-    constexpr int STAGE = NL * 32 * PITCH;   // one chunk buffer of one warp
-    __shared__ R stage[DIR == 0 ? WARPS * 2 * STAGE : 1];
     // x sweep writing the accumulator: the warp collects each sector's worth
     // of cells (CH along x) of its 32 rows here and stores whole sectors
     constexpr bool OSTAGE_ON = DIR == 0 && MODE == SW_FIRST;
@@ -476,51 +458,14 @@ sweep_kernel(const SweepArgs a) {
     const R* __restrict__ qin = static_cast<const R*>(a.qin);
 
     // Values of loaded cell k (index s0 - 3 + k along the pencil) -> v[].
-    // Along x the warp stages chunks of CH cells, aligned to multiples of CH,
-    // of its 32 rows through shared memory with cp.async, double-buffered:
-    // chunk m + 1 is requested when the pencil enters chunk m, so its copy
-    // runs under the CH cells of work on chunk m.  Calls must come in order
-    // of k (all lanes together).
-    R* st = stage + (threadIdx.x >> 5) * (2 * STAGE);
-    const int last_chunk = DIR == 0 ? floor_div(s1 + 2, CH) : 0;
-    auto stage_chunk = [&](int m) {
-        R* buf = st + (m & 1) * STAGE;
-        const int t = lane % CH;
-        const int xg = bc_index(m * CH + t, ns, a.periodic);
-#pragma unroll
-        for (int i = 0; i < CH; ++i) {
-            const int r = lane / CH + (32 / CH) * i;
-            const int row = min(chunk * 32 + r, na - 1);
-            const long long c = (long long)row * sa + (long long)b * sb + xg;
-#pragma unroll
-            for (int f = 0; f < NL; ++f) cp_async_elem(buf + (f * 32 + r) * PITCH + t, qin + LS::field(f) * nc + c);
-        }
-        cp_async_commit();
-    };
+    // Along y and z the warp's 32 loads form one coalesced row per field;
+    // along x each lane reads its own row, and the 32-byte sector it brings
+    // into L1 serves the lane's next CH - 1 cells.
     auto fetch = [&](int k, R* v) {
         const int j = s0 - 3 + k;
-        if constexpr (DIR != 0) {
-            const long long c = base + (long long)bc_index(j, ns, a.periodic) * ss;
+        const long long c = base + (long long)bc_index(j, ns, a.periodic) * ss;
 #pragma unroll
-            for (int f = 0; f < NL; ++f) v[f] = __ldg(qin + LS::field(f) * nc + c);
-        } else {
-            const int m = floor_div(j, CH);
-            const int slot = j - m * CH;
-            if (k == 0 || slot == 0) {
-                if (k == 0) stage_chunk(m);
-                __syncwarp();   // every lane is done with chunk m - 1 (buffer of m + 1)
-                if (m + 1 <= last_chunk) {
-                    stage_chunk(m + 1);
-                    cp_async_wait<1>();   // chunk m has landed
-                } else {
-                    cp_async_wait<0>();
-                }
-                __syncwarp();
-            }
-            const R* buf = st + (m & 1) * STAGE;
-#pragma unroll
-            for (int f = 0; f < NL; ++f) v[f] = buf[(f * 32 + lane) * PITCH + slot];
-        }
+        for (int f = 0; f < NL; ++f) v[f] = __ldg(qin + LS::field(f) * nc + c);
     };
 
     constexpr bool PREFETCH = MFC_PREFETCH != 0;
