@@ -41,7 +41,6 @@ struct mfc_ctx {
     void* sa;         // stage 1 output (FP64, or FP32 cons + p)
     void* sb;         // stage 2 output
     float* s0;        // mixed form: FP32 copy of q^n with p
-    float* dlt;       // FP32 forms: RK increment of the current stage
     void* acc;        // RHS accumulator
     double* tmp64;    // mixed form: FP64 RHS output staging (lazy)
     DevCtrl* ctrl;    // device
@@ -101,7 +100,7 @@ static int state_fields(const mfc_ctx* c) { return fp32_state(c) ? c->neq + 1 : 
 
 static void free_all(mfc_ctx* c) {
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
-    void* bufs[] = {c->qn, c->sa, c->sb, c->s0, c->dlt, c->acc, c->tmp64, c->ctrl, c->gate_w};
+    void* bufs[] = {c->qn, c->sa, c->sb, c->s0, c->acc, c->tmp64, c->ctrl, c->gate_w};
     for (void* b : bufs)
         if (b) cudaFree(b);
     for (int d = 0; d < 3; ++d) {
@@ -158,8 +157,7 @@ extern "C" int mfc_create(const mfc_params* params, void* cuda_stream, mfc_ctx**
               cudaMalloc((void**)&ctx->ctrl, sizeof(DevCtrl)) == cudaSuccess &&
               cudaMallocHost((void**)&ctx->ctrl_h, sizeof(DevCtrl)) == cudaSuccess;
     if (ok && fp32_state(ctx))
-        ok = cudaMalloc((void**)&ctx->s0, nc * sfield * sizeof(float)) == cudaSuccess &&
-             cudaMalloc((void**)&ctx->dlt, nc * ctx->neq * sizeof(float)) == cudaSuccess;
+        ok = cudaMalloc((void**)&ctx->s0, nc * sfield * sizeof(float)) == cudaSuccess;
     if (ok && ctx->form == FORM_GATED)
         ok = cudaMalloc((void**)&ctx->gate_w, kGateParams * sizeof(float)) == cudaSuccess;
     for (int i = 0; ok && i <= kMaxTimedLaunches; ++i) ok = cudaEventCreate(&ctx->ev[i]) == cudaSuccess;
@@ -204,7 +202,6 @@ static SweepArgs base_args(mfc_ctx* ctx) {
     a.order = ctx->p.weno_order == 3 ? 3 : 5;
     a.ctrl = ctx->ctrl;
     a.acc = ctx->acc;
-    a.dlt = ctx->dlt;
     a.qn = ctx->qn;
     a.gate_w = ctx->gate_w;
     for (int d = 0; d < 3; ++d) {

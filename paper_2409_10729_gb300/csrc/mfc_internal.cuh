@@ -76,7 +76,6 @@ struct SweepArgs {
     const double* qn;     // RK base state q^n (FP64)
     void* qout;           // stage output (FP64 or FP32), or FP64 RHS output
     void* qout2;          // mixed form, stage 3: FP32 copy of q^{n+1} with p
-    float* dlt;           // FP32 forms: RK increment q^(k) - q^n (read at stages 2-3, written at 1-2)
     int n[3];
     long long ncell;
     double inv_dx[3];     // n/(hi - lo) per direction (reformulated forms)

@@ -484,9 +484,9 @@ sweep_kernel(const SweepArgs a) {
     }
     double dt = 0.0;
     if (MODE == SW_LAST_RK) dt = a.ctrl->dt;
-    // SSP-RK3 stage weight b of q^(k+1) = (1 - b) q^n + b (q^(k) + dt L), stages 2 and 3
-    const double rk_b = a.stage == 2 ? 0.25 : (2.0 / 3.0);
-    const float bdt32 = float(a.stage == 1 ? dt : rk_b * dt), rk_b32 = float(rk_b);
+    // SSP-RK3 stage coefficients q^(k+1) = rk_a q^n + rk_b (q^(k) + dt L)
+    const double rk_a = a.stage == 2 ? 0.75 : (1.0 / 3.0), rk_b = a.stage == 2 ? 0.25 : (2.0 / 3.0);
+    const float bdt32 = float(a.stage == 1 ? dt : rk_b * dt);
 
     R W[5][NEQ];
 #pragma unroll
@@ -511,7 +511,7 @@ sweep_kernel(const SweepArgs a) {
         if (PREFETCH && j < s1) fetch(j + 3 - (s0 - 3), vnext);
         // the FP32 forms also issue the stage-update operands of the cell
         // this iteration completes (cell j - 1) here, ahead of the stencil work
-        R accp[NEQ], dkp[NEQ];
+        R accp[NEQ], qkp[NEQ];
         double qnp[NEQ];
         if constexpr (EPI_PREFETCH) {
             if (j > s0) {
@@ -526,7 +526,7 @@ sweep_kernel(const SweepArgs a) {
                     for (int f = 0; f < NEQ; ++f) qnp[f] = __ldg(a.qn + f * nc + c);
                     if (a.stage != 1) {
 #pragma unroll
-                        for (int f = 0; f < NEQ; ++f) dkp[f] = a.dlt[f * nc + c];
+                        for (int f = 0; f < NEQ; ++f) qkp[f] = __ldg(qin + f * nc + c);
                     }
                 }
             }
@@ -648,15 +648,15 @@ sweep_kernel(const SweepArgs a) {
                         R tot = NDIM > 1 ? (EPI_PREFETCH ? accp[f] : acc[f * nc + c]) + L[f] : L[f];
                         double qn = EPI_PREFETCH ? qnp[f] : a.qn[f * nc + c];
                         if constexpr (MIXED) {
-                            // SSP-RK3 in increment form, q^(k+1) = q^n + D_(k+1) with
-                            // D_1 = dt L(q^n), D_2 = (D_1 + dt L(q^(1)))/4 and
-                            // D_3 = 2 (D_2 + dt L(q^(2)))/3: the increments are FP32
-                            // (as L is), their sum with q^n is FP64, and the FP32
-                            // rounding of the stage states never enters q^(n+1)
-                            float d = bdt32 * tot;
-                            if (a.stage != 1) d = fmaf(rk_b32, EPI_PREFETCH ? dkp[f] : a.dlt[f * nc + c], d);
-                            if (a.stage != 3) a.dlt[f * nc + c] = d;
-                            qnew[f] = qn + f2d_bits(d);
+                            // q^(k+1) = a q^n + b q^(k) + (b dt) L, accumulated in FP64
+                            // from the FP32 increment (b dt) L (L itself is FP32)
+                            const double inc = f2d_bits(bdt32 * tot);
+                            if (a.stage == 1) {
+                                qnew[f] = qn + inc;
+                            } else {
+                                const double qkd = f2d_bits(EPI_PREFETCH ? qkp[f] : qin[f * nc + c]);
+                                qnew[f] = __fma_rn(rk_a, qn, __fma_rn(rk_b, qkd, inc));
+                            }
                         } else {
                             double dL = dt * double(tot);
                             if (a.stage == 1) {

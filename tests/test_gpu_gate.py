@@ -238,11 +238,11 @@ def test_training_on_gpu_lowers_the_loss():
     from paper_2409_10729_gb300 import train_gate as T
     rng = np.random.default_rng(0)
     X, Y, _ = T.collect([100], 128, 64, 100, 25, 2048, 0.1, rng)
-    theta, hist = T.train(X, Y, epochs=48, batch=1024, lr=3e-3, pos_weight=1.0, seed=1)
-    assert hist[-1] < 0.7 * hist[0], hist
+    theta, hist = T.train(X, Y, epochs=24, batch=1024, lr=3e-3, pos_weight=1.0, seed=1)
+    assert hist[-1] < 0.7 * hist[0]
     z, y = T.evaluate(theta, X, Y)
     acc = float(((z > 0) == (y > 0.5)).float().mean())
-    assert acc > 0.85, (acc, hist[0], hist[-1])
+    assert acc > 0.85
 
 
 def test_trained_gate_gain():
