@@ -40,7 +40,7 @@ UNIT = "ns/(cell*eq*RHS)"
 CFL = 0.4
 
 # Algorithmic work per cell and direction of one sweep, counted from the
-# oracle's formulas (every +, -, *, /, sqrt counts 1; see DESIGN.md):
+# oracle's formulas (every +, -, *, /, sqrt counts 1):
 # cons->prim 22, WENO5-JS 107 per field, HLLC 122 per face, divergence 18.
 FLOPS_CELL_DIR_3D = 22 + 107 * 7 + 122 + 18          # 911
 # with the third-order option: WENO3-JS 38 per field (beta 4, two faces x 17)

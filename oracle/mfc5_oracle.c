@@ -10,10 +10,15 @@
  *   - finite-volume semi-discrete: Sec. II-B, Eq. (eqn:discretization) and the
  *                                  cell-integrated form that follows it
  *   - WENO + HLLC:                 Sec. II-B, last paragraph
- * Readings of points the paper leaves open (mixture rules, sound speed, WENO
- * epsilon, wave-speed estimates, the discrete h(q) div(u) term, the time
- * integrator, the CFL rule, boundary ghosts) are listed in the design doc and are
- * followed here verbatim.
+ * Points the paper leaves open are read as follows, and each function below
+ * states the reading it uses: mixture rules Gamma = sum alpha_i/(gamma_i-1),
+ * Pi = sum alpha_i gamma_i pi_i/(gamma_i-1); sound speed
+ * c^2 = ((Gamma+1)p + Pi)/(Gamma rho); WENO epsilon 1e-6 (absolute, exponent
+ * 2); Davis wave-speed estimates; the alpha_1 row's h(q) div(u) term as
+ * +alpha_1,i (u_f,i+1/2 - u_f,i-1/2)/dx with u_f the HLLC region velocity;
+ * Shu-Osher SSP-RK3 with dt fixed per step from q^n; dt = CFL / max over
+ * cells of sum_d (|u_d| + c)/dx_d; transmissive ghosts copy the nearest
+ * interior cell, periodic ghosts wrap.
  *
  * Only tests/, the smoke check and bench.py's CPU-baseline leg may load this
  * file's shared library.  It shares no code with the CUDA path.
