@@ -40,13 +40,31 @@ UNIT = "ns/(cell*eq*RHS)"
 CFL = 0.4
 
 # Algorithmic work per cell and direction of one sweep, counted from the
-# oracle's formulas (every +, -, *, /, sqrt counts 1):
-# cons->prim 22, WENO5-JS 107 per field, HLLC 122 per face, divergence 18.
-FLOPS_CELL_DIR_3D = 22 + 107 * 7 + 122 + 18          # 911
-# with the third-order option: WENO3-JS 38 per field (beta 4, two faces x 17)
-FLOPS_CELL_DIR_3D_WENO3 = 22 + 38 * 7 + 122 + 18     # 428
-FLOPS_RK_CELL = 28                                     # stage update, mean over the 3 stages
-FLOPS_WAVESPEED_CELL = 45                              # once per step, in the last stage
+# oracle's formulas (every +, -, *, /, sqrt and Davis min/max counts 1), for
+# nf fluids in ndim dimensions (neq = 2 nf + ndim):
+#   cons->prim   6 nf + 3 ndim + 1        (two fluids, 3-D: 22)
+#   WENO5-JS     107 per field (beta 33, two faces x 37); WENO3-JS 38
+#   HLLC         19 nf + 12 ndim + 48 per face, star region (122)
+#   divergence   2 neq + 4 (nf - 1) with the volume-fraction terms (18)
+# The last sweep adds the accumulation (neq), the stage update (4 per field,
+# mean over the three stages) and a third of the wave speed (cons->prim + 23,
+# once per step).
+WENO_FLOPS = {5: 107, 3: 38}
+
+
+def flops_cell_dir(nf=2, ndim=3, order=5):
+    neq = 2 * nf + ndim
+    return (6 * nf + 3 * ndim + 1) + WENO_FLOPS[order] * neq + (19 * nf + 12 * ndim + 48) + \
+        (2 * neq + 4 * (nf - 1))
+
+
+def flops_last_sweep_extra(nf=2, ndim=3):
+    neq = 2 * nf + ndim
+    return neq + 4 * neq + ((6 * nf + 3 * ndim + 1) + 23) / 3.0
+
+
+FLOPS_CELL_DIR_3D = flops_cell_dir()                   # 911
+FLOPS_CELL_DIR_3D_WENO3 = flops_cell_dir(order=3)      # 428
 # Algorithmic bytes per cell, equation and RHS: stage 1 reads q^n and writes
 # q^(1); stages 2-3 read q^(k) and q^n and write q^(k+1): 8/3 state arrays.
 ALG_BYTES = {"fp64": 8.0 / 3.0 * 8.0, "fp64_fast": 8.0 / 3.0 * 8.0, "mixed": (12.0 + 16.0 + 20.0) / 3.0,
@@ -229,11 +247,12 @@ def roofline_for(form, res, peak_alu, alu_src, hbm_peak, hbm_src):
     total_ms, count = kt[name]
     avg_s = total_ms / count * 1e-3
     ncell = res["ncell"]
-    flops = FLOPS_CELL_DIR_3D_WENO3 if form.endswith("_weno3") else FLOPS_CELL_DIR_3D
+    nf, neq = (res["neq"] - 3) // 2, res["neq"]
+    flops = flops_cell_dir(nf, 3, 3 if form.endswith("_weno3") else 5)
     if name == "sweep_y":
-        flops += 7
+        flops += neq
     if name == "sweep_z":
-        flops += 7 + FLOPS_RK_CELL + FLOPS_WAVESPEED_CELL / 3.0
+        flops += flops_last_sweep_extra(nf, 3)
     achieved = flops * ncell / avg_s / 1e12
     share = total_ms / sum(v[0] for v in kt.values())
     return {"bound": "alu", "kernel": name, "achieved": round(achieved, 4), "peak": round(peak_alu, 3),
