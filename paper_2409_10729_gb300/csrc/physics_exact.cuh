@@ -160,14 +160,25 @@ __device__ __forceinline__ double div6(double x) {
     return e == 0u ? x : __longlong_as_double((long long)out);
 }
 
-__device__ __forceinline__ void weno5(double eps, double v0, double v1, double v2, double v3, double v4,
-                                      double& vm, double& vp) {
+// The curvature term of a Jiang-Shu smoothness indicator on the three cells
+// a, b, c: 13/12 (a - 2 b + c)^2.  The stencil {i-1, i, i+1} gives beta_1 of
+// cell i, beta_2 of cell i-1 and beta_0 of cell i+1 the same term, formed
+// from the same three values in the same order -- the same bits -- so a sweep
+// that slides along a pencil can form it once per cell and pass it on.
+__device__ __forceinline__ double curv(double a, double b, double c) {
     const double c13 = 13.0 / 12.0;
+    return c13 * sq(fma2(-2.0, b, a) + c);
+}
+
+// WENO5-JS given the curvature terms t0 = curv(v0, v1, v2), t1 = curv(v1, v2,
+// v3) and t2 = curv(v2, v3, v4) of the three smoothness indicators.
+__device__ __forceinline__ void weno5_t(double eps, double v0, double v1, double v2, double v3, double v4,
+                                        double t0, double t1, double t2, double& vm, double& vp) {
     // b0 = c13 (v0 - 2 v1 + v2)^2 + 1/4 (v0 - 4 v1 + 3 v2)^2, and likewise b1, b2
     const double v2x3 = mul_small<3>(v2);
-    double b0 = fma2(0.25, sq(fma2(-4.0, v1, v0) + v2x3), c13 * sq(fma2(-2.0, v1, v0) + v2));
-    double b1 = fma2(0.25, sq(v1 - v3), c13 * sq(fma2(-2.0, v2, v1) + v3));
-    double b2 = fma2(0.25, sq(fma2(-4.0, v3, v2x3) + v4), c13 * sq(fma2(-2.0, v3, v2) + v4));
+    double b0 = fma2(0.25, sq(fma2(-4.0, v1, v0) + v2x3), t0);
+    double b1 = fma2(0.25, sq(v1 - v3), t1);
+    double b2 = fma2(0.25, sq(fma2(-4.0, v3, v2x3) + v4), t2);
     double s0 = sq(eps + b0), s1 = sq(eps + b1), s2 = sq(eps + b2);
     double y0 = rcp(s0), y1 = rcp(s1), y2 = rcp(s2);
 
@@ -191,6 +202,11 @@ __device__ __forceinline__ void weno5(double eps, double v0, double v1, double v
     p1 = div6(fma2(2.0, v1, v2x5) - v3);                            // (2 v1 + 5 v2 - v3)/6
     p2 = div6(fma2(2.0, v4, v2x11 - mul_small<7>(v3)));             // (11 v2 - 7 v3 + 2 v4)/6
     vp = div_rcp(a0, s, ys) * p0 + div_rcp(a1, s, ys) * p1 + div_rcp(a2, s, ys) * p2;
+}
+
+__device__ __forceinline__ void weno5(double eps, double v0, double v1, double v2, double v3, double v4,
+                                      double& vm, double& vp) {
+    weno5_t(eps, v0, v1, v2, v3, v4, curv(v0, v1, v2), curv(v1, v2, v3), curv(v2, v3, v4), vm, vp);
 }
 
 // WENO3-JS in the reference order: v1..v3 = v_{i-1}..v_{i+1}; weights

@@ -497,6 +497,18 @@ sweep_kernel(const SweepArgs a) {
         else to_prim<NDIM, NF>(er, v, W[k]);
         bad |= !(mix_rho<NF>(W[k]) > R(0));
     }
+    // FP64 reference-order form: the smoothness indicators' curvature terms
+    // of the window's stencils {i-2..i}, {i-1..i+1} (cell i = window centre),
+    // carried along the pencil so that each is formed once (exact::curv)
+    constexpr bool TCARRY = EXACT && !GATED && !NU && NF == 2;
+    double Tm[TCARRY ? NEQ : 1], T0[TCARRY ? NEQ : 1];
+    if constexpr (TCARRY) {
+#pragma unroll
+        for (int f = 0; f < NEQ; ++f) {
+            Tm[f] = exact::curv(W[0][f], W[1][f], W[2][f]);
+            T0[f] = exact::curv(W[1][f], W[2][f], W[3][f]);
+        }
+    }
     R vmPrev[NEQ], Fprev[NEQ];
     R ufPrev = R(0), alphaCell[NA];
 #pragma unroll
@@ -576,10 +588,17 @@ sweep_kernel(const SweepArgs a) {
             } else if (GATED || a.order == 5) {
 #pragma unroll
                 for (int f = 0; f < NEQ; ++f) {
-                    if constexpr (EXACT)
+                    if constexpr (TCARRY) {
+                        const double Tp = exact::curv(W[2][f], W[3][f], W[4][f]);
+                        exact::weno5_t(a.eps, W[0][f], W[1][f], W[2][f], W[3][f], W[4][f], Tm[f], T0[f], Tp,
+                                       vm[f], vp[f]);
+                        Tm[f] = T0[f];
+                        T0[f] = Tp;
+                    } else if constexpr (EXACT) {
                         exact::weno5(a.eps, W[0][f], W[1][f], W[2][f], W[3][f], W[4][f], vm[f], vp[f]);
-                    else
+                    } else {
                         weno5(W[0][f], W[1][f], W[2][f], W[3][f], W[4][f], eps, vm[f], vp[f]);
+                    }
                 }
             } else {   // WENO3 (uniform over the launch): cells i-1 .. i+1 of the window
 #pragma unroll
