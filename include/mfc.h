@@ -79,7 +79,8 @@ typedef struct {
 } mfc_params;
 
 /* Creates a context: validates params (MFC_EINVAL), allocates the state,
- * stage and accumulator buffers on the current CUDA device (MFC_ENOMEM) and
+ * stage and accumulator buffers on the current CUDA device (MFC_ENOMEM; also
+ * returned, before any device call, for more than 2^36 cells) and
  * binds the CUDA stream `cuda_stream` (a cudaStream_t; NULL = legacy default
  * stream).  *out receives the context, or NULL on failure. */
 int mfc_create(const mfc_params* params, void* cuda_stream, mfc_ctx** out);

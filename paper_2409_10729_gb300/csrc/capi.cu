@@ -71,6 +71,12 @@ struct mfc_ctx {
         }                                          \
     } while (0)
 
+// Largest cell count a context accepts: 2^36 cells, beyond what any device
+// holds in any form (the FP64 form alone needs 4 state arrays of neq doubles
+// per cell), and small enough that every byte count and index of the library
+// fits in 64 bits.
+static const long long kMaxCells = 1LL << 36;
+
 static int validate(const mfc_params* p) {
     if (!p || p->ndim < 1 || p->ndim > 3) return MFC_EINVAL;
     for (int d = 0; d < p->ndim; ++d) {
@@ -78,6 +84,12 @@ static int validate(const mfc_params* p) {
         if (!(p->hi[d] > p->lo[d]) || !isfinite(p->hi[d] - p->lo[d])) return MFC_EINVAL;
         int b0 = p->bc[d][0], b1 = p->bc[d][1];
         if (b0 < 0 || b0 > 1 || b1 < 0 || b1 > 1 || b0 != b1) return MFC_EINVAL;
+    }
+    // cell count, checked step by step so that it cannot overflow
+    long long ncell = 1;
+    for (int d = 0; d < p->ndim; ++d) {
+        if (ncell > kMaxCells / p->n[d]) return MFC_ENOMEM;
+        ncell *= p->n[d];
     }
     if (p->nfluids != 0 && (p->nfluids < 2 || p->nfluids > MFC_MAX_FLUIDS)) return MFC_EINVAL;
     const int nf = params_nfluids(p->nfluids);

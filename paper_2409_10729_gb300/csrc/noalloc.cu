@@ -84,14 +84,17 @@ extern "C" int mfc_rhs_noalloc(const mfc_params* params, const double* q, double
     if (!q || !rhs) return MFC_EINVAL;
     int st = check_params(params);
     if (st) return st;
+    const int ndim = params->ndim, neq = 2 * params_nfluids(params->nfluids) + ndim;
+    // neq * ncell against the scratch, checked per factor so that no product
+    // can overflow (each n[d] >= 1)
+    const long long cap = ((long long)MFC_NOALLOC_MAX_DOUBLES - kCtrlDoubles) / neq;
     int n[3];
     long long ncell = 1;
     for (int d = 0; d < 3; ++d) {
-        n[d] = d < params->ndim ? params->n[d] : 1;
+        n[d] = d < ndim ? params->n[d] : 1;
+        if (ncell > cap / n[d]) return MFC_ETOOBIG;
         ncell *= n[d];
     }
-    const int ndim = params->ndim, neq = 2 * params_nfluids(params->nfluids) + ndim;
-    if ((long long)neq * ncell > (long long)MFC_NOALLOC_MAX_DOUBLES - kCtrlDoubles) return MFC_ETOOBIG;
 
     double* scratch = nullptr;
     st = scratch_for_current_device(&scratch);

@@ -92,3 +92,24 @@ def test_null_arguments_are_rejected(lib):
     assert lib.mfc_rhs(None, None, 0) == mfc.MFC_EINVAL
     assert lib.mfc_step_rk3(None, 0.4, 1, None) == mfc.MFC_EINVAL
     assert mfc.strerror(mfc.MFC_ENONPHYSICAL).startswith("non-physical")
+
+
+@pytest.mark.parametrize("n", [[2 ** 21, 2 ** 21, 2 ** 22],        # 2^64 cells: wraps to 0 in 64 bits
+                               [2 ** 31 - 1] * 3, [4096, 4096, 4097]])
+def test_create_rejects_cell_counts_no_device_can_hold(lib, n):
+    """More than 2^36 cells is refused with MFC_ENOMEM before any device call,
+    including counts whose 64-bit product would wrap."""
+    handle = ctypes.c_void_p()
+    st = lib.mfc_create(ctypes.byref(mfc.make_params(_params(n=n), "fp64")), None, ctypes.byref(handle))
+    assert st == mfc.MFC_ENOMEM
+    assert not handle.value
+
+
+@pytest.mark.parametrize("n", [[2 ** 21, 2 ** 21, 2 ** 22], [2 ** 31 - 1] * 3, [96, 96, 96], [66, 66, 69]])
+def test_noalloc_rejects_problems_beyond_its_scratch_before_touching_the_device(lib, n):
+    """mfc_rhs_noalloc's size check (neq * ncells + 32 doubles against the
+    fixed scratch) runs before any device call and cannot be fooled by a
+    wrapping cell count."""
+    p = mfc.make_params(_params(n=n), "fp64")
+    dummy = ctypes.c_void_p(16)   # never dereferenced: the call returns first
+    assert lib.mfc_rhs_noalloc(ctypes.byref(p), dummy, dummy, None) == mfc.MFC_ETOOBIG
