@@ -159,7 +159,8 @@ int mfc_kernel_time(mfc_ctx* ctx, int index, const char** name, double* ms, long
  * FP64-fast and mixed forms: MFC_EINVAL for WENO3 or MFC_GATED contexts, a
  * bad direction, or edges that are not strictly increasing.  Synchronises
  * the context's stream; the wave speed of a state already set is
- * recomputed.  The edges are copied. */
+ * recomputed.  The edges are copied.  On MFC_ENOMEM or MFC_ECUDA while the
+ * new tables are allocated or copied, the context keeps its previous grid. */
 int mfc_set_grid(mfc_ctx* ctx, int dir, const double* edges);
 
 /* Sets the gate weights of a MFC_GATED context (host array of n =

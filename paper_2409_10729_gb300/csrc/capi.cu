@@ -459,23 +459,35 @@ extern "C" int mfc_set_grid(mfc_ctx* ctx, int dir, const double* edges) {
     }
     const bool fp32 = fp32_state(ctx);
     if (fp32) tab32.assign(tab.begin(), tab.end());
-    CK(cudaStreamSynchronize(ctx->stream));
-    void* old[] = {ctx->gtab[dir], ctx->gw[dir], ctx->grw[dir], ctx->grw32[dir]};
-    for (void* b : old)
-        if (b) cudaFree(b);
-    ctx->gtab[dir] = ctx->gw[dir] = ctx->grw[dir] = nullptr;
-    ctx->grw32[dir] = nullptr;
+    // the new tables go into new buffers first: on failure the context keeps
+    // its current grid (and the captured step its buffers)
     const size_t tb = tab.size() * (fp32 ? sizeof(float) : sizeof(double));
-    if (cudaMalloc(&ctx->gtab[dir], tb) != cudaSuccess ||
-        cudaMalloc((void**)&ctx->gw[dir], n * sizeof(double)) != cudaSuccess ||
-        cudaMalloc((void**)&ctx->grw[dir], n * sizeof(double)) != cudaSuccess ||
-        cudaMalloc((void**)&ctx->grw32[dir], n * sizeof(float)) != cudaSuccess)
+    void* nt = nullptr;
+    double *nw = nullptr, *nrw = nullptr;
+    float* nrw32 = nullptr;
+    auto free_new = [&]() {
+        void* b[] = {nt, nw, nrw, nrw32};
+        for (void* x : b)
+            if (x) cudaFree(x);
+    };
+    if (cudaMalloc(&nt, tb) != cudaSuccess || cudaMalloc((void**)&nw, n * sizeof(double)) != cudaSuccess ||
+        cudaMalloc((void**)&nrw, n * sizeof(double)) != cudaSuccess ||
+        cudaMalloc((void**)&nrw32, n * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        free_new();
         return MFC_ENOMEM;
-    CK(cudaMemcpy(ctx->gtab[dir], fp32 ? (const void*)tab32.data() : (const void*)tab.data(), tb,
-                  cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(ctx->gw[dir], width.data(), n * sizeof(double), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(ctx->grw[dir], rw.data(), n * sizeof(double), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(ctx->grw32[dir], rw32.data(), n * sizeof(float), cudaMemcpyHostToDevice));
+    }
+    cudaError_t e = cudaMemcpy(nt, fp32 ? (const void*)tab32.data() : (const void*)tab.data(), tb,
+                               cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(nw, width.data(), n * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(nrw, rw.data(), n * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(nrw32, rw32.data(), n * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) {
+        ctx->last_cuda = (int)e;
+        free_new();
+        return MFC_ECUDA;
+    }
     // the captured step refers to the old buffers; the wave speed of the
     // current state changes with the widths
     if (ctx->gexec) {
@@ -483,6 +495,13 @@ extern "C" int mfc_set_grid(mfc_ctx* ctx, int dir, const double* edges) {
         ctx->gexec = NULL;
     }
     ctx->graph_ok = false;
+    void* old[] = {ctx->gtab[dir], ctx->gw[dir], ctx->grw[dir], ctx->grw32[dir]};
+    for (void* b : old)
+        if (b) cudaFree(b);
+    ctx->gtab[dir] = nt;
+    ctx->gw[dir] = nw;
+    ctx->grw[dir] = nrw;
+    ctx->grw32[dir] = nrw32;
     if (ctx->have_state) {
         CK(launch_wavespeed(ctx->ndim, ctx->qn, ctx->n, ctx->gw, ctx->grw, ctx->ncell, ctx->dx, ctx->rdx, ctx->eos,
                             ctx->ctrl, ctx->stream));
