@@ -135,26 +135,34 @@ class ClockSampler:
         except Exception:
             self.proc.kill()
         self.fh.close()
-        sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         with open(self.out_path) as f:
-            for line in f:
-                parts = [x.strip() for x in line.split(",")]
-                if len(parts) < 7:
-                    continue
-                try:
-                    sm.append(float(parts[0]))
-                    smax.append(float(parts[1]))
-                except ValueError:
-                    continue
-                for nm, v in zip(names, parts[3:7]):
-                    if v.lower().startswith("active"):
-                        reasons.add(nm)
+            out = parse_clock_samples(f)
         os.unlink(self.out_path)
-        if not sm:
-            return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        return out
+
+
+def parse_clock_samples(lines):
+    """Median SM clock, the largest max clock and the active throttle reasons
+    of nvidia-smi samples (csv, noheader, nounits, fields as ClockSampler
+    queries them); None without a usable sample."""
+    sm, smax, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in lines:
+        parts = [x.strip() for x in line.split(",")]
+        if len(parts) < 7:
+            continue
+        try:
+            sm.append(float(parts[0]))
+            smax.append(float(parts[1]))
+        except ValueError:
+            continue
+        for nm, v in zip(names, parts[3:7]):
+            if v.lower().startswith("active"):
+                reasons.add(nm)
+    if not sm:
+        return None
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+            "samples": len(sm)}
 
 
 def read_traffic(kernel: str):

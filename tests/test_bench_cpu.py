@@ -1,0 +1,48 @@
+"""Host logic of bench.py (CPU): clock-sample parsing, the algorithmic flop
+counts and the roofline arithmetic of the dominant kernel."""
+import bench
+
+
+def test_clock_samples_median_max_and_reasons():
+    lines = [
+        "2070, 2070, 900.5, Not Active, Not Active, Not Active, Not Active\n",
+        "1980, 2070, 1390.0, Not Active, Not Active, Not Active, Active\n",
+        "2010, 2070, 1200.0, Not Active, Not Active, Not Active, Not Active\n",
+        "[N/A], 2070, 0, Not Active, Not Active, Not Active, Not Active\n",   # unreadable sample
+        "garbage\n",
+    ]
+    out = bench.parse_clock_samples(lines)
+    assert out == {"sm_mhz": 2010.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    assert bench.parse_clock_samples([]) is None
+    hot = bench.parse_clock_samples(["1500, 2070, 1400, Active, Not Active, Active, Not Active\n"])
+    assert hot["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
+
+
+def test_flop_counts_two_and_three_fluids():
+    # two fluids in 3-D: cons->prim 22, WENO5 107 x 7 fields, HLLC 122, divergence 18
+    assert bench.flops_cell_dir(2, 3, 5) == 22 + 107 * 7 + 122 + 18 == 911
+    assert bench.flops_cell_dir(2, 3, 3) == 22 + 38 * 7 + 122 + 18 == 428
+    # last sweep: accumulate 7 + stage update 28 + a third of the wave speed 45
+    assert bench.flops_cell_dir() + bench.flops_last_sweep_extra() == 961
+    # each added fluid adds two fields (partial density and volume fraction)
+    assert bench.flops_cell_dir(3, 3, 5) - bench.flops_cell_dir(2, 3, 5) == 6 + 107 * 2 + 19 + 2 * 2 + 4
+    assert bench.flops_cell_dir(3, 3, 5) == 1158
+
+
+def test_roofline_of_the_dominant_kernel():
+    ncell = 256 ** 3
+    res = {"kernels": {"sweep_x": (3 * 38.0, 3), "sweep_y": (3 * 38.5, 3), "sweep_z": (3 * 40.0, 3),
+                       "step_begin": (0.03, 1)},
+           "ncell": ncell, "neq": 7, "grind": 1.0}
+    r = bench.roofline_for("fp64", res, 1.23, "measured", 6782.1, "measured")
+    assert r["kernel"] == "sweep_z" and r["bound"] == "alu" and r["unit"] == "TFLOP/s"
+    achieved = 961 * ncell / 40.0e-3 / 1e12
+    assert abs(r["achieved"] - achieved) < 1e-4 and abs(r["frac"] - achieved / 1.23) < 1e-4
+    assert abs(r["share_of_step"] - 120.0 / (114.0 + 115.5 + 120.0 + 0.03)) < 1e-3
+    # algorithmic HBM bytes: 8/3 state arrays of FP64 per cell, equation and RHS
+    assert abs(r["hbm"]["achieved_gbs"] - 21.3) < 0.06
+    # three fluids: 9 equations, the N-fluid count
+    res3 = dict(res, neq=9)
+    r3 = bench.roofline_for("fp64_3fluid", res3, 1.23, "measured", 6782.1, "measured")
+    assert r3["algorithmic_flops_per_cell"] == 1220.0
+    assert r3["traffic"] is None and r3["pipe_busy_ncu"] is None   # only the base forms carry ncu figures
