@@ -209,8 +209,20 @@ def gate_weights():
     return np.load(os.path.join(ROOT, "paper_2409_10729_gb300", "gate_weights.npy"))
 
 
-def time_form(form, p, w, steps, warmup, device_index, rank, world):
-    """Run `warmup` + `steps` RK3 steps of one form; returns a result dict."""
+def split_steps(steps: int, regions: int = 5):
+    """K timed steps as up to `regions` consecutive regions of nearly equal
+    length (every region at least one step)."""
+    r = max(1, min(regions, steps))
+    base, extra = divmod(steps, r)
+    return [base + (1 if i < extra else 0) for i in range(r)]
+
+
+def time_form(form, p, w, steps, warmup, device_index, rank, world, kernel_steps=3):
+    """Run `warmup` + `steps` RK3 steps of one form, replaying the captured
+    step graph exactly as the product does, timed with CUDA events on the
+    context's stream as consecutive regions (median per-step time over the
+    regions next to the total); then a separate, shorter pass with per-kernel
+    events (direct launches) for the kernel split.  Returns a result dict."""
     import torch
     from paper_2409_10729_gb300 import mfc
     s = mfc.Solver(p, form)
@@ -218,37 +230,61 @@ def time_form(form, p, w, steps, warmup, device_index, rank, world):
         s.set_mlp_weights(gate_weights())
     s.set_state_prim(w)
     s.step_rk3(CFL, warmup)
-    s.set_timing(True)
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
     sampler = ClockSampler(device_index)
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     stream = torch.cuda.current_stream()
-    ev0.record(stream)
-    t_adv = s.step_rk3(CFL, steps)
-    ev1.record(stream)
+    parts = split_steps(steps)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(parts) + 1)]
+    t_adv = 0.0
+    evs[0].record(stream)
+    for i, k in enumerate(parts):
+        t_adv += s.step_rk3(CFL, k)
+        evs[i + 1].record(stream)
     torch.cuda.synchronize()
     clocks = sampler.stop()
-    ms = max_over_ranks(ev0.elapsed_time(ev1), world)
+    region_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(len(parts))]
+    ms = max_over_ranks(evs[0].elapsed_time(evs[-1]), world)
+    per_step = sorted(r / k for r, k in zip(region_ms, parts))
+    median_step_ms = max_over_ranks(statistics.median(per_step), world)
     if world > 1:
         torch.distributed.barrier()
-    kt = s.kernel_times()
     gate = (*s.gate_stats(), s.gate_flat()) if form == "gated" else None
     launches = s.launches_per_step() * steps
+    # per-kernel split: direct launches bracketed by per-kernel events
+    ks = max(1, min(kernel_steps, steps))
+    s.set_timing(True)
+    s.step_rk3(CFL, ks)
+    kt = s.kernel_times()
+    launches += s.launches_per_step() * ks
     s.set_timing(False)
     ncell = p["n"][0] * p["n"][1] * p["n"][2]
     neq = 2 * len(p["gamma"]) + p["ndim"]
     grind = aggregate_grind(ms * 1e-3, steps, ncell, neq, world)
+    grind_median = aggregate_grind(median_step_ms * 1e-3, 1, ncell, neq, world)
     s.close()
     del s
     torch.cuda.empty_cache()
-    return {"ms": ms, "grind": grind, "kernels": kt, "launches": launches, "clocks": clocks,
-            "t_advanced": t_adv, "ncell": ncell, "neq": neq, "steps": steps, "gate": gate}
+    return {"ms": ms, "grind": grind, "grind_median": grind_median, "median_step_ms": median_step_ms,
+            "region_steps": parts, "region_ms": region_ms, "kernels": kt, "kernel_steps": ks,
+            "launches": launches, "clocks": clocks, "t_advanced": t_adv, "ncell": ncell, "neq": neq,
+            "steps": steps, "gate": gate}
 
 
 def roofline_for(form, res, peak_alu, alu_src, hbm_peak, hbm_src):
-    """Roofline object for the dominant kernel of one form."""
+    """Roofline object for the dominant kernel of one form.
+
+    FP64 forms: the sweeps are bound by the FP64 pipe.  The reference-order
+    form is built without FMA contraction, so every algorithmic +, -, *, /,
+    sqrt issues at least one FP64 instruction, and its ceiling is the FP64
+    instruction rate: the FMA-chain probe's FMA instructions per second (its
+    TFLOP/s over 2).  achieved = algorithmic operations per second; the gap
+    to ncu's FP64 pipe-busy fraction is what a correctly rounded division or
+    square root costs beyond its one algorithmic operation.  The reorganised
+    FP64 form contracts FMAs and is measured the same way (one operation per
+    instruction slot), as are the FP32 forms against the FP32 probe, whose
+    code is FMA-contracted: for them the ceiling is TFLOP/s at 2 per FMA."""
     kt = res["kernels"]
     base = form.replace("_weno3", "").replace("_stretched", "").replace("_3fluid", "")
     name = max((k for k in kt if kt[k][1] > 0), key=lambda k: kt[k][0])
@@ -263,14 +299,69 @@ def roofline_for(form, res, peak_alu, alu_src, hbm_peak, hbm_src):
         flops += flops_last_sweep_extra(nf, 3)
     achieved = flops * ncell / avg_s / 1e12
     share = total_ms / sum(v[0] for v in kt.values())
-    return {"bound": "alu", "kernel": name, "achieved": round(achieved, 4), "peak": round(peak_alu, 3),
-            "unit": "TFLOP/s", "frac": round(achieved / peak_alu, 4), "peak_source": alu_src,
+    fp64 = base.startswith("fp64")
+    if fp64:
+        peak, unit = peak_alu / 2.0, "Top/s"
+        src = (f"{alu_src}: {peak_alu:.3f} TFLOP/s = {peak_alu / 2:.3f} T FP64 FMA instructions/s; one algorithmic "
+               "operation (+, -, *, /, sqrt, min/max) per FP64 instruction slot")
+    else:
+        peak, unit = peak_alu, "TFLOP/s"
+        src = f"{alu_src} (FP32, 2 flops per FMA)"
+    return {"bound": "alu", "kernel": name, "achieved": round(achieved, 4), "peak": round(peak, 4),
+            "unit": unit, "frac": round(achieved / peak, 4), "peak_source": src,
             "traffic": read_traffic(f"{form}:{name}") if form == base else None, "share_of_step": round(share, 3),
             "avg_launch_ms": round(total_ms / count, 4),
             "algorithmic_flops_per_cell": flops,
             "pipe_busy_ncu": pipe_busy(form, name) if form == base else None,
             "hbm": {"achieved_gbs": round(ALG_BYTES[base] / res["grind"], 1), "peak": hbm_peak,
                     "frac": round(ALG_BYTES[base] / res["grind"] / hbm_peak, 4), "peak_source": hbm_src}}
+
+
+def host_info():
+    """Core count and CPU model of this host (nproc, lscpu)."""
+    info = {"nproc": os.cpu_count() or 1, "model": None}
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            k, _, v = line.partition(":")
+            if k.strip() in ("Model name", "Model"):
+                if info["model"] is None or k.strip() == "Model name":
+                    info["model"] = v.strip()
+    except Exception:
+        pass
+    if info["model"] is None:
+        try:
+            with open("/proc/cpuinfo") as fh:
+                for line in fh:
+                    if line.lower().startswith(("model name", "cpu part")):
+                        info["model"] = line.partition(":")[2].strip()
+                        break
+        except OSError:
+            pass
+    try:
+        info["nproc"] = len(os.sched_getaffinity(0))
+    except Exception:
+        pass
+    return info
+
+
+def baseline_entry(grind: float, sample: str):
+    """cpu_baseline object: the serial oracle's grind on one core, the host,
+    and the ideal-scaling figure (single-core grind / nproc)."""
+    h = host_info()
+    return {"value": round(grind, 4), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+            "host": {"nproc": h["nproc"], "cpu_model": h["model"]},
+            "ideal_scaling_all_cores": {"value": round(grind / h["nproc"], 4), "unit": UNIT,
+                                        "cores": h["nproc"],
+                                        "note": "single-core grind / nproc (ideal scaling), not measured"}}
+
+
+def headline_config(ncell=256 ** 3, neq=7, n_gpus=1):
+    """The workload the headline value is quoted on (both arms print it)."""
+    return {"workload": "3-D shock-droplet array, 256^3 cells, 7 equations, FP64, SSP-RK3 at CFL 0.4 "
+                        "(step = one RK3 step = 3 RHS evaluations)",
+            "cells": ncell, "neq": neq, "precision": "fp64", "parallelism": f"replicas x{n_gpus}",
+            "l2": "no flush: each state array is 0.94 GB (7 fields x 256^3 x 8 B) > 129 MB L2"}
 
 
 def cpu_baseline(target_s=15.0):
@@ -299,9 +390,8 @@ def cpu_baseline(target_s=15.0):
     t, ps = sample(k)
     ncell = 256 * 256 * k
     grind = t * 1e9 / (ncell * 7)
-    return {"value": round(grind, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"one oracle RHS on a 256x256x{k} z-slab (z from {z0}) of the 256^3 shock-droplet "
-                      f"initial state, {t:.1f} s"}, t, k
+    return baseline_entry(grind, f"one oracle RHS on a 256x256x{k} z-slab (z from {z0}) of the 256^3 "
+                                 f"shock-droplet initial state, {t:.1f} s"), t, k
 
 
 def run_reference(args):
@@ -333,12 +423,10 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(el * 1e3 / args.steps, 2),
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": {"workload": "3-D shock-droplet array 256^3 (7 eq), FP64 RHS; oracle on a "
-                                   f"256x256x{k} z-slab sample per step", "cells_per_step": 256 * 256 * k,
-                       "neq": 7},
-            "cpu_baseline": {"value": round(grind, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"one oracle RHS per step on a 256x256x{k} z-slab of the 256^3 "
-                                       "shock-droplet initial state"},
+            "config": headline_config(n_gpus=args.gpus),
+            "cpu_baseline": baseline_entry(grind, f"each step: one oracle RHS on a 256x256x{k} z-slab (z from "
+                                                  f"{z0}) of the 256^3 shock-droplet initial state "
+                                                  f"({256 * 256 * k} cells), serial, one core"),
             "e2e": {"value": round(grind, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -425,7 +513,8 @@ def run_ours(args):
     for name, r in forms.items():
         peak = fp32_peak if name.startswith(("mixed", "gated")) else fp64_peak
         rf = roofline_for(name, r, peak, "measured FMA-chain probe", hbm_peak, hbm_src)
-        out_forms[name] = {"grind": round(r["grind"], 5), "unit": UNIT, "ms_per_step": round(r["ms"] / r["steps"], 3),
+        out_forms[name] = {"grind": round(r["grind"], 5), "grind_median": round(r["grind_median"], 5), "unit": UNIT,
+            "ms_per_step": round(r["ms"] / r["steps"], 3),
             "cells": r["ncell"],
             "hbm_frac": rf["hbm"]["frac"], "hbm_gbs_algorithmic": rf["hbm"]["achieved_gbs"],
             "alu_frac": rf["frac"], "dominant_kernel": rf["kernel"],
@@ -441,10 +530,15 @@ def run_ours(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(res["ms"] / args.steps, 3),
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": "3-D shock-droplet array, 256^3 cells, 7 equations, FP64, SSP-RK3 at CFL 0.4 "
-                               "(step = one RK3 step = 3 RHS evaluations)",
-                   "cells": ncell, "neq": neq, "precision": "fp64", "parallelism": f"replicas x{world}",
-                   "l2": "no flush: each state array is 0.94 GB (7 fields x 256^3 x 8 B) > 129 MB L2"},
+        "config": headline_config(ncell, neq, world),
+        "timing": {"how": "CUDA events on the context stream around replays of the captured step graph "
+                          f"(the product path), the {args.steps} steps as {len(res['region_steps'])} consecutive "
+                          "regions; value from their total, median_ms_per_step = median over the regions; "
+                          "per-kernel split from a separate pass of direct launches with per-kernel events",
+                   "region_steps": res["region_steps"], "region_ms": [round(x, 3) for x in res["region_ms"]],
+                   "median_ms_per_step": round(res["median_step_ms"], 3),
+                   "median_grind": round(res["grind_median"], 5),
+                   "kernel_pass_steps": res["kernel_steps"]},
         "roofline": roof,
         "forms": out_forms,
         "e2e": {"value": round(e2e_grind, 5), "unit": UNIT, "h2d_bytes_per_step": ncell * neq * 8,

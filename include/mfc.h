@@ -224,7 +224,10 @@ int mfc_alu_peak(int fp64, double* tflops);
  * paper; the arithmetic is that of mfc_rhs.
  *   params       problem statement; precision must be MFC_FP64 (else MFC_EINVAL)
  *   q            device pointer, conservative FP64 state, layout above
- *   rhs          device pointer, receives L(q), same layout
+ *   rhs          device pointer, receives L(q), same layout; the ranges
+ *                [q, q + neq*ncells) and [rhs, rhs + neq*ncells) must not
+ *                overlap (MFC_EINVAL): the last sweep writes L into cells
+ *                that other warps still read as stencil input
  *   cuda_stream  cudaStream_t the kernels run on (NULL = legacy default)
  * No context, no allocation of any kind: the only scratch (accumulator and
  * status word) is a fixed array in device memory that belongs to the loaded
@@ -232,10 +235,12 @@ int mfc_alu_peak(int fp64, double* tflops);
  * Problems with neq * ncells + 32 > MFC_NOALLOC_MAX_DOUBLES are rejected with
  * MFC_ETOOBIG before anything is launched.  The first call on a device looks
  * up the array's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture.  Every call
- * shares the array: calls whose kernels may overlap on the GPU race and must
- * be serialised by the caller.  The call synchronises `cuda_stream` to read
- * the status; returns MFC_ENONPHYSICAL as mfc_rhs does. */
+ * current and keeps it for the life of the process; make that first call
+ * before any stream capture begins, and do not call again on a device after
+ * cudaDeviceReset() on it.  Every call shares the array: calls whose kernels
+ * may overlap on the GPU race and must be serialised by the caller.  Every
+ * call synchronises `cuda_stream` before returning, to read the status word;
+ * returns MFC_ENONPHYSICAL as mfc_rhs does. */
 int mfc_rhs_noalloc(const mfc_params* params, const double* q, double* rhs, void* cuda_stream);
 
 /* Instrumentation, no counterpart in the paper: checks the mixed form's

@@ -33,15 +33,40 @@ _LIB_OVERRIDE = os.environ.get("MFC5_ORACLE_LIB")
 OK, EINVAL, ENOMEM, ENONPHYSICAL = 0, -1, -2, -4
 
 
+_CMD = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared"]
+
+
+def _key() -> str:
+    """SHA-256 of the sources, the compile command and the compiler version."""
+    import hashlib
+    h = hashlib.sha256(" ".join(_CMD).encode())
+    for f in _SRCS:
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    try:
+        h.update(subprocess.run(["gcc", "--version"], capture_output=True, text=True).stdout.encode())
+    except OSError:
+        pass
+    return h.hexdigest()
+
+
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (no fast-math, no FMA contraction)."""
-    newest = max(os.path.getmtime(f) for f in _SRCS)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
+    """Compile the oracle with gcc (no fast-math, no FMA contraction).  The
+    build is keyed on a hash of the sources, command and compiler (stored in
+    liboracle_mfc5.so.key): a library whose key differs is rebuilt."""
+    key = _key()
+    try:
+        with open(_LIB + ".key") as fh:
+            stored = fh.read().strip()
+    except OSError:
+        stored = ""
+    if force or not os.path.exists(_LIB) or stored != key:
         tmp = _LIB + f".tmp{os.getpid()}"
-        cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-               "-shared", "-o", tmp, *_SRCS, "-lm"]
-        subprocess.run(cmd, check=True)
+        subprocess.run([*_CMD, "-o", tmp, *_SRCS, "-lm"], check=True)
         os.replace(tmp, _LIB)
+        with open(_LIB + f".key.tmp{os.getpid()}", "w") as fh:
+            fh.write(key + "\n")
+        os.replace(_LIB + f".key.tmp{os.getpid()}", _LIB + ".key")
     return _LIB
 
 

@@ -16,15 +16,21 @@
 // doubles (16 MiB).  Every device that loads the library holds it until the
 // process exits.  In host code its name is only a host-side stand-in, not a
 // device address, so its address is looked up per device with
-// cudaGetSymbolAddress on the first call made with that device current; that
-// first call should therefore come before any stream capture.  All calls
-// share the array and it keeps the previous call's contents: the status word
-// is cleared at the start of every call (the accumulator is fully rewritten
-// by the first sweep).  Calls whose kernels overlap on the GPU -- on
-// different streams, or from different host threads -- race on the array and
-// must be serialised by the caller.
+// cudaGetSymbolAddress on the first call made with that device current, and
+// kept for the life of the process: that first call should come before any
+// stream capture, and the library must not be called again on a device after
+// cudaDeviceReset() (the array is then reloaded at an address the cache does
+// not know).  All calls share the array and it keeps the previous call's
+// contents: the status word is cleared at the start of every call (the
+// accumulator is fully rewritten by the first sweep).  Calls whose kernels
+// overlap on the GPU -- on different streams, or from different host
+// threads -- race on the array and must be serialised by the caller.  Every
+// call synchronises its stream before returning, to read the status word.
+// The output must not overlap the input: the last sweep writes L into cells
+// whose neighbours other warps are still reading as stencil input.
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stdint.h>
 #include <string.h>
 
 #include "mfc.h"
@@ -95,6 +101,11 @@ extern "C" int mfc_rhs_noalloc(const mfc_params* params, const double* q, double
         if (ncell > cap / n[d]) return MFC_ETOOBIG;
         ncell *= n[d];
     }
+    // input and output ranges must be disjoint (compared as addresses; the
+    // byte count is below 16 MiB, so no sum wraps)
+    const uintptr_t qa = (uintptr_t)q, ra = (uintptr_t)rhs;
+    const uintptr_t bytes = (uintptr_t)(neq * ncell) * sizeof(double);
+    if (qa < ra + bytes && ra < qa + bytes) return MFC_EINVAL;
 
     double* scratch = nullptr;
     st = scratch_for_current_device(&scratch);

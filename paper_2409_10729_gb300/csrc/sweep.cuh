@@ -803,21 +803,26 @@ sweep_kernel(const SweepArgs a) {
     }
 }
 
-// Resident blocks of one sweep kernel on the whole device (occupancy x SMs),
-// looked up once per kernel.
+// Resident blocks of one sweep kernel on the current device (occupancy x
+// SMs), looked up once per kernel and device (devices may differ in SM count).
 template <int NDIM, int DIR, int MODE, int FORM, bool NU, int NF>
 long long sweep_slots() {
-    static const long long slots = [] {
-        int dev = 0, sms = 0, per_sm = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel<NDIM, DIR, MODE, FORM, NU, NF>,
-                                                          sweep_threads(DIR), 0) != cudaSuccess) {
-            cudaGetLastError();
-            per_sm = 1;
-        }
-        return (long long)(sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
-    }();
+    constexpr int kMaxDev = 64;
+    static long long cache[kMaxDev];   // 0: not yet looked up (a benign race: every writer stores the same value)
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        dev = 0;
+    }
+    if (dev >= 0 && dev < kMaxDev && cache[dev] > 0) return cache[dev];
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel<NDIM, DIR, MODE, FORM, NU, NF>,
+                                                      sweep_threads(DIR), 0) != cudaSuccess) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    const long long slots = (long long)(sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+    if (dev >= 0 && dev < kMaxDev) cache[dev] = slots;
     return slots;
 }
 

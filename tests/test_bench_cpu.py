@@ -35,9 +35,12 @@ def test_roofline_of_the_dominant_kernel():
                        "step_begin": (0.03, 1)},
            "ncell": ncell, "neq": 7, "grind": 1.0}
     r = bench.roofline_for("fp64", res, 1.23, "measured", 6782.1, "measured")
-    assert r["kernel"] == "sweep_z" and r["bound"] == "alu" and r["unit"] == "TFLOP/s"
+    # FP64 forms: algorithmic operations per second against the FP64
+    # instruction rate, i.e. the FMA probe's TFLOP/s over 2 flops per FMA
+    assert r["kernel"] == "sweep_z" and r["bound"] == "alu" and r["unit"] == "Top/s"
     achieved = 961 * ncell / 40.0e-3 / 1e12
-    assert abs(r["achieved"] - achieved) < 1e-4 and abs(r["frac"] - achieved / 1.23) < 1e-4
+    assert abs(r["peak"] - 0.615) < 1e-4
+    assert abs(r["achieved"] - achieved) < 1e-4 and abs(r["frac"] - achieved / 0.615) < 1e-4
     assert abs(r["share_of_step"] - 120.0 / (114.0 + 115.5 + 120.0 + 0.03)) < 1e-3
     # algorithmic HBM bytes: 8/3 state arrays of FP64 per cell, equation and RHS
     assert abs(r["hbm"]["achieved_gbs"] - 21.3) < 0.06
@@ -46,3 +49,31 @@ def test_roofline_of_the_dominant_kernel():
     r3 = bench.roofline_for("fp64_3fluid", res3, 1.23, "measured", 6782.1, "measured")
     assert r3["algorithmic_flops_per_cell"] == 1220.0
     assert r3["traffic"] is None and r3["pipe_busy_ncu"] is None   # only the base forms carry ncu figures
+    # FP32 forms: TFLOP/s against the FP32 probe at 2 flops per FMA
+    rm = bench.roofline_for("mixed", res, 77.5, "measured", 6782.1, "measured")
+    assert rm["unit"] == "TFLOP/s" and rm["peak"] == 77.5
+    assert abs(rm["frac"] - achieved / 77.5) < 1e-4
+    # algorithmic HBM bytes of the mixed form: 16 B per cell, equation and RHS
+    assert abs(rm["hbm"]["achieved_gbs"] - 16.0) < 1e-9
+
+
+def test_timed_steps_split_into_regions():
+    assert bench.split_steps(20) == [4, 4, 4, 4, 4]
+    assert bench.split_steps(12) == [3, 3, 2, 2, 2]
+    assert bench.split_steps(3) == [1, 1, 1]
+    assert bench.split_steps(1) == [1]
+    for k in range(1, 40):
+        parts = bench.split_steps(k)
+        assert sum(parts) == k and min(parts) >= 1 and len(parts) == min(5, k)
+
+
+def test_cpu_baseline_entry_states_the_host():
+    b = bench.baseline_entry(100.0, "a sample")
+    n = b["host"]["nproc"]
+    assert n >= 1 and b["cores"] == 1 and b["kind"] == "oracle"
+    assert abs(b["ideal_scaling_all_cores"]["value"] - 100.0 / n) < 1e-3
+    assert b["ideal_scaling_all_cores"]["cores"] == n
+
+
+def test_both_arms_quote_the_same_config():
+    assert bench.headline_config(n_gpus=2) == bench.headline_config(256 ** 3, 7, 2)

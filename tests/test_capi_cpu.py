@@ -113,3 +113,15 @@ def test_noalloc_rejects_problems_beyond_its_scratch_before_touching_the_device(
     p = mfc.make_params(_params(n=n), "fp64")
     dummy = ctypes.c_void_p(16)   # never dereferenced: the call returns first
     assert lib.mfc_rhs_noalloc(ctypes.byref(p), dummy, dummy, None) == mfc.MFC_ETOOBIG
+
+
+@pytest.mark.parametrize("offset_doubles", [0, 1, -1, 8 * 8 * 8 * 7 - 1, -(8 * 8 * 8 * 7 - 1)])
+def test_noalloc_refuses_overlapping_buffers_before_touching_the_device(lib, offset_doubles):
+    """mfc_rhs_noalloc refuses an output range that overlaps the input range
+    (in place, or shifted by fewer cells than the state holds) with
+    MFC_EINVAL before any device call; the addresses are never dereferenced."""
+    p = mfc.make_params(_params(), "fp64")
+    base = 1 << 40
+    q = ctypes.c_void_p(base)
+    rhs = ctypes.c_void_p(base + 8 * offset_doubles)
+    assert lib.mfc_rhs_noalloc(ctypes.byref(p), q, rhs, None) == mfc.MFC_EINVAL
