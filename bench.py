@@ -282,9 +282,9 @@ def roofline_for(form, res, peak_alu, alu_src, hbm_peak, hbm_src):
     TFLOP/s over 2).  achieved = algorithmic operations per second; the gap
     to ncu's FP64 pipe-busy fraction is what a correctly rounded division or
     square root costs beyond its one algorithmic operation.  The reorganised
-    FP64 form contracts FMAs and is measured the same way (one operation per
-    instruction slot), as are the FP32 forms against the FP32 probe, whose
-    code is FMA-contracted: for them the ceiling is TFLOP/s at 2 per FMA."""
+    FP64 form and the FP32 forms are built with FMA contraction: their
+    ceiling is the probe's TFLOP/s at 2 flops per FMA (FP64 and FP32 probe
+    respectively)."""
     kt = res["kernels"]
     base = form.replace("_weno3", "").replace("_stretched", "").replace("_3fluid", "")
     name = max((k for k in kt if kt[k][1] > 0), key=lambda k: kt[k][0])
@@ -299,14 +299,13 @@ def roofline_for(form, res, peak_alu, alu_src, hbm_peak, hbm_src):
         flops += flops_last_sweep_extra(nf, 3)
     achieved = flops * ncell / avg_s / 1e12
     share = total_ms / sum(v[0] for v in kt.values())
-    fp64 = base.startswith("fp64")
-    if fp64:
+    if base == "fp64":   # the reference-order form (no FMA contraction)
         peak, unit = peak_alu / 2.0, "Top/s"
         src = (f"{alu_src}: {peak_alu:.3f} TFLOP/s = {peak_alu / 2:.3f} T FP64 FMA instructions/s; one algorithmic "
                "operation (+, -, *, /, sqrt, min/max) per FP64 instruction slot")
     else:
         peak, unit = peak_alu, "TFLOP/s"
-        src = f"{alu_src} (FP32, 2 flops per FMA)"
+        src = f"{alu_src} ({'FP64' if base == 'fp64_fast' else 'FP32'}, 2 flops per FMA)"
     return {"bound": "alu", "kernel": name, "achieved": round(achieved, 4), "peak": round(peak, 4),
             "unit": unit, "frac": round(achieved / peak, 4), "peak_source": src,
             "traffic": read_traffic(f"{form}:{name}") if form == base else None, "share_of_step": round(share, 3),

@@ -212,6 +212,85 @@ int mfc_mlp_forward_tc(const float* X, long long n, const float* theta, float* z
  * synchronises the legacy default stream. */
 int mfc_alu_peak(int fp64, double* tflops);
 
+/* ---- block decomposition (Sec. III-A) --------------------------------------
+ * The global grid is split into Cartesian blocks, one context per block (on
+ * one GPU or several).  A block needs three ghost layers of the stage state
+ * beyond every side that borders another block; they are exchanged once per
+ * RK stage, and dt comes from the wave speed reduced over all blocks.  One
+ * SSP-RK3 step of a decomposed grid, driven by the caller:
+ *   S   = max over blocks of mfc_block_wavespeed     (dt = cfl / S)
+ *   mfc_block_begin_step(b, dt) for every block
+ *   for stage k = 1, 2, 3:
+ *     mfc_block_pack(b, k, send_b) for every block
+ *     copy each packed side into the facing side of the neighbour's halo
+ *     mfc_block_stage(b, k, halo_b) for every block
+ * The result is bit-identical to the undecomposed grid's in every form: a
+ * cell's update depends only on the cells of its stencils and on dt.
+ *
+ * Halo layout of a block (mfc_halo_layout): one segment per side (d, s) that
+ * borders another block, in the order (x low, x high, y low, y high, z low,
+ * z high); a segment is [field][layer 0..2][plane], the plane index being a
+ * cell's position in the plane normal to d, x fastest (y + ny z normal to x,
+ * x + nx z normal to y, x + nx y normal to z).  Layer l of the low side is
+ * the block's cell l - 3 along d, of the high side its cell n_d + l.  The
+ * fields are the stage state's: the neq conservative FP64 fields in the FP64
+ * forms; in the FP32 forms, neq FP32 fields and the pressure (neq + 1).
+ * mfc_block_pack writes a block's own boundary layers in the same layout (low
+ * side: its cells 0, 1, 2; high side: n_d - 3 .. n_d - 1), so the packed low
+ * side of block B is the high-side halo segment of B's low neighbour, and the
+ * packed high side the low-side segment of its high neighbour. */
+typedef struct {
+    int lo[3];   /* global index of the block's first cell per dimension (0 beyond ndim) */
+    int n[3];    /* cells of the block per dimension (1 beyond ndim); at least 3 along a
+                    dimension in which the block has a neighbour */
+} mfc_block;
+
+/* Creates the context of one block of the grid `global` (validated as by
+ * mfc_create).  Its state, stage and accumulator buffers hold the block's
+ * cells only (layout as above, with the block's n); the grid spacing is the
+ * global grid's.  A side borders another block unless it is a domain
+ * boundary of a non-periodic dimension, or the block spans a periodic
+ * dimension (then it wraps onto itself).  MFC_EINVAL for a block outside the
+ * grid or thinner than 3 cells in a dimension with a neighbour.  Such a
+ * context takes the state calls (mfc_set_state, mfc_get_state, ...) for its
+ * own cells; mfc_rhs, mfc_step_rk3 and mfc_step_rk3_dt return MFC_ESTATE when
+ * it has a neighbour (use the calls below), and mfc_set_grid MFC_EINVAL. */
+int mfc_create_block(const mfc_params* global, const mfc_block* block, void* cuda_stream, mfc_ctx** out);
+
+/* Halo layout: offset[2 d + s] = element offset of side (d, s)'s segment, or
+ * -1 where that side has no neighbour (offset has room for 6); *total = the
+ * elements of the pack and halo buffers; *elem_bytes = 8 (FP64 forms) or 4
+ * (FP32 forms).  Any output may be NULL.  A context that is not a block
+ * reports no segments. */
+int mfc_halo_layout(mfc_ctx* ctx, long long* offset, long long* total, int* elem_bytes);
+
+/* Packs the boundary layers of the state that stage `stage` (1..3) reads
+ * (q^n for stage 1) into the device buffer `out` (halo layout, caller-owned,
+ * `total` elements).  Ordered on the context's stream; does not synchronise. */
+int mfc_block_pack(mfc_ctx* ctx, int stage, void* out);
+
+/* Starts a step of size dt > 0 (cfl / S with S reduced over all blocks):
+ * the counterpart of the first kernel of mfc_step_rk3's step. */
+int mfc_block_begin_step(mfc_ctx* ctx, double dt);
+
+/* Stage `stage` (1..3) of SSP-RK3 on the block: the direction sweeps with
+ * the stage update folded into the last; ghost cells beyond a side with a
+ * neighbour are read from `halo` (device, halo layout, filled with the
+ * neighbours' packed layers of the same stage's input; may be NULL for a
+ * block without neighbours).  Stage 3 also reduces the block's wave speed.
+ * Ordered on the context's stream; does not synchronise. */
+int mfc_block_stage(mfc_ctx* ctx, int stage, const void* halo);
+
+/* The block's wave speed S: of the state set last (mfc_set_state*), or, after
+ * a stage 3, of the new state.  Synchronises the stream.  Returns
+ * MFC_ENONPHYSICAL (and clears the flag) when a state or face since the last
+ * such report was non-physical. */
+int mfc_block_wavespeed(mfc_ctx* ctx, double* s);
+
+/* L(q^n) of the block (as mfc_rhs) with the ghost cells beyond its sides
+ * with neighbours taken from `halo` (the neighbours' packed stage-1 layers). */
+int mfc_block_rhs(mfc_ctx* ctx, const void* halo, double* rhs, int on_device);
+
 /* Capacity, in doubles, of the fixed device scratch used by mfc_rhs_noalloc
  * (16 MiB): it must hold neq * ncells doubles plus a 32-double control block. */
 #define MFC_NOALLOC_MAX_DOUBLES (2 * 1024 * 1024)

@@ -38,7 +38,7 @@ EXTRA = {"sweep_mixed.cu": FAST32, "sweep_gated.cu": FAST32,
 # of the build key
 USER_FLAGS = os.environ.get("MFC5_NVCC_FLAGS", "").split()
 UNITS = ["capi.cu", "aux.cu", "sweep_fp64.cu", "sweep_fp64x.cu", "sweep_mixed.cu", "sweep_gated.cu", "mlp.cu",
-         "noalloc.cu", "grid.cu"]
+         "noalloc.cu", "grid.cu", "blocks.cu"]
 
 
 def nvcc() -> str:

@@ -60,6 +60,13 @@ struct mfc_ctx {
     double* gw[3];     // cell widths
     double* grw[3];    // RN(1/width)
     float* grw32[3];   // 1/width in FP32
+    // block of a decomposed grid (mfc_create_block); zero otherwise
+    int is_block;
+    int blk_lo[3];     // global index of the block's first cell
+    int nbr[3][2];     // 1 where side (d, s) borders another block
+    long long hoff[6]; // halo layout: element offset of side (d, s) at 2 d + s, -1 if none
+    long long htotal;  // halo buffer elements
+    const void* halo_cur;  // halo buffer of the call in progress (sweeps read ghosts there)
 };
 
 #define CK(call)                                   \
@@ -227,6 +234,13 @@ static SweepArgs base_args(mfc_ctx* ctx) {
 static cudaError_t launch_sweep(mfc_ctx* ctx, int dir, int mode, SweepArgs a, cudaStream_t s) {
     a.periodic = ctx->periodic[dir];
     a.tab = ctx->gtab[dir];
+    if (ctx->is_block && ctx->halo_cur) {
+        const char* h = static_cast<const char*>(ctx->halo_cur);
+        const size_t el = state_elem(ctx);
+        if (ctx->nbr[dir][0]) a.hlo = h + ctx->hoff[2 * dir] * el;
+        if (ctx->nbr[dir][1]) a.hhi = h + ctx->hoff[2 * dir + 1] * el;
+        a.hplane = ctx->ncell / ctx->n[dir];
+    }
     switch (ctx->form) {
         case FORM_FP64_EXACT: return launch_sweep_fp64x(ctx->ndim, dir, mode, a, s);
         case FORM_FP64_FAST: return launch_sweep_fp64(ctx->ndim, dir, mode, a, s);
@@ -360,8 +374,13 @@ static int write_ctrl_params(mfc_ctx* ctx, double cfl, double dt_fixed) {
     return MFC_OK;
 }
 
-extern "C" int mfc_rhs(mfc_ctx* ctx, double* rhs, int on_device) {
-    if (!ctx || !rhs) return MFC_EINVAL;
+static bool has_neighbours(const mfc_ctx* ctx) {
+    for (int d = 0; d < 3; ++d)
+        if (ctx->nbr[d][0] || ctx->nbr[d][1]) return true;
+    return false;
+}
+
+static int rhs_impl(mfc_ctx* ctx, double* rhs, int on_device) {
     if (!ctx->have_state || (ctx->form == FORM_GATED && !ctx->have_gate)) return MFC_ESTATE;
     int st = write_ctrl_params(ctx, 0.0, 0.0);
     if (st) return st;
@@ -394,6 +413,12 @@ extern "C" int mfc_rhs(mfc_ctx* ctx, double* rhs, int on_device) {
     return ctx->ctrl_h->status ? MFC_ENONPHYSICAL : MFC_OK;
 }
 
+extern "C" int mfc_rhs(mfc_ctx* ctx, double* rhs, int on_device) {
+    if (!ctx || !rhs) return MFC_EINVAL;
+    if (has_neighbours(ctx)) return MFC_ESTATE;   // a block's ghosts: mfc_block_rhs
+    return rhs_impl(ctx, rhs, on_device);
+}
+
 extern "C" int mfc_max_wavespeed(mfc_ctx* ctx, double* s) {
     if (!ctx || !s) return MFC_EINVAL;
     if (!ctx->have_state) return MFC_ESTATE;
@@ -410,6 +435,7 @@ extern "C" int mfc_max_wavespeed(mfc_ctx* ctx, double* s) {
 
 static int run_steps(mfc_ctx* ctx, double cfl, double dt_fixed, int nsteps, double* t_out) {
     if (!ctx->have_state || (ctx->form == FORM_GATED && !ctx->have_gate)) return MFC_ESTATE;
+    if (has_neighbours(ctx)) return MFC_ESTATE;   // a block steps stage by stage (mfc_block_stage)
     int st = write_ctrl_params(ctx, cfl, dt_fixed);
     if (st) return st;
     if (ctx->timing) {
@@ -447,6 +473,7 @@ extern "C" int mfc_step_rk3_dt(mfc_ctx* ctx, double dt, int nsteps) {
 
 extern "C" int mfc_set_grid(mfc_ctx* ctx, int dir, const double* edges) {
     if (!ctx || !edges || dir < 0 || dir >= ctx->ndim) return MFC_EINVAL;
+    if (ctx->is_block) return MFC_EINVAL;
     if (ctx->form == FORM_GATED || ctx->p.weno_order == 3 || ctx->eos.nf != 2) return MFC_EINVAL;
     const int n = ctx->n[dir];
     std::vector<double> tab, width;
@@ -579,6 +606,138 @@ extern "C" int mfc_alu_peak(int fp64, double* tflops) {
         return MFC_ECUDA;
     }
     return MFC_OK;
+}
+
+// ---- block decomposition (Sec. III-A) ---------------------------------------
+
+extern "C" int mfc_create_block(const mfc_params* global, const mfc_block* block, void* cuda_stream,
+                                mfc_ctx** out) {
+    if (!out) return MFC_EINVAL;
+    *out = NULL;
+    if (!block) return MFC_EINVAL;
+    int st = validate(global);
+    if (st) return st;
+    mfc_params pb = *global;
+    int lo[3], n[3], nbr[3][2];
+    double dx[3];
+    for (int d = 0; d < 3; ++d) {
+        lo[d] = d < global->ndim ? block->lo[d] : 0;
+        n[d] = d < global->ndim ? block->n[d] : 1;
+        const int N = d < global->ndim ? global->n[d] : 1;
+        if (lo[d] < 0 || n[d] < 1 || lo[d] > N - n[d]) return MFC_EINVAL;
+        const bool periodic = d < global->ndim && global->bc[d][0] == MFC_BC_PERIODIC;
+        // a side borders another block unless it is a non-periodic domain
+        // boundary, or the block spans a periodic direction (its own wrap)
+        nbr[d][0] = d < global->ndim && (lo[d] > 0 || (periodic && n[d] < N));
+        nbr[d][1] = d < global->ndim && (lo[d] + n[d] < N || (periodic && n[d] < N));
+        if ((nbr[d][0] || nbr[d][1]) && n[d] < 3) return MFC_EINVAL;   // three ghost layers from one neighbour
+        if (d < global->ndim) {
+            dx[d] = (global->hi[d] - global->lo[d]) / (double)N;
+            pb.n[d] = n[d];
+            pb.lo[d] = global->lo[d] + lo[d] * dx[d];
+            pb.hi[d] = global->lo[d] + (lo[d] + n[d]) * dx[d];
+            if (!(pb.hi[d] > pb.lo[d])) return MFC_EINVAL;
+        }
+    }
+    mfc_ctx* ctx = NULL;
+    st = mfc_create(&pb, cuda_stream, &ctx);
+    if (st) return st;
+    // the grid spacing is the global grid's, bit for bit
+    for (int d = 0; d < global->ndim; ++d) {
+        ctx->inv_dx[d] = (double)global->n[d] / (global->hi[d] - global->lo[d]);
+        ctx->dx[d] = dx[d];
+        ctx->rdx[d] = 1.0 / dx[d];
+    }
+    ctx->is_block = 1;
+    long long off = 0;
+    for (int d = 0; d < 3; ++d) {
+        ctx->blk_lo[d] = lo[d];
+        for (int sd = 0; sd < 2; ++sd) {
+            ctx->nbr[d][sd] = nbr[d][sd];
+            ctx->hoff[2 * d + sd] = nbr[d][sd] ? off : -1;
+            if (nbr[d][sd]) off += (long long)state_fields(ctx) * 3 * (ctx->ncell / ctx->n[d]);
+        }
+    }
+    ctx->htotal = off;
+    *out = ctx;
+    return MFC_OK;
+}
+
+extern "C" int mfc_halo_layout(mfc_ctx* ctx, long long* offset, long long* total, int* elem_bytes) {
+    if (!ctx) return MFC_EINVAL;
+    if (offset)
+        for (int i = 0; i < 6; ++i) offset[i] = ctx->is_block ? ctx->hoff[i] : -1;
+    if (total) *total = ctx->htotal;
+    if (elem_bytes) *elem_bytes = (int)state_elem(ctx);
+    return MFC_OK;
+}
+
+// The state stage k (1..3) reads: q^n (or its FP32 copy) for k = 1.
+static const void* stage_input(mfc_ctx* ctx, int k) {
+    SweepArgs a;
+    memset(&a, 0, sizeof(a));
+    stage_buffers(ctx, k, a);
+    return a.qin;
+}
+
+extern "C" int mfc_block_pack(mfc_ctx* ctx, int stage, void* out) {
+    if (!ctx || stage < 1 || stage > 3 || (!out && ctx->htotal > 0)) return MFC_EINVAL;
+    if (!ctx->have_state) return MFC_ESTATE;
+    const void* q = stage_input(ctx, stage);
+    const int el = (int)state_elem(ctx);
+    for (int d = 0; d < 3; ++d)
+        for (int sd = 0; sd < 2; ++sd)
+            if (ctx->nbr[d][sd])
+                CK(launch_pack_side(q, static_cast<char*>(out) + ctx->hoff[2 * d + sd] * el, el,
+                                    state_fields(ctx), ctx->ncell, ctx->n, d, sd, ctx->stream));
+    return MFC_OK;
+}
+
+extern "C" int mfc_block_begin_step(mfc_ctx* ctx, double dt) {
+    if (!ctx || !(dt > 0.0) || !isfinite(dt)) return MFC_EINVAL;
+    if (!ctx->have_state || (ctx->form == FORM_GATED && !ctx->have_gate)) return MFC_ESTATE;
+    CK(launch_block_begin(ctx->ctrl, dt, ctx->stream));
+    return MFC_OK;
+}
+
+extern "C" int mfc_block_stage(mfc_ctx* ctx, int stage, const void* halo) {
+    if (!ctx || stage < 1 || stage > 3 || (!halo && ctx->htotal > 0)) return MFC_EINVAL;
+    if (!ctx->have_state || (ctx->form == FORM_GATED && !ctx->have_gate)) return MFC_ESTATE;
+    SweepArgs a = base_args(ctx);
+    stage_buffers(ctx, stage, a);
+    ctx->halo_cur = halo;
+    cudaError_t e = cudaSuccess;
+    for (int d = 0; d < ctx->ndim && e == cudaSuccess; ++d) {
+        int mode = d == ctx->ndim - 1 ? SW_LAST_RK : (d == 0 ? SW_FIRST : SW_MID);
+        e = launch_sweep(ctx, d, mode, a, ctx->stream);
+    }
+    ctx->halo_cur = NULL;
+    CK(e);
+    return MFC_OK;
+}
+
+extern "C" int mfc_block_wavespeed(mfc_ctx* ctx, double* s) {
+    if (!ctx || !s) return MFC_EINVAL;
+    if (!ctx->have_state) return MFC_ESTATE;
+    int st = read_ctrl(ctx);
+    if (st) return st;
+    unsigned long long bits = ctx->ctrl_h->S_bits;
+    memcpy(s, &bits, sizeof(double));
+    const unsigned status = ctx->ctrl_h->status;
+    if (status) {   // reported once: cleared for the steps that follow
+        const unsigned zero = 0;
+        CK(cudaMemcpyAsync(&ctx->ctrl->status, &zero, sizeof(zero), cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
+    return status ? MFC_ENONPHYSICAL : MFC_OK;
+}
+
+extern "C" int mfc_block_rhs(mfc_ctx* ctx, const void* halo, double* rhs, int on_device) {
+    if (!ctx || !rhs || (!halo && ctx->htotal > 0)) return MFC_EINVAL;
+    ctx->halo_cur = halo;
+    int st = rhs_impl(ctx, rhs, on_device);
+    ctx->halo_cur = NULL;
+    return st;
 }
 
 extern "C" const char* mfc_strerror(int status) {

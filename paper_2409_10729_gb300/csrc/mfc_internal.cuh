@@ -95,6 +95,13 @@ struct SweepArgs {
     const double* cw[3];  // per direction: cell widths
     const double* crw[3]; // per direction: RN(1/width)
     const float* crw32[3];  // per direction: 1/width in FP32 (FP32 forms)
+    // block decomposition (Sec. III-A): the sweep direction's ghost layers
+    // beyond a side that borders another block, [field][layer 0..2][plane],
+    // in the stage state's element type (null where the side is a domain
+    // boundary and the BC applies); hplane = cells of the plane normal to it
+    const void* hlo;      // cells -3 .. -1 (layer l = cell l - 3)
+    const void* hhi;      // cells n .. n + 2 (layer l = cell n + l)
+    long long hplane;
 };
 
 // Arithmetic forms of the sweep kernels:
@@ -123,6 +130,13 @@ cudaError_t launch_wavespeed(int ndim, const double* q, const int* n, const doub
                              const double* rdx, const Eos& e, DevCtrl* ctrl, cudaStream_t s);
 cudaError_t launch_step_begin(DevCtrl* ctrl, cudaStream_t s);
 cudaError_t launch_f32_to_f64(const float* src, double* dst, long long count, cudaStream_t s);
+// block decomposition (blocks.cu): the three boundary layers of side `side`
+// (0 low, 1 high) of direction `dir` of a state of nfields fields, element
+// size elem (4 or 8 bytes), into out[field][layer][plane]; the start of a
+// step with a given dt
+cudaError_t launch_pack_side(const void* q, void* out, int elem, int nfields, long long nc, const int* n, int dir,
+                             int side, cudaStream_t s);
+cudaError_t launch_block_begin(DevCtrl* ctrl, double dt, cudaStream_t s);
 cudaError_t run_fma_probe(int fp64, double* tflops, cudaStream_t s);
 
 // thread-block size of every sweep launch

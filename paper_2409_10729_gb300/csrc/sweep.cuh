@@ -461,11 +461,27 @@ sweep_kernel(const SweepArgs a) {
     // Along y and z the warp's 32 loads form one coalesced row per field;
     // along x each lane reads its own row, and the 32-byte sector it brings
     // into L1 serves the lane's next CH - 1 cells.
+    // A ghost cell beyond a side that borders another block (block
+    // decomposition) comes from that side's halo buffer; any other from the
+    // BC index map.  j is the same for the whole warp.
     auto fetch = [&](int k, R* v) {
         const int j = s0 - 3 + k;
-        const long long c = base + (long long)bc_index(j, ns, a.periodic) * ss;
+        const R* h = j < 0 ? static_cast<const R*>(a.hlo) : (j >= ns ? static_cast<const R*>(a.hhi) : nullptr);
+        if (h) {
+            // the pencil's position in the plane normal to DIR, from its first
+            // cell `base` (x fastest): y + n1 z along x, x + n0 z along y, x + n0 y along z
+            long long p;
+            if constexpr (DIR == 0) p = base / n0;
+            else if constexpr (DIR == 1) p = base % n0 + (long long)n0 * (base / ((long long)n0 * n1));
+            else p = base;
+            const long long hc = (long long)(j < 0 ? j + 3 : j - ns) * a.hplane + p;
 #pragma unroll
-        for (int f = 0; f < NL; ++f) v[f] = __ldg(qin + LS::field(f) * nc + c);
+            for (int f = 0; f < NL; ++f) v[f] = __ldg(h + (long long)LS::field(f) * 3 * a.hplane + hc);
+        } else {
+            const long long c = base + (long long)bc_index(j, ns, a.periodic) * ss;
+#pragma unroll
+            for (int f = 0; f < NL; ++f) v[f] = __ldg(qin + LS::field(f) * nc + c);
+        }
     };
 
     constexpr bool PREFETCH = MFC_PREFETCH != 0;

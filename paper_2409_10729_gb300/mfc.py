@@ -38,6 +38,10 @@ class MfcParams(ctypes.Structure):
     ]
 
 
+class MfcBlock(ctypes.Structure):
+    _fields_ = [("lo", ctypes.c_int * 3), ("n", ctypes.c_int * 3)]
+
+
 class MfcError(RuntimeError):
     def __init__(self, status: int, what: str):
         self.status = status
@@ -88,6 +92,14 @@ def lib() -> ctypes.CDLL:
                               vp], ip),
             "mfc_mlp_forward": ([vp, ctypes.c_longlong, vp, vp, vp], ip),
             "mfc_mlp_forward_tc": ([vp, ctypes.c_longlong, vp, vp, vp], ip),
+            "mfc_create_block": ([ctypes.POINTER(MfcParams), ctypes.POINTER(MfcBlock), vp, ctypes.POINTER(vp)], ip),
+            "mfc_halo_layout": ([vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
+                                 ctypes.POINTER(ip)], ip),
+            "mfc_block_pack": ([vp, ip, vp], ip),
+            "mfc_block_begin_step": ([vp, ctypes.c_double], ip),
+            "mfc_block_stage": ([vp, ip, vp], ip),
+            "mfc_block_wavespeed": ([vp, dp], ip),
+            "mfc_block_rhs": ([vp, vp, vp, ip], ip),
             "mfc_strerror": ([ip], ctypes.c_char_p),
             "mfc_last_cuda_error": ([vp], ip),
         }
@@ -150,23 +162,33 @@ def _ptr(a, ncells_neq: int):
 
 class Solver:
     """One mfc_ctx: a problem (params dict as produced by ``inputs``) on the
-    current CUDA device, bound to torch's current stream unless given one."""
+    current CUDA device, bound to torch's current stream unless given one.
+    With ``block`` = (lo, n) the context is one block of the global grid
+    ``p`` (mfc_create_block)."""
 
-    def __init__(self, p: dict, precision="fp64", stream=None):
+    def __init__(self, p: dict, precision="fp64", stream=None, block=None):
         import torch
         self.p = p
         self.neq = 2 * len(p["gamma"]) + int(p["ndim"])
-        self.shape = (self.neq, int(p["n"][2]) if p["ndim"] > 2 else 1,
-                      int(p["n"][1]) if p["ndim"] > 1 else 1, int(p["n"][0]))
+        n = list(p["n"]) if block is None else [int(block[1][d]) if d < p["ndim"] else 1 for d in range(3)]
+        self.shape = (self.neq, int(n[2]) if p["ndim"] > 2 else 1, int(n[1]) if p["ndim"] > 1 else 1, int(n[0]))
         self.size = int(np.prod(self.shape))
         if stream is None:
             stream = torch.cuda.current_stream()
         self._stream = stream
         handle = ctypes.c_void_p()
-        st = lib().mfc_create(ctypes.byref(make_params(p, precision)), ctypes.c_void_p(stream.cuda_stream),
-                              ctypes.byref(handle))
+        if block is None:
+            st = lib().mfc_create(ctypes.byref(make_params(p, precision)), ctypes.c_void_p(stream.cuda_stream),
+                                  ctypes.byref(handle))
+        else:
+            b = MfcBlock()
+            for d in range(3):
+                b.lo[d] = int(block[0][d]) if d < p["ndim"] else 0
+                b.n[d] = int(block[1][d]) if d < p["ndim"] else 1
+            st = lib().mfc_create_block(ctypes.byref(make_params(p, precision)), ctypes.byref(b),
+                                        ctypes.c_void_p(stream.cuda_stream), ctypes.byref(handle))
         if st != MFC_OK:
-            raise MfcError(st, "mfc_create")
+            raise MfcError(st, "mfc_create_block" if block is not None else "mfc_create")
         self.ctx = handle
         # non-uniform directions given as cell edges in the params dict
         for d, e in enumerate(p.get("edges") or []):
@@ -265,6 +287,42 @@ class Solver:
 
     def step_rk3_dt(self, dt: float, nsteps: int):
         return self._check(lib().mfc_step_rk3_dt(self.ctx, float(dt), int(nsteps)), "mfc_step_rk3_dt")
+
+    # -- block decomposition -----------------------------------------------
+    def halo_layout(self):
+        """(offsets of the six sides, -1 where none; total elements; element bytes)."""
+        off = (ctypes.c_longlong * 6)()
+        tot, el = ctypes.c_longlong(), ctypes.c_int()
+        self._check(lib().mfc_halo_layout(self.ctx, off, ctypes.byref(tot), ctypes.byref(el)), "mfc_halo_layout")
+        return list(off), tot.value, el.value
+
+    def block_pack(self, stage: int, out):
+        """Boundary layers of stage `stage`'s input into the device tensor `out`."""
+        return self._check(lib().mfc_block_pack(self.ctx, int(stage), ctypes.c_void_p(out.data_ptr())),
+                           "mfc_block_pack")
+
+    def block_begin_step(self, dt: float):
+        return self._check(lib().mfc_block_begin_step(self.ctx, float(dt)), "mfc_block_begin_step")
+
+    def block_stage(self, stage: int, halo):
+        ptr = ctypes.c_void_p(halo.data_ptr() if halo is not None and halo.numel() else None)
+        return self._check(lib().mfc_block_stage(self.ctx, int(stage), ptr), "mfc_block_stage")
+
+    def block_wavespeed(self, allow_nonphysical=False):
+        """(S of the block's current state, status)."""
+        s = ctypes.c_double()
+        allow = (MFC_ENONPHYSICAL,) if allow_nonphysical else ()
+        st = self._check(lib().mfc_block_wavespeed(self.ctx, ctypes.byref(s)), "mfc_block_wavespeed", allow)
+        return s.value, st
+
+    def block_rhs(self, halo, out=None, allow_nonphysical=False):
+        if out is None:
+            out = np.empty(self.shape, dtype=np.float64)
+        ptr, dev = _ptr(out, self.size)
+        hp = ctypes.c_void_p(halo.data_ptr() if halo is not None and halo.numel() else None)
+        allow = (MFC_ENONPHYSICAL,) if allow_nonphysical else ()
+        self.last_status = self._check(lib().mfc_block_rhs(self.ctx, hp, ptr, dev), "mfc_block_rhs", allow)
+        return out
 
     # -- instrumentation ---------------------------------------------------
     def launches_per_step(self) -> int:

@@ -49,6 +49,9 @@ def test_roofline_of_the_dominant_kernel():
     r3 = bench.roofline_for("fp64_3fluid", res3, 1.23, "measured", 6782.1, "measured")
     assert r3["algorithmic_flops_per_cell"] == 1220.0
     assert r3["traffic"] is None and r3["pipe_busy_ncu"] is None   # only the base forms carry ncu figures
+    # the reorganised FP64 form contracts FMAs: TFLOP/s at 2 flops per FMA
+    rf = bench.roofline_for("fp64_fast", res, 1.23, "measured", 6782.1, "measured")
+    assert rf["unit"] == "TFLOP/s" and rf["peak"] == 1.23
     # FP32 forms: TFLOP/s against the FP32 probe at 2 flops per FMA
     rm = bench.roofline_for("mixed", res, 77.5, "measured", 6782.1, "measured")
     assert rm["unit"] == "TFLOP/s" and rm["peak"] == 77.5
