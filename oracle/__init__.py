@@ -102,11 +102,13 @@ def lib():
             "orc_cons_to_prim": ([pp, dp, dp], ctypes.c_int),
             "orc_rhs": ([pp, dp, dp], ctypes.c_int),
             "orc_rhs_points": ([pp, dp, lp, ctypes.c_long, dp], ctypes.c_int),
+            "orc_rhs_gated": ([pp, dp, dp, ctypes.c_double, dp, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
             "orc_max_wavespeed": ([pp, dp, dp], ctypes.c_int),
             "orc_step_dt": ([pp, dp, ctypes.c_double], ctypes.c_int),
             "orc_run_cfl": ([pp, dp, ctypes.c_double, ctypes.c_int, dp], ctypes.c_int),
             "orc_weno5_cell": ([ctypes.c_double, dp, dp, dp], None),
             "orc_weno3_cell": ([ctypes.c_double, dp, dp, dp], None),
+            "orc_linear5_cell": ([dp, dp, dp], None),
             "orc_weno5_table": ([dp, dp], ctypes.c_int),
             "orc_weno5_nu_cell": ([dp, ctypes.c_double, dp, dp, dp], None),
             "orc_hllc_face": ([pp, ctypes.c_int, dp, dp, dp, dp], ctypes.c_int),
@@ -117,7 +119,7 @@ def lib():
             "mlp_loss_grad": ([dp, dp, dp, ctypes.c_long, ctypes.c_double, dp], ctypes.c_double),
             "mlp_adam": ([dp, dp, dp, dp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                           ctypes.c_double], None),
-            "mlp_normalise": ([dp, dp], None),
+            "mlp_normalise": ([dp, ctypes.c_double, dp], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(_lib, name)
@@ -197,6 +199,25 @@ def rhs(p: dict, q: np.ndarray, allow_nonphysical: bool = False) -> np.ndarray:
     return out
 
 
+GATE_INFO = 5   # z_rho, z_p, flat ratios of both sensors, admissibility margin
+
+
+def rhs_gated(p: dict, q: np.ndarray, theta, delta: float, allow_nonphysical: bool = False):
+    """L(q) of the gated form (network parameters theta, round-off floor
+    delta): returns (L, decisions [ndim][nz][ny][nx] (0 WENO, 1 linear,
+    2 fallback), info [ndim][nz][ny][nx][GATE_INFO])."""
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    out = np.empty_like(q)
+    nd = int(p["ndim"])
+    dec = np.zeros((nd,) + q.shape[1:], dtype=np.int8)
+    info = np.zeros((nd,) + q.shape[1:] + (GATE_INFO,))
+    st = lib().orc_rhs_gated(ctypes.byref(params(p)), _dptr(q), _dptr(th), float(delta), _dptr(out),
+                             dec.ctypes.data_as(ctypes.c_void_p), info.ctypes.data_as(ctypes.c_void_p))
+    _check(st, "rhs_gated", allow_nonphysical)
+    return out, dec, info
+
+
 def rhs_points(p: dict, q: np.ndarray, cells: np.ndarray) -> np.ndarray:
     """L(q) at flat cell indices ``cells``; returns [len(cells), neq]."""
     q = np.ascontiguousarray(q, dtype=np.float64)
@@ -237,6 +258,14 @@ def weno5_cell(v5, eps: float = 1e-6):
     v = np.ascontiguousarray(v5, dtype=np.float64)
     vm, vp = ctypes.c_double(), ctypes.c_double()
     lib().orc_weno5_cell(float(eps), _dptr(v), ctypes.byref(vm), ctypes.byref(vp))
+    return vm.value, vp.value
+
+
+def linear5_cell(v5):
+    """Linear-weight face values (v_{i+1/2}^-, v_{i-1/2}^+) of the middle cell of v5."""
+    v = np.ascontiguousarray(v5, dtype=np.float64)
+    vm, vp = ctypes.c_double(), ctypes.c_double()
+    lib().orc_linear5_cell(_dptr(v), ctypes.byref(vm), ctypes.byref(vp))
     return vm.value, vp.value
 
 
@@ -324,11 +353,22 @@ def mlp_adam(theta, g, m, v, t: int, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
     return th, mm, vv
 
 
-def mlp_normalise(v5) -> np.ndarray:
+GATE_FLOOR = 1e-4   # the gated form's relative round-off floor (the library's MFC_GATE_FLOOR)
+
+
+def mlp_normalise(v5, delta: float = GATE_FLOOR) -> np.ndarray:
+    """Normalised sensor stencil (v_k - v_2)/max_j |v_j - v_2|; zeros when the
+    stencil is flat (variation at most delta |v_2|)."""
     v = np.ascontiguousarray(v5, dtype=np.float64)
     x = np.empty(5)
-    lib().mlp_normalise(_dptr(v), _dptr(x))
+    lib().mlp_normalise(_dptr(v), float(delta), _dptr(x))
     return x
+
+
+def is_flat(v5, delta: float = GATE_FLOOR) -> bool:
+    v = np.ascontiguousarray(v5, dtype=np.float64)
+    x = np.empty(5)
+    return lib().mlp_normalise(_dptr(v), float(delta), _dptr(x)) == 0
 
 
 def weno5_weights(v5, eps: float = 1e-6):
@@ -338,12 +378,15 @@ def weno5_weights(v5, eps: float = 1e-6):
     return wm, wp
 
 
-def troubled(w5, eps: float = 1e-6, tau: float = 0.1) -> bool:
+def troubled(w5, eps: float = 1e-6, tau: float = 0.1, delta: float = GATE_FLOOR) -> bool:
     """Troubled-cell label of one cell from its primitive stencils w5[f][5]:
-    some field's nonlinear WENO weight departs from its linear weight by more
-    than tau (relative) at either face."""
+    some field whose stencil is not flat (variation above delta of its
+    centre value) has a nonlinear WENO weight departing from its linear
+    weight by more than tau (relative) at either face."""
     dm, dp = np.array([0.1, 0.6, 0.3]), np.array([0.3, 0.6, 0.1])
     for v in np.asarray(w5):
+        if is_flat(v, delta):
+            continue
         wm, wp = weno5_weights(v, eps)
         if max(np.max(np.abs(wm - dm) / dm), np.max(np.abs(wp - dp) / dp)) > tau:
             return True

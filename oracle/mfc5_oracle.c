@@ -426,6 +426,128 @@ static void weno(const grid* g, const double* v, double* vm, double* vp) {
         weno5(g->eps, v, vm, vp);
 }
 
+/* ---- MLP-gated reconstruction (the gated form; no counterpart in the paper)
+ * The gated form of the solver reconstructs smooth cells with the linear
+ * weights and troubled cells with WENO5-JS, a small network deciding which
+ * is which.  Per cell and direction two sensor stencils are read from the
+ * primitives of the five stencil cells: the mixture density
+ * alpha1 rho1 + alpha2 rho2 and the pressure.  A sensor stencil s is flat
+ * when max_k |s_k - s_2| <= delta |s_2| (a round-off floor: below it the
+ * linear and the WENO face values differ by at most about 3 delta |s_2|);
+ * a flat stencil counts as smooth.  Otherwise it is normalised,
+ * x_k = (s_k - s_2) / max_j |s_j - s_2|, and the network's logit z(x)
+ * (mlp_oracle.c) decides: smooth when z < 0.  A cell whose two sensors are
+ * smooth is reconstructed with the linear weights for every primitive field,
+ * unless one of its two linear face states is non-physical -- rho <= 0,
+ * alpha1 outside [0, 1] or (Gamma + 1) p + Pi <= 0 -- when WENO5-JS is used
+ * instead (fallback); every other cell with WENO5-JS.  Two fluids only. */
+typedef struct {
+    const double* theta;  /* network parameters (1281, mlp_oracle.c layout) */
+    double delta;         /* round-off floor of the flat test */
+    signed char* dec;     /* out, per direction and cell: 0 WENO, 1 linear, 2 fallback to WENO */
+    double* info;         /* out (or NULL), per direction and cell, GATE_INFO values: z of the
+                             density and of the pressure stencil (NaN where flat), max_k|s_k - s_2|
+                             / (delta |s_2|) of both, and the admissibility margin of the linear
+                             faces (NaN where the cell is not smooth) */
+} gate_ctx;
+
+#define GATE_INFO 5
+
+void mlp_forward(const double* th, const double* x, long n, double* z);   /* mlp_oracle.c */
+int mlp_normalise(const double* v5, double delta, double* x);            /* mlp_oracle.c */
+
+/* Linear-weight (fifth-order upwind) face values: the WENO5 candidates of
+ * weno5 combined with the linear weights themselves. */
+static void linear5(const double* v, double* vm, double* vp) {
+    double p0 = (2.0 * v[0] - 7.0 * v[1] + 11.0 * v[2]) / 6.0;
+    double p1 = (-v[1] + 5.0 * v[2] + 2.0 * v[3]) / 6.0;
+    double p2 = (2.0 * v[2] + 5.0 * v[3] - v[4]) / 6.0;
+    *vm = 0.1 * p0 + 0.6 * p1 + 0.3 * p2;
+    p0 = (-v[0] + 5.0 * v[1] + 2.0 * v[2]) / 6.0;
+    p1 = (2.0 * v[1] + 5.0 * v[2] - v[3]) / 6.0;
+    p2 = (11.0 * v[2] - 7.0 * v[3] + 2.0 * v[4]) / 6.0;
+    *vp = 0.3 * p0 + 0.6 * p1 + 0.1 * p2;
+}
+
+/* One sensor stencil: 1 when it counts as smooth.  *z: the logit (NaN when
+ * flat); *ratio: max_k |s_k - s_2| / (delta |s_2|) (flat iff <= 1). */
+static int sensor_smooth(const gate_ctx* G, const double* s, double* z, double* ratio) {
+    double m = 0.0;
+    for (int k = 0; k < 5; k++) {
+        double d = fabs(s[k] - s[2]);
+        if (d > m) m = d;
+    }
+    double fl = G->delta * fabs(s[2]);
+    *ratio = fl > 0.0 ? m / fl : (m > 0.0 ? INFINITY : 0.0);
+    double x[5];
+    if (!mlp_normalise(s, G->delta, x)) {
+        *z = NAN;
+        return 1;
+    }
+    mlp_forward(G->theta, x, 1, z);
+    return *z < 0.0;
+}
+
+/* A linear face state is usable when rho > 0, 0 <= alpha1 <= 1 and
+ * (Gamma + 1) p + Pi > 0.  *margin (> 0 inside, < 0 outside, 0 on the
+ * boundary): the smallest of rho/(|a1r1| + |a2r2|), alpha1, 1 - alpha1 and
+ * ((Gamma + 1) p + Pi)/((Gamma + 1)|p| + |Pi|). */
+static int face_admissible(const grid* g, const double* w, double* margin) {
+    double rho = w[0] + w[1];
+    double a1 = w[IA(g)];
+    double G, Pi;
+    mixture(g, &w[IA(g)], &G, &Pi);
+    double c = (G + 1.0) * w[IE(g)] + Pi;
+    double m = rho / (fabs(w[0]) + fabs(w[1]));
+    if (a1 < m) m = a1;
+    if (1.0 - a1 < m) m = 1.0 - a1;
+    double mc = c / ((G + 1.0) * fabs(w[IE(g)]) + fabs(Pi));
+    if (mc < m) m = mc;
+    *margin = m;
+    return rho > 0.0 && a1 >= 0.0 && a1 <= 1.0 && c > 0.0;
+}
+
+/* Reconstruction of cell j (both faces, every field) from the pencil rows
+ * W5 (cells j-2 .. j+2) under the gate; returns the decision code. */
+static int gated_cell(const grid* g, const gate_ctx* G, const double* W5, double* vm, double* vp, double* info) {
+    int neq = g->neq;
+    double sr[5], sp[5], zr, zp, rr, rp;
+    for (int s = 0; s < 5; s++) {
+        sr[s] = W5[s * neq + 0] + W5[s * neq + 1];
+        sp[s] = W5[s * neq + IE(g)];
+    }
+    int smooth_r = sensor_smooth(G, sr, &zr, &rr);
+    int smooth_p = sensor_smooth(G, sp, &zp, &rp);
+    int code = 0;
+    double adm = NAN;
+    if (smooth_r && smooth_p) {
+        for (int f = 0; f < neq; f++) {
+            double v[5];
+            for (int s = 0; s < 5; s++) v[s] = W5[s * neq + f];
+            linear5(v, &vm[f], &vp[f]);
+        }
+        double mm, mp;
+        int ok = face_admissible(g, vm, &mm) & face_admissible(g, vp, &mp);
+        adm = mm < mp ? mm : mp;
+        code = ok ? 1 : 2;
+    }
+    if (code != 1) {
+        for (int f = 0; f < neq; f++) {
+            double v[5];
+            for (int s = 0; s < 5; s++) v[s] = W5[s * neq + f];
+            weno5(g->eps, v, &vm[f], &vp[f]);
+        }
+    }
+    if (info) {
+        info[0] = zr;
+        info[1] = zp;
+        info[2] = rr;
+        info[3] = rp;
+        info[4] = adm;
+    }
+    return code;
+}
+
 /* ---- HLLC (Sec. II-B; Toro's three-wave approximate solver) -------------- */
 
 typedef struct {
@@ -567,7 +689,7 @@ static int cell_dir(const grid* g, int d, long i, const double* W7, double* L) {
 /* Full RHS for direction d over all pencils, computing each face once.
  * Returns 1 when a cell (rho <= 0) or a face state (rho <= 0, c^2 <= 0) of
  * the stencils was non-physical. */
-static int rhs_dir(const grid* g, int d, const double* q, double* rhs, int first,
+static int rhs_dir(const grid* g, int d, const double* q, double* rhs, int first, const gate_ctx* gate,
                    double* W, double* VM, double* VP, double* FF, double* UF) {
     int neq = g->neq;
     long nd = g->n[d];
@@ -581,8 +703,17 @@ static int rhs_dir(const grid* g, int d, const double* q, double* rhs, int first
                 long src = bc_map(j, nd, g->periodic[d]);
                 bad |= load_prim(g, q, base + src * g->stride[d], &W[(j + 3) * neq]);
             }
-            /* WENO at cells -1 .. nd (slot = j + 1) */
+            /* WENO (or, under a gate, the gated reconstruction) at cells
+             * -1 .. nd (slot = j + 1) */
             for (long j = -1; j < nd + 1; j++) {
+                if (gate) {
+                    long cell = base + bc_map(j, nd, g->periodic[d]) * g->stride[d];
+                    int inside = j >= 0 && j < nd;
+                    double* info = inside && gate->info ? &gate->info[((long)d * g->ncell + cell) * GATE_INFO] : NULL;
+                    int code = gated_cell(g, gate, &W[(j + 1) * neq], &VM[(j + 1) * neq], &VP[(j + 1) * neq], info);
+                    if (inside) gate->dec[(long)d * g->ncell + cell] = (signed char)code;
+                    continue;
+                }
                 for (int f = 0; f < neq; f++) {
                     double v[5];
                     for (int s = 0; s < 5; s++) v[s] = W[(j + 1 + s) * neq + f];
@@ -613,7 +744,7 @@ static int rhs_dir(const grid* g, int d, const double* q, double* rhs, int first
     return bad;
 }
 
-static int rhs_all(const grid* g, const double* q, double* rhs) {
+static int rhs_all(const grid* g, const double* q, double* rhs, const gate_ctx* gate) {
     long nmax = 1;
     for (int d = 0; d < g->ndim; d++)
         if (g->n[d] > nmax) nmax = g->n[d];
@@ -628,7 +759,7 @@ static int rhs_all(const grid* g, const double* q, double* rhs) {
         return ORC_ENOMEM;
     }
     int bad = 0;
-    for (int d = 0; d < g->ndim; d++) bad |= rhs_dir(g, d, q, rhs, d == 0, W, VM, VP, FF, UF);
+    for (int d = 0; d < g->ndim; d++) bad |= rhs_dir(g, d, q, rhs, d == 0, gate, W, VM, VP, FF, UF);
     free(W); free(VM); free(VP); free(FF); free(UF);
     for (long i = 0; i < (long)neq * g->ncell; i++)
         if (isnan(rhs[i]) || isinf(rhs[i])) bad = 1;
@@ -677,7 +808,28 @@ int orc_rhs(const orc_params* p, const double* q, double* rhs) {
     grid g;
     int st = make_grid(p, &g);
     if (st) return st;
-    st = rhs_all(&g, q, rhs);
+    st = rhs_all(&g, q, rhs, NULL);
+    free_grid(&g);
+    return st;
+}
+
+/* L(q) of the gated form: the right-hand side with each cell's
+ * reconstruction chosen by the gate (see gated_cell), network parameters
+ * theta, round-off floor delta.  dec receives ndim * ncell decision codes
+ * [direction][cell] (0 WENO, 1 linear, 2 fallback); info, if not NULL,
+ * ndim * ncell * GATE_INFO values.  Two fluids, WENO5, uniform grids. */
+int orc_rhs_gated(const orc_params* p, const double* q, const double* theta, double delta, double* rhs,
+                  signed char* dec, double* info) {
+    grid g;
+    int st = make_grid(p, &g);
+    if (st) return st;
+    if (g.nf != 2 || g.order != 5 || g.stretched[0] || g.stretched[1] || g.stretched[2] || !theta || !dec ||
+        !(delta >= 0.0)) {
+        free_grid(&g);
+        return ORC_EINVAL;
+    }
+    gate_ctx G = {theta, delta, dec, info};
+    st = rhs_all(&g, q, rhs, &G);
     free_grid(&g);
     return st;
 }
@@ -762,11 +914,11 @@ int orc_step_dt(const orc_params* p, double* q, double dt) {
         return ORC_ENOMEM;
     }
     int bad = 0;
-    bad |= rhs_all(&g, q, L) != ORC_OK;
+    bad |= rhs_all(&g, q, L, NULL) != ORC_OK;
     for (long i = 0; i < m; i++) q1[i] = q[i] + dt * L[i];
-    bad |= rhs_all(&g, q1, L) != ORC_OK;
+    bad |= rhs_all(&g, q1, L, NULL) != ORC_OK;
     for (long i = 0; i < m; i++) q2[i] = 0.75 * q[i] + 0.25 * (q1[i] + dt * L[i]);
-    bad |= rhs_all(&g, q2, L) != ORC_OK;
+    bad |= rhs_all(&g, q2, L, NULL) != ORC_OK;
     for (long i = 0; i < m; i++) q[i] = (1.0 / 3.0) * q[i] + (2.0 / 3.0) * (q2[i] + dt * L[i]);
     free(L); free(q1); free(q2);
     free_grid(&g);
@@ -819,6 +971,10 @@ void orc_weno5_weights(double eps, const double* v, double* wm, double* wp) {
 void orc_weno5_cell(double eps, const double* v5, double* vm, double* vp) { weno5(eps, v5, vm, vp); }
 
 void orc_weno3_cell(double eps, const double* v5, double* vm, double* vp) { weno3(eps, v5, vm, vp); }
+
+/* Linear-weight face values of the middle cell of v5 (the gated form's
+ * reconstruction of smooth cells). */
+void orc_linear5_cell(const double* v5, double* vm, double* vp) { linear5(v5, vm, vp); }
 
 /* Non-uniform WENO5 table (NT doubles, layout of cell_table) of a cell from
  * the widths w5 of cells i-2 .. i+2; returns 1 if degenerate. */

@@ -107,12 +107,19 @@ void mlp_adam(double* th, const double* g, double* m, double* v, int t, double l
     }
 }
 
-/* Normalised sensor stencil: (v_k - v_2) / (max_k |v_k - v_2| + 1e-12). */
-void mlp_normalise(const double* v5, double* x) {
+/* Normalised sensor stencil x_k = (v_k - v_2) / max_j |v_j - v_2|.  A stencil
+ * whose variation max_j |v_j - v_2| is at most delta |v_2| (a relative
+ * round-off floor) is flat: x = 0 and the return value is 0; otherwise 1. */
+int mlp_normalise(const double* v5, double delta, double* x) {
     double m = 0.0;
     for (int k = 0; k < 5; k++) {
         double d = fabs(v5[k] - v5[2]);
         if (d > m) m = d;
     }
-    for (int k = 0; k < 5; k++) x[k] = (v5[k] - v5[2]) / (m + 1e-12);
+    if (!(m > delta * fabs(v5[2]))) {
+        for (int k = 0; k < 5; k++) x[k] = 0.0;
+        return 0;
+    }
+    for (int k = 0; k < 5; k++) x[k] = (v5[k] - v5[2]) / m;
+    return 1;
 }

@@ -80,8 +80,15 @@ def test_adam_first_step_is_lr_sign():
 
 def test_normalised_stencil():
     x = O.mlp_normalise([1.0, 2.0, 3.0, 5.0, 3.5])
-    np.testing.assert_allclose(x, [-1.0, -0.5, 0.0, 1.0, 0.25], rtol=1e-11)
+    assert np.array_equal(x, [-1.0, -0.5, 0.0, 1.0, 0.25])       # exact: divisions by 2
     assert np.all(O.mlp_normalise([7.0] * 5) == 0.0)
+    # the round-off floor: variation 0.9e-4 of the centre value is flat, 1.1e-4 is not
+    s = 1e5 * np.array([1.0, 1.0, 1.0, 1.0 + 0.9e-4, 1.0])
+    assert O.is_flat(s) and np.all(O.mlp_normalise(s) == 0.0)
+    s = 1e5 * np.array([1.0, 1.0, 1.0, 1.0 + 1.1e-4, 1.0])
+    assert not O.is_flat(s)
+    np.testing.assert_allclose(O.mlp_normalise(s), [0.0, 0.0, 0.0, 1.0, 0.0], atol=1e-12)
+    assert O.is_flat(s, delta=2e-4)
 
 
 def test_labels_from_weno_weights():
@@ -92,5 +99,12 @@ def test_labels_from_weno_weights():
     assert not O.troubled(smooth)
     jump = [np.array([1.0, 1.0, 1.0, 5.0, 5.0]), np.full(5, 1e5)]
     assert O.troubled(jump)
+    # a pressure stencil wiggling at round-off (1e-9 of 1e5: WENO's absolute
+    # epsilon reads it as non-smooth) is below the floor and not troubled
+    wiggle = [np.full(5, 1.2), 1e5 * (1.0 + 1e-9 * np.array([1.0, -1.0, 1.0, -1.0, 1.0]))]
+    wm, _ = O.weno5_weights(wiggle[1])
+    assert np.max(np.abs(wm - [0.1, 0.6, 0.3]) / [0.1, 0.6, 0.3]) > 0.1
+    assert not O.troubled(wiggle)
+    assert O.troubled(wiggle, delta=0.0)
     wm, wp = O.weno5_weights(np.array([1.0, 1.0, 1.0, 5.0, 5.0]))
     assert wm[0] > 0.99 and wp[0] > 0.99

@@ -13,6 +13,7 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "mfc5_oracle.c")
+MLP_SRC = os.path.join(ROOT, "oracle", "mlp_oracle.c")
 
 MUTATIONS = {
     "drop_alpha_source": ("L[IA(g) + k] = L[IA(g) + k] + ak * (UF[i + 1] - UF[i]) / dx;", "L[IA(g) + k] = L[IA(g) + k];"),
@@ -65,23 +66,40 @@ MUTATIONS = {
                       "for (int i = 0; i < g->nf - 1; i++) F[IA(g) + i] = K->a[0] * un;"),
     "nu_wavespeed_width": ("(fabs(w[IU(&g) + d]) + cs) / cell_width(&g, d, (c / g.stride[d]) % g.n[d]);",
                            "(fabs(w[IU(&g) + d]) + cs) / g.dx[d];"),
+    # the gated form's rule
+    "gate_either_sensor": ("if (smooth_r && smooth_p) {", "if (smooth_r || smooth_p) {"),
+    "gate_logit_sign": ("return *z < 0.0;", "return *z > 0.0;"),
+    "gate_linear_weight": ("*vm = 0.1 * p0 + 0.6 * p1 + 0.3 * p2;", "*vm = 0.3 * p0 + 0.6 * p1 + 0.1 * p2;"),
+    "gate_fallback_alpha": ("return rho > 0.0 && a1 >= 0.0 && a1 <= 1.0 && c > 0.0;", "return rho > 0.0 && c > 0.0;"),
+    "gate_pressure_sensor": ("sp[s] = W5[s * neq + IE(g)];", "sp[s] = W5[s * neq + IU(g)];"),
+    "gate_density_sensor": ("sr[s] = W5[s * neq + 0] + W5[s * neq + 1];", "sr[s] = W5[s * neq + 0];"),
 }
 
 
-@pytest.mark.parametrize("name", sorted(MUTATIONS))
+# mistakes in the network's input normalisation (mlp_oracle.c)
+MLP_MUTATIONS = {
+    "gate_floor_ignored": ("if (!(m > delta * fabs(v5[2]))) {", "if (!(m > 0.0)) {"),
+    "gate_norm_centre": ("x[k] = (v5[k] - v5[2]) / m;", "x[k] = (v5[k] - v5[0]) / m;"),
+    "gate_norm_reversed": ("x[k] = (v5[k] - v5[2]) / m;", "x[k] = (v5[4 - k] - v5[2]) / m;"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS) + sorted(MLP_MUTATIONS))
 def test_planted_mistake_is_caught(name, tmp_path):
-    before, after = MUTATIONS[name]
-    src = open(SRC).read()
+    target = SRC if name in MUTATIONS else MLP_SRC
+    before, after = MUTATIONS[name] if name in MUTATIONS else MLP_MUTATIONS[name]
+    src = open(target).read()
     assert src.count(before) >= 1, "mutation anchor no longer in the oracle source"
     csrc = tmp_path / "mutant.c"
     csrc.write_text(src.replace(before, after))
+    other = MLP_SRC if target == SRC else SRC
     so = tmp_path / "libmutant.so"
     subprocess.run(["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o",
-                    str(so), str(csrc), "-lm"], check=True)
+                    str(so), str(csrc), other, "-lm"], check=True)
     env = dict(os.environ, MFC5_ORACLE_LIB=str(so))
     suites = [os.path.join(ROOT, "tests", f) for f in
               ("test_oracle_elements.py", "test_oracle_physics.py", "test_oracle_stretched.py",
-               "test_oracle_nfluids.py")]
+               "test_oracle_nfluids.py", "test_oracle_gate.py", "test_oracle_mlp.py")]
     r = subprocess.run([sys.executable, "-m", "pytest", *suites, "-x", "-q", "-p", "no:cacheprovider",
                         "-m", "not gpu"], cwd=ROOT, env=env, capture_output=True, text=True,
                        timeout=600)
