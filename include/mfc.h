@@ -138,14 +138,20 @@ int mfc_set_timing(mfc_ctx* ctx, int enable);
 int mfc_kernel_time(mfc_ctx* ctx, int index, const char** name, double* ms, long long* launches);
 
 /* ---- gated form (MFC_GATED): the troubled-cell network ------------------
- * No counterpart in the paper.  A 5 -> 32 -> 32 -> 1 perceptron (ReLU hidden
- * layers, logistic output) reads a normalised 5-cell stencil
- * (v_k - v_i)/(max_k |v_k - v_i| + 1e-12) of one sensor field; a cell is
- * reconstructed with the linear WENO5 weights in a direction when the logit
- * is negative for both the mixture-density and the pressure stencil, and
- * with full WENO5-JS otherwise -- and also whenever a linear face state has
- * rho <= 0, alpha1 outside [0, 1] or (Gamma + 1) p + Pi <= 0.  Parameters
+ * No counterpart in the paper.  Per cell and direction two sensor stencils
+ * are read from the five stencil cells' primitives: the mixture density
+ * alpha1 rho1 + alpha2 rho2 and the pressure.  A sensor stencil s is flat
+ * when max_k |s_k - s_2| <= MFC_GATE_FLOOR |s_2| (a round-off floor) and then
+ * counts as smooth; otherwise a 5 -> 32 -> 32 -> 1 perceptron (ReLU hidden
+ * layers, logistic output; FP32 arithmetic, evaluated on the tensor cores
+ * with every operand split into two f16 halves) reads the normalised stencil
+ * x_k = (s_k - s_2) / max_j |s_j - s_2| and calls it smooth when its logit
+ * is negative.  A cell whose two sensors are smooth is reconstructed with
+ * the linear WENO5 weights in that direction, unless a linear face state has
+ * rho <= 0, alpha1 outside [0, 1] or (Gamma + 1) p + Pi <= 0 (then WENO5-JS,
+ * the fallback); every other cell with full WENO5-JS.  Parameters
  * (MFC_MLP_NPARAMS floats): W1[32][5], b1[32], W2[32][32], b2[32], w3[32], b3. */
+#define MFC_GATE_FLOOR 1e-4
 #define MFC_MLP_NPARAMS 1281
 
 /* Makes direction `dir` (0 <= dir < ndim) non-uniform: `edges` is a host
@@ -174,17 +180,28 @@ int mfc_set_mlp_weights(mfc_ctx* ctx, const float* w, int n);
 int mfc_gate_stats(mfc_ctx* ctx, long long* gated, long long* fallback, long long* cells);
 
 /* Of the cell reconstructions counted by mfc_gate_stats, those whose warp
- * step had exactly flat density and pressure stencils in all 32 pencils: the
- * network input is then exactly zero and its output, the same for every
- * lane, is taken from one evaluation at zero input instead of being
- * recomputed (same decisions).  MFC_EINVAL on a NULL argument. */
+ * step had flat density and pressure stencils (below the round-off floor) in
+ * all 32 pencils: every one counts as smooth and the network is not
+ * evaluated for that step.  MFC_EINVAL on a NULL argument. */
 int mfc_gate_flat(mfc_ctx* ctx, long long* flat);
+
+/* L(q^n) of a MFC_GATED context as mfc_rhs, and the gate's decision for
+ * every direction and cell: decisions[d * ncells + cell] = 0 (WENO5-JS),
+ * 1 (linear weights) or 2 (called smooth, but a linear face was non-physical:
+ * WENO5-JS).  decisions is host (on_device = 0) or device memory with room
+ * for ndim * ncells bytes.  The first call allocates a device buffer of that
+ * size (MFC_ENOMEM).  MFC_EINVAL for other forms; synchronises the stream. */
+int mfc_gate_rhs(mfc_ctx* ctx, double* rhs, signed char* decisions, int on_device);
 
 /* Labelled training samples from the current state (FP64 WENO5-JS weights):
  * for every direction d and cell c, two samples (mixture-density stencil,
  * pressure stencil), index (d * ncells + c) * 2 + sensor; X[sample][5] the
  * normalised stencil, Y[sample] = 1 when some primitive's nonlinear weight at
- * either face departs from its linear weight by more than tau (relative).
+ * either face departs from its linear weight by more than tau (relative) on
+ * a stencil of that primitive that is not flat (variation above
+ * MFC_GATE_FLOOR of its centre value: below it the two reconstructions differ
+ * by round-off), else 0; a flat sensor stencil, which the gate never shows
+ * the network, gets X = 0 and Y = -1.
  * X, Y are device pointers with room for capacity >= 2 * ndim * ncells
  * samples; *count receives that number.  Synchronises the context stream. */
 int mfc_gate_samples(mfc_ctx* ctx, float* X, float* Y, long long capacity, float tau, long long* count);
@@ -196,7 +213,8 @@ int mfc_gate_samples(mfc_ctx* ctx, float* X, float* Y, long long capacity, float
  * mfc_mlp_adam: one Adam step t (1-based) of theta with moments m, v.
  * mfc_mlp_forward: logits z[n] of X[n][5] (FP32 CUDA cores).
  * mfc_mlp_forward_tc: the same logits as the gated sweep computes them --
- *   both hidden layers on the tensor cores, fp16 operands, FP32 accumulation. */
+ *   every layer on the tensor cores, operands split into two f16 halves
+ *   (hi * hi + lo * hi + hi * lo), FP32 accumulation. */
 int mfc_mlp_nparams(void);
 int mfc_mlp_loss_grad(const float* X, const float* Y, long long n, const float* theta, float pos_weight,
                       float* grad, float* loss, void* cuda_stream);

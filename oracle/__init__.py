@@ -199,7 +199,7 @@ def rhs(p: dict, q: np.ndarray, allow_nonphysical: bool = False) -> np.ndarray:
     return out
 
 
-GATE_INFO = 5   # z_rho, z_p, flat ratios of both sensors, admissibility margin
+GATE_INFO = 8   # z_rho, z_p, flat ratios of both sensors; rho, alpha1, 1 - alpha1, c^2 margins of the linear faces
 
 
 def rhs_gated(p: dict, q: np.ndarray, theta, delta: float, allow_nonphysical: bool = False):

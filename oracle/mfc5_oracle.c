@@ -447,11 +447,13 @@ typedef struct {
     signed char* dec;     /* out, per direction and cell: 0 WENO, 1 linear, 2 fallback to WENO */
     double* info;         /* out (or NULL), per direction and cell, GATE_INFO values: z of the
                              density and of the pressure stencil (NaN where flat), max_k|s_k - s_2|
-                             / (delta |s_2|) of both, and the admissibility margin of the linear
-                             faces (NaN where the cell is not smooth) */
+                             / (delta |s_2|) of both, and, over the two linear faces (NaN where the
+                             cell is not smooth), the smallest rho / (|a1r1| + |a2r2|), alpha1,
+                             1 - alpha1 and ((Gamma + 1) p + Pi) / ((Gamma + 1)|p| + |Pi|): a linear
+                             face is admissible when the first and last are > 0, the middle two >= 0 */
 } gate_ctx;
 
-#define GATE_INFO 5
+#define GATE_INFO 8
 
 void mlp_forward(const double* th, const double* x, long n, double* z);   /* mlp_oracle.c */
 int mlp_normalise(const double* v5, double delta, double* x);            /* mlp_oracle.c */
@@ -489,21 +491,18 @@ static int sensor_smooth(const gate_ctx* G, const double* s, double* z, double* 
 }
 
 /* A linear face state is usable when rho > 0, 0 <= alpha1 <= 1 and
- * (Gamma + 1) p + Pi > 0.  *margin (> 0 inside, < 0 outside, 0 on the
- * boundary): the smallest of rho/(|a1r1| + |a2r2|), alpha1, 1 - alpha1 and
- * ((Gamma + 1) p + Pi)/((Gamma + 1)|p| + |Pi|). */
-static int face_admissible(const grid* g, const double* w, double* margin) {
+ * (Gamma + 1) p + Pi > 0.  m[0..3] receive rho/(|a1r1| + |a2r2|), alpha1,
+ * 1 - alpha1 and ((Gamma + 1) p + Pi)/((Gamma + 1)|p| + |Pi|). */
+static int face_admissible(const grid* g, const double* w, double* m) {
     double rho = w[0] + w[1];
     double a1 = w[IA(g)];
     double G, Pi;
     mixture(g, &w[IA(g)], &G, &Pi);
     double c = (G + 1.0) * w[IE(g)] + Pi;
-    double m = rho / (fabs(w[0]) + fabs(w[1]));
-    if (a1 < m) m = a1;
-    if (1.0 - a1 < m) m = 1.0 - a1;
-    double mc = c / ((G + 1.0) * fabs(w[IE(g)]) + fabs(Pi));
-    if (mc < m) m = mc;
-    *margin = m;
+    m[0] = rho / (fabs(w[0]) + fabs(w[1]));
+    m[1] = a1;
+    m[2] = 1.0 - a1;
+    m[3] = c / ((G + 1.0) * fabs(w[IE(g)]) + fabs(Pi));
     return rho > 0.0 && a1 >= 0.0 && a1 <= 1.0 && c > 0.0;
 }
 
@@ -519,16 +518,16 @@ static int gated_cell(const grid* g, const gate_ctx* G, const double* W5, double
     int smooth_r = sensor_smooth(G, sr, &zr, &rr);
     int smooth_p = sensor_smooth(G, sp, &zp, &rp);
     int code = 0;
-    double adm = NAN;
+    double adm[4] = {NAN, NAN, NAN, NAN};
     if (smooth_r && smooth_p) {
         for (int f = 0; f < neq; f++) {
             double v[5];
             for (int s = 0; s < 5; s++) v[s] = W5[s * neq + f];
             linear5(v, &vm[f], &vp[f]);
         }
-        double mm, mp;
-        int ok = face_admissible(g, vm, &mm) & face_admissible(g, vp, &mp);
-        adm = mm < mp ? mm : mp;
+        double mm[4], mp[4];
+        int ok = face_admissible(g, vm, mm) & face_admissible(g, vp, mp);
+        for (int k = 0; k < 4; k++) adm[k] = mm[k] < mp[k] ? mm[k] : mp[k];
         code = ok ? 1 : 2;
     }
     if (code != 1) {
@@ -543,7 +542,7 @@ static int gated_cell(const grid* g, const gate_ctx* G, const double* W5, double
         info[1] = zp;
         info[2] = rr;
         info[3] = rp;
-        info[4] = adm;
+        for (int k = 0; k < 4; k++) info[4 + k] = adm[k];
     }
     return code;
 }

@@ -6,6 +6,7 @@
 // sweep of a stage applies the stage update, and the last sweep of stage 3
 // reduces the wave speed of the new state.  The launches of one step are
 // captured once into a CUDA graph and replayed.
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stddef.h>
@@ -41,6 +42,7 @@ struct mfc_ctx {
     void* sa;         // stage 1 output (FP64, or FP32 cons + p)
     void* sb;         // stage 2 output
     float* s0;        // mixed form: FP32 copy of q^n with p
+    float* dinc;      // FP32 forms: RK increment D_k (q^(k) = q^n + D_k), neq fields
     void* acc;        // RHS accumulator
     double* tmp64;    // mixed form: FP64 RHS output staging (lazy)
     DevCtrl* ctrl;    // device
@@ -67,6 +69,13 @@ struct mfc_ctx {
     long long hoff[6]; // halo layout: element offset of side (d, s) at 2 d + s, -1 if none
     long long htotal;  // halo buffer elements
     const void* halo_cur;  // halo buffer of the call in progress (sweeps read ghosts there)
+    signed char* dec_dev;  // gated form: per-direction, per-cell decisions of mfc_gate_rhs (lazy)
+    bool dec_on;           // the call in progress records decisions
+    // MFC_TMA_YZ builds, FP32 forms: tensor maps of the stage inputs (s0, sa,
+    // sb) for the y and z sweeps, tmap[2 b + d] (64-byte aligned host
+    // allocation); tma_ok when all were encoded
+    CUtensorMap* tmap;
+    bool tma_ok;
 };
 
 #define CK(call)                                   \
@@ -119,7 +128,7 @@ static int state_fields(const mfc_ctx* c) { return fp32_state(c) ? c->neq + 1 : 
 
 static void free_all(mfc_ctx* c) {
     if (c->gexec) cudaGraphExecDestroy(c->gexec);
-    void* bufs[] = {c->qn, c->sa, c->sb, c->s0, c->acc, c->tmp64, c->ctrl, c->gate_w};
+    void* bufs[] = {c->qn, c->sa, c->sb, c->s0, c->dinc, c->acc, c->tmp64, c->ctrl, c->gate_w, c->dec_dev};
     for (void* b : bufs)
         if (b) cudaFree(b);
     for (int d = 0; d < 3; ++d) {
@@ -128,9 +137,62 @@ static void free_all(mfc_ctx* c) {
             if (b) cudaFree(b);
     }
     if (c->ctrl_h) cudaFreeHost(c->ctrl_h);
+    free(c->tmap);
     for (int i = 0; i <= kMaxTimedLaunches; ++i)
         if (c->ev[i]) cudaEventDestroy(c->ev[i]);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+}
+
+// cuTensorMapEncodeTiled, looked up through the runtime (no link against the
+// driver library).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = NULL;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* f = NULL;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)f;
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// Tensor maps of an FP32 stage buffer [field][z][y][x] as a 4-D tensor
+// (x, y, z, field) with boxes of 32 x-cells by kTmaCells cells along y or z.
+// TMA needs 16-byte row strides: nx a multiple of 4.
+static void setup_tma(mfc_ctx* ctx) {
+    ctx->tma_ok = false;
+    if (!MFC_TMA_YZ || !fp32_state(ctx) || ctx->ndim < 2 || ctx->n[0] % 4 != 0) return;
+    EncodeTiledFn enc = encode_tiled();
+    if (!enc) return;
+    ctx->tmap = (CUtensorMap*)aligned_alloc(64, 6 * sizeof(CUtensorMap));
+    if (!ctx->tmap) return;
+    memset(ctx->tmap, 0, 6 * sizeof(CUtensorMap));
+    void* bufs[3] = {ctx->s0, ctx->sa, ctx->sb};
+    const cuuint64_t dims[4] = {(cuuint64_t)ctx->n[0], (cuuint64_t)ctx->n[1], (cuuint64_t)ctx->n[2],
+                                (cuuint64_t)state_fields(ctx)};
+    const cuuint64_t strides[3] = {(cuuint64_t)ctx->n[0] * 4, (cuuint64_t)ctx->n[0] * ctx->n[1] * 4,
+                                   (cuuint64_t)ctx->ncell * 4};
+    const cuuint32_t ones[4] = {1, 1, 1, 1};
+    const cuuint32_t box[2][4] = {{32, kTmaCells, 1, 1}, {32, 1, kTmaCells, 1}};
+    for (int b = 0; b < 3; ++b)
+        for (int d = 0; d < 2; ++d) {
+            if (d == 1 && ctx->ndim < 3) continue;
+            if (enc(&ctx->tmap[2 * b + d], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, bufs[b], dims, strides, box[d], ones,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+                return;
+        }
+    ctx->tma_ok = true;
 }
 
 extern "C" int mfc_create(const mfc_params* params, void* cuda_stream, mfc_ctx** out) {
@@ -176,7 +238,8 @@ extern "C" int mfc_create(const mfc_params* params, void* cuda_stream, mfc_ctx**
               cudaMalloc((void**)&ctx->ctrl, sizeof(DevCtrl)) == cudaSuccess &&
               cudaMallocHost((void**)&ctx->ctrl_h, sizeof(DevCtrl)) == cudaSuccess;
     if (ok && fp32_state(ctx))
-        ok = cudaMalloc((void**)&ctx->s0, nc * sfield * sizeof(float)) == cudaSuccess;
+        ok = cudaMalloc((void**)&ctx->s0, nc * sfield * sizeof(float)) == cudaSuccess &&
+             cudaMalloc((void**)&ctx->dinc, nc * ctx->neq * sizeof(float)) == cudaSuccess;
     if (ok && ctx->form == FORM_GATED)
         ok = cudaMalloc((void**)&ctx->gate_w, kGateParams * sizeof(float)) == cudaSuccess;
     for (int i = 0; ok && i <= kMaxTimedLaunches; ++i) ok = cudaEventCreate(&ctx->ev[i]) == cudaSuccess;
@@ -186,6 +249,7 @@ extern "C" int mfc_create(const mfc_params* params, void* cuda_stream, mfc_ctx**
         free(ctx);
         return MFC_ENOMEM;
     }
+    setup_tma(ctx);
     memset(ctx->ctrl_h, 0, sizeof(DevCtrl));
     if (cudaMemcpyAsync(ctx->ctrl, ctx->ctrl_h, sizeof(DevCtrl), cudaMemcpyHostToDevice, ctx->stream) !=
             cudaSuccess ||
@@ -223,6 +287,7 @@ static SweepArgs base_args(mfc_ctx* ctx) {
     a.acc = ctx->acc;
     a.qn = ctx->qn;
     a.gate_w = ctx->gate_w;
+    a.dinc = ctx->dinc;
     for (int d = 0; d < 3; ++d) {
         a.cw[d] = ctx->gw[d];
         a.crw[d] = ctx->grw[d];
@@ -240,6 +305,11 @@ static cudaError_t launch_sweep(mfc_ctx* ctx, int dir, int mode, SweepArgs a, cu
         if (ctx->nbr[dir][0]) a.hlo = h + ctx->hoff[2 * dir] * el;
         if (ctx->nbr[dir][1]) a.hhi = h + ctx->hoff[2 * dir + 1] * el;
         a.hplane = ctx->ncell / ctx->n[dir];
+    }
+    if (ctx->dec_on) a.gate_dec = ctx->dec_dev + (long long)dir * ctx->ncell;
+    if (ctx->tma_ok && dir >= 1 && !ctx->gtab[dir]) {
+        const int bi = a.qin == ctx->s0 ? 0 : (a.qin == ctx->sa ? 1 : (a.qin == ctx->sb ? 2 : -1));
+        if (bi >= 0) a.tmap = &ctx->tmap[2 * bi + dir - 1];
     }
     switch (ctx->form) {
         case FORM_FP64_EXACT: return launch_sweep_fp64x(ctx->ndim, dir, mode, a, s);
@@ -417,6 +487,25 @@ extern "C" int mfc_rhs(mfc_ctx* ctx, double* rhs, int on_device) {
     if (!ctx || !rhs) return MFC_EINVAL;
     if (has_neighbours(ctx)) return MFC_ESTATE;   // a block's ghosts: mfc_block_rhs
     return rhs_impl(ctx, rhs, on_device);
+}
+
+extern "C" int mfc_gate_rhs(mfc_ctx* ctx, double* rhs, signed char* decisions, int on_device) {
+    if (!ctx || !rhs || !decisions) return MFC_EINVAL;
+    if (ctx->form != FORM_GATED) return MFC_EINVAL;
+    if (has_neighbours(ctx)) return MFC_ESTATE;
+    const size_t nb = (size_t)ctx->ndim * ctx->ncell;
+    if (!ctx->dec_dev && cudaMalloc((void**)&ctx->dec_dev, nb) != cudaSuccess) {
+        cudaGetLastError();
+        return MFC_ENOMEM;
+    }
+    ctx->dec_on = true;
+    int st = rhs_impl(ctx, rhs, on_device);
+    ctx->dec_on = false;
+    if (st != MFC_OK && st != MFC_ENONPHYSICAL) return st;
+    CK(cudaMemcpyAsync(decisions, ctx->dec_dev, nb, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return st;
 }
 
 extern "C" int mfc_max_wavespeed(mfc_ctx* ctx, double* s) {

@@ -76,6 +76,7 @@ struct SweepArgs {
     const double* qn;     // RK base state q^n (FP64)
     void* qout;           // stage output (FP64 or FP32), or FP64 RHS output
     void* qout2;          // mixed form, stage 3: FP32 copy of q^{n+1} with p
+    float* dinc;          // FP32 forms: the RK increment D_k of the stage (neq fields), read and rewritten
     int n[3];
     long long ncell;
     double inv_dx[3];     // n/(hi - lo) per direction (reformulated forms)
@@ -102,7 +103,26 @@ struct SweepArgs {
     const void* hlo;      // cells -3 .. -1 (layer l = cell l - 3)
     const void* hhi;      // cells n .. n + 2 (layer l = cell n + l)
     long long hplane;
+    // gated form: per-cell decisions of this sweep's direction (0 WENO,
+    // 1 linear, 2 fallback to WENO), or null
+    signed char* gate_dec;
+    // FP32 y/z sweeps staged through TMA (MFC_TMA_YZ builds): host address of
+    // the CUtensorMap of the stage input for this direction, or null
+    const void* tmap;
 };
+
+// TMA staging of the FP32 forms' y and z sweeps: 0 = direct loads (default),
+// 1 = interior pencil segments staged through shared memory by
+// cp.async.bulk.tensor, kTmaCells cells per box, double-buffered per warp.
+#ifndef MFC_TMA_YZ
+#define MFC_TMA_YZ 0
+#endif
+// FP32 x sweeps: 1 = 16-byte row loads of four cells per field (rows of a
+// multiple of 4 cells), 0 = one cell per load
+#ifndef MFC_XVEC
+#define MFC_XVEC 1
+#endif
+constexpr int kTmaCells = 4;
 
 // Arithmetic forms of the sweep kernels:
 //   FORM_FP64_FAST   FP64, formulas reorganised for fewer FP64 instructions

@@ -4,11 +4,13 @@
 //
 // Network: 5 -> 32 -> 32 -> 1, ReLU hidden layers, logistic output; input is
 // a 5-cell stencil of one sensor field (mixture density or pressure)
-// normalised as (v_k - v_i)/(max_k |v_k - v_i| + 1e-12).  Parameters (1281
-// floats): W1[32][5], b1[32], W2[32][32], b2[32], w3[32], b3.  Label of a
-// cell and direction: troubled (1) when, for some primitive field, a
-// nonlinear WENO5-JS weight at either face departs from its linear weight by
-// more than tau relative; smooth (0) otherwise.  Loss: weighted binary
+// normalised as (v_k - v_i)/max_k |v_k - v_i|; a stencil whose variation is
+// at most MFC_GATE_FLOOR |v_i| is flat and never shown to the network.
+// Parameters (1281 floats): W1[32][5], b1[32], W2[32][32], b2[32], w3[32],
+// b3.  Label of a cell and direction: troubled (1) when, for some primitive
+// field whose stencil is not flat, a nonlinear WENO5-JS weight at either
+// face departs from its linear weight by more than tau relative; smooth (0)
+// otherwise (below the floor the two reconstructions differ by round-off).  Loss: weighted binary
 // cross-entropy on the logit (positive-class weight wp).  Training is FP32;
 // the samples are formed in FP64 from reference-order primitives (this file is
 // built with -fmad=false).
@@ -212,6 +214,9 @@ __global__ void gate_samples_kernel(const double* __restrict__ q, int n0, int n1
         for (int f = 0; f < FL::NEQ; ++f) {
             const double c13 = 13.0 / 12.0;
             double v0 = w[0][f], v1 = w[1][f], v2 = w[2][f], v3 = w[3][f], v4 = w[4][f];
+            double mf = 0.0;
+            for (int k = 0; k < 5; ++k) mf = fmax(mf, fabs(w[k][f] - v2));
+            if (!(mf > MFC_GATE_FLOOR * fabs(v2))) continue;   // flat: round-off only
             double b[3];
             b[0] = c13 * (v0 - 2.0 * v1 + v2) * (v0 - 2.0 * v1 + v2) + 0.25 * (v0 - 4.0 * v1 + 3.0 * v2) * (v0 - 4.0 * v1 + 3.0 * v2);
             b[1] = c13 * (v1 - 2.0 * v2 + v3) * (v1 - 2.0 * v2 + v3) + 0.25 * (v1 - v3) * (v1 - v3);
@@ -234,8 +239,9 @@ __global__ void gate_samples_kernel(const double* __restrict__ q, int n0, int n1
             for (int k = 0; k < 5; ++k) v[k] = sensor == 0 ? w[k][0] + w[k][1] : w[k][FL::IE];
             for (int k = 0; k < 5; ++k) m = fmax(m, fabs(v[k] - v[2]));
             long long sidx = t * 2 + sensor;
-            for (int k = 0; k < 5; ++k) X[sidx * 5 + k] = float((v[k] - v[2]) / (m + 1e-12));
-            Y[sidx] = troubled ? 1.f : 0.f;
+            const bool live = m > MFC_GATE_FLOOR * fabs(v[2]);
+            for (int k = 0; k < 5; ++k) X[sidx * 5 + k] = live ? float((v[k] - v[2]) / m) : 0.f;
+            Y[sidx] = !live ? -1.f : (troubled ? 1.f : 0.f);
         }
     }
 }

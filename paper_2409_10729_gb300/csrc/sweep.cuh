@@ -21,10 +21,14 @@
 // a segment.  Boundary ghosts come from index clamping (transmissive) or
 // wrapping (periodic) in the loads.
 #pragma once
+#include <cuda.h>
 #include <cuda_fp16.h>
+
+#include <string.h>
 
 #include <type_traits>
 
+#include "mfc.h"
 #include "mfc_internal.cuh"
 #include "physics_exact.cuh"
 
@@ -194,55 +198,84 @@ struct XStage {
 template <int FORM>
 using FormReal = typename std::conditional<FORM == FORM_MIXED || FORM == FORM_GATED, float, double>::type;
 
-// ---- gate network on the tensor cores -------------------------------------
+// ---- gate network on the tensor cores, FP32-accurate ----------------------
 // A warp evaluates the network for its 32 cells x 2 sensors = 64 samples at
-// once: layer 1 (5 -> 32, K padded to 8) as 4x4 mma.m16n8k8 and layer 2
-// (32 -> 32) as 4x4x2 mma.m16n8k16, fp16 operands with FP32 accumulation;
-// the fragments of layer 1's result are layer 2's A fragments as they stand.
-// The 32 -> 1 output is a dot product of the layer-2 fragments with w3,
-// reduced over the four lanes of a fragment group.
+// once, as four 16-row m16n8k16 tiles (rows 0-31: the warp's density
+// stencils, 32-63: its pressure stencils), f16 operands, FP32 accumulation.
+// To keep FP32 accuracy every FP32 operand v (inputs, weights, hidden
+// activations) is split into two f16 halves, v = hi + lo with hi = f16(v)
+// and lo = f16(v - hi), and each product is formed as hi*hi + lo*hi + hi*lo:
+// products of f16 values are exact in FP32, the neglected lo*lo is below
+// 2^-22 of the product, and a lo below the f16 normal range keeps an
+// absolute error under 2^-25.  Layer 1 (5 -> 32) packs the three terms into
+// one K = 16 contraction -- A row = [x_hi, x_lo, x_hi, 0], B column =
+// [w_hi; w_hi; w_lo; 0]; layers 2 (32 -> 32) and 3 (32 -> 1, w3 in every
+// column) run the three terms as six K = 16 MMAs per output tile.  Biases
+// enter as the accumulator input; one layer's accumulator fragments are the
+// next layer's A fragments, so activations never leave registers.
 struct GateSmem {
-    unsigned w1f[4][32];       // layer-1 B fragments, per n-tile and lane
-    unsigned w2f[2][4][32][2]; // layer-2 B fragments, per k-tile, n-tile, lane
-    unsigned w3f[2][32][2];    // layer-3 B fragments (w3 in every column), per k-tile, lane
+    unsigned w1f[4][32][2];        // layer-1 B fragments (K = 16 packing), per n-tile and lane
+    unsigned w2h[2][4][32][2];     // layer-2 B fragments, high halves: per k-tile, n-tile, lane
+    unsigned w2l[2][4][32][2];     // layer-2 B fragments, low halves
+    unsigned w3h[2][32][2];        // layer-3 B fragments (w3 in every column), high halves
+    unsigned w3l[2][32][2];        // layer-3 B fragments, low halves
     float b1[32], b2[32], b3;
 };
 
-__device__ __forceinline__ unsigned pack_half2(float lo, float hi) {
-    __half2 h = __floats2half2_rn(lo, hi);
-    return *reinterpret_cast<unsigned*>(&h);
+// f16 halves of an FP32 value: hi = f16(v), lo = f16(v - hi).
+__device__ __forceinline__ __half f16_hi(float v) { return __float2half_rn(v); }
+__device__ __forceinline__ __half f16_lo(float v) { return __float2half_rn(v - __half2float(__float2half_rn(v))); }
+
+// Two halves packed as one 32-bit operand register (a in the low 16 bits).
+__device__ __forceinline__ unsigned pack2(__half a, __half b) {
+    return (unsigned)__half_as_ushort(a) | ((unsigned)__half_as_ushort(b) << 16);
 }
 
-// max(lo, 0) and max(hi, 0) rounded to f16 and packed (lo in the low half).
-__device__ __forceinline__ unsigned relu_half2(float lo, float hi) {
-    unsigned r;
-    asm("cvt.rn.relu.f16x2.f32 %0, %1, %2;\n" : "=r"(r) : "f"(hi), "f"(lo));
-    return r;
+// max(a, 0) and max(b, 0) split into packed high and low halves.
+__device__ __forceinline__ void relu_split(float a, float b, unsigned& hi, unsigned& lo) {
+    a = fmaxf(a, 0.f);
+    b = fmaxf(b, 0.f);
+    const __half ha = __float2half_rn(a), hb = __float2half_rn(b);
+    hi = pack2(ha, hb);
+    lo = pack2(__float2half_rn(a - __half2float(ha)), __float2half_rn(b - __half2float(hb)));
 }
 
 // Fill the block's fragment tables from the 1281 weights (all threads).
-// Fragment layouts follow the PTX m16n8k8 / m16n8k16 f16 B operand: lane
-// (g = lane / 4, t = lane % 4) holds column n = g, rows k = 2t, 2t + 1 (and
-// k = 2t + 8, 2t + 9 in its second register for k16).
+// Fragment layouts follow the PTX m16n8k16 f16 B operand: lane (g = lane / 4,
+// t = lane % 4) holds column n = g, rows k = 2t, 2t + 1 in its first register
+// and k = 2t + 8, 2t + 9 in its second.
 __device__ __forceinline__ void gate_fill(GateSmem& g, const float* __restrict__ w) {
     constexpr int OB1 = 160, OW2 = 192, OB2 = 1216, OW3 = 1248, OB3 = 1280;
+    // layer-1 operand row k of neuron n: [w_hi (k < 5), w_hi (k < 10), w_lo (k < 15), 0]
+    auto b1k = [&](int n, int k) -> __half {
+        if (k < 5) return f16_hi(w[n * 5 + k]);
+        if (k < 10) return f16_hi(w[n * 5 + k - 5]);
+        if (k < 15) return f16_lo(w[n * 5 + k - 10]);
+        return __float2half_rn(0.f);
+    };
     for (int i = threadIdx.x; i < 4 * 32; i += blockDim.x) {
         int nt = i / 32, l = i % 32, gq = l / 4, t = l % 4;
         int n = nt * 8 + gq, k = 2 * t;
-        float lo = k < 5 ? w[n * 5 + k] : 0.f, hi = k + 1 < 5 ? w[n * 5 + k + 1] : 0.f;
-        g.w1f[nt][l] = pack_half2(lo, hi);
+        g.w1f[nt][l][0] = pack2(b1k(n, k), b1k(n, k + 1));
+        g.w1f[nt][l][1] = pack2(b1k(n, k + 8), b1k(n, k + 9));
     }
     for (int i = threadIdx.x; i < 2 * 4 * 32; i += blockDim.x) {
         int kt = i / 128, nt = (i / 32) % 4, l = i % 32, gq = l / 4, t = l % 4;
         int n = nt * 8 + gq, k = kt * 16 + 2 * t;
-        g.w2f[kt][nt][l][0] = pack_half2(w[OW2 + n * 32 + k], w[OW2 + n * 32 + k + 1]);
-        g.w2f[kt][nt][l][1] = pack_half2(w[OW2 + n * 32 + k + 8], w[OW2 + n * 32 + k + 9]);
+        const float* r = w + OW2 + n * 32;
+        g.w2h[kt][nt][l][0] = pack2(f16_hi(r[k]), f16_hi(r[k + 1]));
+        g.w2h[kt][nt][l][1] = pack2(f16_hi(r[k + 8]), f16_hi(r[k + 9]));
+        g.w2l[kt][nt][l][0] = pack2(f16_lo(r[k]), f16_lo(r[k + 1]));
+        g.w2l[kt][nt][l][1] = pack2(f16_lo(r[k + 8]), f16_lo(r[k + 9]));
     }
     for (int i = threadIdx.x; i < 2 * 32; i += blockDim.x) {
         int kt = i / 32, l = i % 32, t = l % 4;
         int k = kt * 16 + 2 * t;
-        g.w3f[kt][l][0] = pack_half2(w[OW3 + k], w[OW3 + k + 1]);
-        g.w3f[kt][l][1] = pack_half2(w[OW3 + k + 8], w[OW3 + k + 9]);
+        const float* r = w + OW3;
+        g.w3h[kt][l][0] = pack2(f16_hi(r[k]), f16_hi(r[k + 1]));
+        g.w3h[kt][l][1] = pack2(f16_hi(r[k + 8]), f16_hi(r[k + 9]));
+        g.w3l[kt][l][0] = pack2(f16_lo(r[k]), f16_lo(r[k + 1]));
+        g.w3l[kt][l][1] = pack2(f16_lo(r[k + 8]), f16_lo(r[k + 9]));
     }
     for (int i = threadIdx.x; i < 32; i += blockDim.x) {
         g.b1[i] = w[OB1 + i];
@@ -267,23 +300,11 @@ __device__ __forceinline__ uint2 lds_u64(const void* p) {
     return v;
 }
 
-__device__ __forceinline__ void ldsm_x2(unsigned& r0, unsigned& r1, const void* row) {
-    unsigned a = (unsigned)__cvta_generic_to_shared(row);
-    asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n" : "=r"(r0), "=r"(r1) : "r"(a));
-}
-
 __device__ __forceinline__ void ldsm_x4(unsigned& r0, unsigned& r1, unsigned& r2, unsigned& r3, const void* row) {
     unsigned a = (unsigned)__cvta_generic_to_shared(row);
     asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
                  : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
                  : "r"(a));
-}
-
-// d = a b + c, f16 operands, f32 accumulate (c and d distinct).
-__device__ __forceinline__ void mma_k8(float* d, unsigned a0, unsigned a1, unsigned b0, float c0, float c1) {
-    asm("mma.sync.aligned.m16n8k8.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5}, {%6}, {%7,%8,%7,%8};\n"
-        : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
-        : "r"(a0), "r"(a1), "r"(b0), "f"(c0), "f"(c1));
 }
 
 __device__ __forceinline__ void mma_k16c(float* d, unsigned a0, unsigned a1, unsigned a2, unsigned a3, unsigned b0,
@@ -295,28 +316,52 @@ __device__ __forceinline__ void mma_k16c(float* d, unsigned a0, unsigned a1, uns
 }
 
 // d += a b, f16 operands, f32 accumulate.
-__device__ __forceinline__ void mma_k16(float* d, unsigned a0, unsigned a1, unsigned a2, unsigned a3, unsigned b0,
-                                        unsigned b1) {
+__device__ __forceinline__ void mma_k16(float* d, const unsigned* a, uint2 b) {
     asm("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
         "{%0,%1,%2,%3};\n"
         : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b.x), "r"(b.y));
+}
+
+// One sample's layer-1 A row, 16 halves as two 16-byte chunks:
+// [x_hi(5), x_lo(5), x_hi(5), 0].
+__device__ __forceinline__ void gate_row(const float* x, uint4& r0, uint4& r1) {
+    __half h[5], l[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        h[k] = f16_hi(x[k]);
+        l[k] = __float2half_rn(x[k] - __half2float(h[k]));
+    }
+    const __half z = __float2half_rn(0.f);
+    r0 = make_uint4(pack2(h[0], h[1]), pack2(h[2], h[3]), pack2(h[4], l[0]), pack2(l[1], l[2]));
+    r1 = make_uint4(pack2(l[3], l[4]), pack2(h[0], h[1]), pack2(h[2], h[3]), pack2(h[4], z));
 }
 
 // Logits of this lane's cell for both sensors.  xr, xp: the normalised
-// density and pressure stencils of the lane's cell; tile: this warp's 1 KB
-// A tile (64 rows x 8 halves).  Must be called by all 32 lanes together.
-// All three layers run as m16n8 MMAs over four 16-row tiles (rows 0-31: the
-// warp's density stencils, 32-63: its pressure stencils).  Biases enter as
-// the accumulator input; ReLU and the f16 rounding of the hidden activations
-// are one conversion, and the accumulator layout of one layer is the A
-// fragment layout of the next, so the activations never leave registers.
+// density and pressure stencils of the lane's cell; need_r, need_p: whether
+// the caller uses that logit -- a 16-sample tile none of whose samples is
+// needed is skipped (its logits are left as they were).  With `both`, a
+// pressure logit is needed only where the density sensor came out smooth
+// (not needed, or logit < 0): the gate wants both smooth.  tile: this warp's
+// 2 KB A tile (64 rows x 16 halves).  Must be called by all 32 lanes together.
 __device__ __forceinline__ void gate_logits(const GateSmem& g, uint4* tile, const float* xr, const float* xp,
-                                            float& zr, float& zp) {
+                                            bool need_r, bool need_p, bool both, float& zr, float& zp) {
     const int lane = threadIdx.x & 31, t = lane & 3;
+    const unsigned nr = __ballot_sync(0xffffffffu, need_r);
+    unsigned np = __ballot_sync(0xffffffffu, need_p);
+    // row r's two 16-byte chunks are stored swapped when bit 2 of r is set,
+    // so that the eight rows an ldmatrix phase reads fall in distinct banks
+    const int sw = (lane >> 2) & 1;
     __syncwarp();
-    tile[lane] = make_uint4(pack_half2(xr[0], xr[1]), pack_half2(xr[2], xr[3]), pack_half2(xr[4], 0.f), 0u);
-    tile[32 + lane] = make_uint4(pack_half2(xp[0], xp[1]), pack_half2(xp[2], xp[3]), pack_half2(xp[4], 0.f), 0u);
+    {
+        uint4 r0, r1;
+        gate_row(xr, r0, r1);
+        tile[2 * lane + sw] = r0;
+        tile[2 * lane + (sw ^ 1)] = r1;
+        gate_row(xp, r0, r1);
+        tile[2 * (32 + lane) + sw] = r0;
+        tile[2 * (32 + lane) + (sw ^ 1)] = r1;
+    }
     __syncwarp();
     // sample row r of m-tile mt ends in fragment group r % 8, half r / 8 (c[0]
     // or c[2]); the lane's own rows are (mt = lane / 16, r = lane % 16) for
@@ -324,47 +369,73 @@ __device__ __forceinline__ void gate_logits(const GateSmem& g, uint4* tile, cons
     const int src = 4 * (lane & 7), half = (lane >> 3) & 1, hi16 = lane >> 4;
 #pragma unroll 1
     for (int mt = 0; mt < 4; ++mt) {
-        unsigned a0, a1, h1[2][4], h2[2][4];
-        ldsm_x2(a0, a1, tile + 16 * mt + (lane & 15));
+        if (both && mt == 2) np = __ballot_sync(0xffffffffu, need_p && (!need_r || zr < 0.f));
+        if ((((mt < 2 ? nr : np) >> (16 * (mt & 1))) & 0xffffu) == 0u) continue;   // uniform over the warp
+        unsigned a[4];
+        ldsm_x4(a[0], a[1], a[2], a[3], tile + 2 * (16 * mt + (lane & 15)) + ((lane >> 4) ^ ((lane >> 2) & 1)));
+        // layer 1: its accumulator fragments become layer 2's A fragments
+        // (k-tile nt / 2; rows g in registers 0, 2, rows g + 8 in 1, 3)
+        unsigned hh[2][4], hl[2][4];
 #pragma unroll
         for (int nt = 0; nt < 4; ++nt) {
             const uint2 bb = lds_u64(&g.b1[nt * 8 + 2 * t]);
+            const uint2 w = lds_u64(&g.w1f[nt][lane][0]);
             float c[4];
-            mma_k8(c, a0, a1, lds_u32(&g.w1f[nt][lane]), __uint_as_float(bb.x), __uint_as_float(bb.y));
-            h1[nt >> 1][(nt & 1) * 2 + 0] = relu_half2(c[0], c[1]);
-            h1[nt >> 1][(nt & 1) * 2 + 1] = relu_half2(c[2], c[3]);
+            mma_k16c(c, a[0], a[1], a[2], a[3], w.x, w.y, __uint_as_float(bb.x), __uint_as_float(bb.y));
+            relu_split(c[0], c[1], hh[nt >> 1][(nt & 1) * 2], hl[nt >> 1][(nt & 1) * 2]);
+            relu_split(c[2], c[3], hh[nt >> 1][(nt & 1) * 2 + 1], hl[nt >> 1][(nt & 1) * 2 + 1]);
         }
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt) {
-            const uint2 bb = lds_u64(&g.b2[nt * 8 + 2 * t]);
-            const uint2 w0 = lds_u64(&g.w2f[0][nt][lane][0]), w1 = lds_u64(&g.w2f[1][nt][lane][0]);
-            float c[4];
-            mma_k16c(c, h1[0][0], h1[0][1], h1[0][2], h1[0][3], w0.x, w0.y, __uint_as_float(bb.x),
-                     __uint_as_float(bb.y));
-            mma_k16(c, h1[1][0], h1[1][1], h1[1][2], h1[1][3], w1.x, w1.y);
-            h2[nt >> 1][(nt & 1) * 2 + 0] = relu_half2(c[0], c[1]);
-            h2[nt >> 1][(nt & 1) * 2 + 1] = relu_half2(c[2], c[3]);
-        }
-        const uint2 w0 = lds_u64(&g.w3f[0][lane][0]), w1 = lds_u64(&g.w3f[1][lane][0]);
+        // layers 2 and 3, k-tile by k-tile of layer 3: layer-2 n-tiles 2 kt
+        // and 2 kt + 1 form layer 3's A fragments of k-tile kt
         const float b3 = __uint_as_float(lds_u32(&g.b3));
-        float c[4];
-        mma_k16c(c, h2[0][0], h2[0][1], h2[0][2], h2[0][3], w0.x, w0.y, b3, b3);
-        mma_k16(c, h2[1][0], h2[1][1], h2[1][2], h2[1][3], w1.x, w1.y);
-        const float v0 = __shfl_sync(0xffffffffu, c[0], src), v1 = __shfl_sync(0xffffffffu, c[2], src);
+        float z[4] = {b3, b3, b3, b3};
+#pragma unroll
+        for (int kt = 0; kt < 2; ++kt) {
+            unsigned gh[4], gl[4];
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int nt = 2 * kt + j;
+                const uint2 bb = lds_u64(&g.b2[nt * 8 + 2 * t]);
+                float c[4] = {__uint_as_float(bb.x), __uint_as_float(bb.y), __uint_as_float(bb.x),
+                              __uint_as_float(bb.y)};
+                const uint2 h0 = lds_u64(&g.w2h[0][nt][lane][0]), h1 = lds_u64(&g.w2h[1][nt][lane][0]);
+                mma_k16(c, hh[0], h0);
+                mma_k16(c, hh[1], h1);
+                mma_k16(c, hl[0], h0);
+                mma_k16(c, hl[1], h1);
+                const uint2 l0 = lds_u64(&g.w2l[0][nt][lane][0]), l1 = lds_u64(&g.w2l[1][nt][lane][0]);
+                mma_k16(c, hh[0], l0);
+                mma_k16(c, hh[1], l1);
+                relu_split(c[0], c[1], gh[j * 2], gl[j * 2]);
+                relu_split(c[2], c[3], gh[j * 2 + 1], gl[j * 2 + 1]);
+            }
+            const uint2 wh = lds_u64(&g.w3h[kt][lane][0]), wl = lds_u64(&g.w3l[kt][lane][0]);
+            mma_k16(z, gh, wh);
+            mma_k16(z, gl, wh);
+            mma_k16(z, gh, wl);
+        }
+        const float v0 = __shfl_sync(0xffffffffu, z[0], src), v1 = __shfl_sync(0xffffffffu, z[2], src);
         const float v = half ? v1 : v0;
         if (mt == hi16) zr = v;
         if (mt == 2 + hi16) zp = v;
     }
 }
 
-// Normalised sensor stencil (v_k - v_2) / (max_k |v_k - v_2| + 1e-12).
-__device__ __forceinline__ void gate_input(const float* v, float* x) {
+// Relative round-off floor of the gate's flat test (MFC_GATE_FLOOR).
+constexpr float kGateFloor32 = (float)MFC_GATE_FLOOR;
+
+// Normalised sensor stencil: x_k = (v_k - v_2) / max_j |v_j - v_2|.  Returns
+// false, with x = 0, when the stencil is flat -- max_j |v_j - v_2| <= floor
+// |v_2| -- and counts as smooth without the network.
+__device__ __forceinline__ bool gate_input(const float* v, float* x) {
     float m = 0.f;
 #pragma unroll
     for (int k = 0; k < 5; ++k) m = fmaxf(m, fabsf(v[k] - v[2]));
-    float r = __fdividef(1.f, m + 1e-12f);
+    const bool live = m > kGateFloor32 * fabsf(v[2]);
+    const float r = live ? __frcp_rn(m) : 0.f;
 #pragma unroll
     for (int k = 0; k < 5; ++k) x[k] = (v[k] - v[2]) * r;
+    return live;
 }
 
 // Linear-weight (fifth-order upwind) face values of cell i: the WENO5
@@ -386,6 +457,39 @@ __device__ __forceinline__ bool face_ok(const EosR<float, 2>& e, const float* w)
     return (w[0] + w[1] > 0.f) && (a1 >= 0.f) && (a1 <= 1.f) && ((G + 1.f) * w[FL::IE] + Pi > 0.f);
 }
 
+// ---- TMA staging (MFC_TMA_YZ builds) ----------------------------------------
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// True once the phase of `bar` with the given parity has completed.
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// One 4-D box of the tensor map into shared memory, completing on `bar`.
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5}], [%6];\n" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<unsigned long long>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+        : "memory");
+}
+
 // Minimum resident blocks for the register allocator, in blocks of the
 // sweep's own size (x sweeps run one-warp blocks, each with its own output
 // tile in static shared memory).
@@ -404,7 +508,7 @@ constexpr int sweep_min_blocks() {
 // the uniform-grid kernels carry none of that code.
 template <int NDIM, int DIR, int MODE, int FORM, bool NU, int NF>
 __global__ void __launch_bounds__(sweep_threads(DIR), sweep_min_blocks<FORM, MODE, DIR, NF>())
-sweep_kernel(const SweepArgs a) {
+sweep_kernel(const SweepArgs a, const __grid_constant__ CUtensorMap tmap) {
     using R = FormReal<FORM>;
     constexpr bool EXACT = FORM == FORM_FP64_EXACT;
     constexpr bool GATED = FORM == FORM_GATED;
@@ -421,7 +525,13 @@ sweep_kernel(const SweepArgs a) {
     constexpr int OSTAGE = NEQ * 32 * PITCH;
     __shared__ R ostage[OSTAGE_ON ? WARPS * OSTAGE : 1];
     __shared__ GateSmem gsm[GATED ? 1 : 0 + 1];
-    __shared__ uint4 gtile[GATED ? WARPS * 64 : 1];
+    __shared__ uint4 gtile[GATED ? WARPS * 128 : 1];
+    // TMA staging of the FP32 y/z sweeps: per warp two slots of NL fields x
+    // kTmaCells cells x 32 lanes, one mbarrier per slot
+    constexpr bool TMA = MFC_TMA_YZ && (FORM == FORM_MIXED || FORM == FORM_GATED) && (DIR == 1 || DIR == 2) && !NU;
+    constexpr int TC = kTmaCells, TSLOT = NL * TC * 32;
+    __shared__ __align__(128) float tbuf[TMA ? WARPS * 2 * TSLOT : 1];
+    __shared__ __align__(8) uint64_t tbar[TMA ? WARPS * 2 : 1];
     if constexpr (GATED) {
         gate_fill(gsm[0], a.gate_w);   // every thread, before any warp leaves
         __syncthreads();
@@ -461,11 +571,99 @@ sweep_kernel(const SweepArgs a) {
     // Along y and z the warp's 32 loads form one coalesced row per field;
     // along x each lane reads its own row, and the 32-byte sector it brings
     // into L1 serves the lane's next CH - 1 cells.
+    // TMA staging: interior segments (no ghost cell) of launches given a
+    // tensor map read their cells from the warp's shared-memory slots; chunk
+    // ck (cells s0 - 3 + ck TC ..) lands in slot ck & 1, and starting to read
+    // chunk ck refills the other slot with chunk ck + 1.  Waits are bounded:
+    // a box that never lands sets status bit 2 instead of hanging.
+    const int wib = threadIdx.x >> 5;
+    const int kcells = s1 - s0 + 6;
+    const bool use_tma = TMA && a.tmap && s0 >= 3 && s1 + 3 <= ns;
+    bool tma_fail = false;
+    auto tma_issue = [&](int ck) {   // one lane
+        if constexpr (TMA) {
+            uint64_t* bar = tbar + wib * 2 + (ck & 1);
+            float* dst = tbuf + (wib * 2 + (ck & 1)) * TSLOT;
+            mbar_expect_tx(bar, (unsigned)(TSLOT * sizeof(float)));
+            const int jc = s0 - 3 + ck * TC;
+#pragma unroll
+            for (int f = 0; f < NL; ++f) {
+                if constexpr (DIR == 1) tma_load_4d(dst + f * TC * 32, &tmap, chunk * 32, jc, b, LS::field(f), bar);
+                else tma_load_4d(dst + f * TC * 32, &tmap, chunk * 32, b, jc, LS::field(f), bar);
+            }
+        }
+    };
+    if constexpr (TMA) {
+        if (use_tma) {
+            if (lane == 0) {
+                mbar_init(tbar + wib * 2, 1);
+                mbar_init(tbar + wib * 2 + 1, 1);
+                asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+            }
+            __syncwarp();
+            if (lane == 0) tma_issue(0);
+        }
+    }
+
+    // FP32 x sweep with rows of a multiple of 4 cells: 16-byte aligned rows,
+    // loaded four cells at a time (cells are fetched in order along the row)
+    constexpr bool XVEC = MIXED && DIR == 0 && MFC_XVEC;
+    const bool xvec_ok = XVEC && (n0 & 3) == 0;
+    float xq[XVEC ? NL : 1][3];
+    int xpend = 0;
+
     // A ghost cell beyond a side that borders another block (block
     // decomposition) comes from that side's halo buffer; any other from the
     // BC index map.  j is the same for the whole warp.
     auto fetch = [&](int k, R* v) {
+        if constexpr (TMA) {
+            if (use_tma) {
+                const int ck = k / TC, cc = k - ck * TC;
+                if (cc == 0) {
+                    bool ok = false;
+                    for (int it = 0; it < (1 << 22) && !ok; ++it) ok = mbar_try_wait(tbar + wib * 2 + (ck & 1), (ck >> 1) & 1);
+                    tma_fail |= !ok;
+                    if ((ck + 1) * TC < kcells) {
+                        // every lane's reads of the slot being refilled (chunk
+                        // ck - 1) are ordered before the copy that overwrites it
+                        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                        __syncwarp();
+                        if (lane == 0) tma_issue(ck + 1);
+                    }
+                }
+                const float* src = tbuf + (wib * 2 + (ck & 1)) * TSLOT + cc * 32 + lane;
+#pragma unroll
+                for (int f = 0; f < NL; ++f) v[f] = src[f * TC * 32];
+                return;
+            }
+        }
         const int j = s0 - 3 + k;
+        if constexpr (XVEC) {
+            // FP32 x sweep: four cells of the lane's row per 16-byte load, the
+            // three not yet used kept in registers for the next steps
+            if (xpend > 0) {
+#pragma unroll
+                for (int f = 0; f < NL; ++f) {
+                    v[f] = xq[f][0];
+                    xq[f][0] = xq[f][1];
+                    xq[f][1] = xq[f][2];
+                }
+                --xpend;
+                return;
+            }
+            if (xvec_ok && (j & 3) == 0 && j >= 0 && j + 3 < ns) {
+#pragma unroll
+                for (int f = 0; f < NL; ++f) {
+                    const float4 t = __ldg(reinterpret_cast<const float4*>(qin + LS::field(f) * nc + base + j));
+                    v[f] = t.x;
+                    xq[f][0] = t.y;
+                    xq[f][1] = t.z;
+                    xq[f][2] = t.w;
+                }
+                xpend = 3;
+                return;
+            }
+        }
         const R* h = j < 0 ? static_cast<const R*>(a.hlo) : (j >= ns ? static_cast<const R*>(a.hhi) : nullptr);
         if (h) {
             // the pencil's position in the plane normal to DIR, from its first
@@ -489,20 +687,15 @@ sweep_kernel(const SweepArgs a) {
     bool bad = false;
     R smax = R(0);
     unsigned n_gated = 0, n_fallback = 0, n_cells = 0, n_flat = 0;
-    // gated form: the network's logit at zero input (tensor-core path, as for
-    // any other input), for warp steps whose stencils are all flat
-    float z_flat = 0.f;
-    if constexpr (GATED) {
-        const float x0[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-        float zr0, zp0;
-        gate_logits(gsm[0], gtile + (threadIdx.x >> 5) * 64, x0, x0, zr0, zp0);
-        z_flat = zr0;
-    }
     double dt = 0.0;
     if (MODE == SW_LAST_RK) dt = a.ctrl->dt;
-    // SSP-RK3 stage coefficients q^(k+1) = rk_a q^n + rk_b (q^(k) + dt L)
-    const double rk_a = a.stage == 2 ? 0.75 : (1.0 / 3.0), rk_b = a.stage == 2 ? 0.25 : (2.0 / 3.0);
-    const float bdt32 = float(a.stage == 1 ? dt : rk_b * dt);
+    // FP32 forms: SSP-RK3 in increment form, q^(k) = q^n + D_k with FP32
+    // increments D_1 = dt L(q^n), D_2 = (D_1 + dt L(q^(1)))/4,
+    // D_3 = 2 (D_2 + dt L(q^(2)))/3 -- the same stages as
+    // q^(2) = 3/4 q^n + 1/4 (q^(1) + dt L), q^(3) = 1/3 q^n + 2/3 (q^(2) + dt L) --
+    // and one FP64 addition per field forms q^(k) from the FP64 q^n
+    const float dt32 = float(dt);
+    const float kfac = a.stage == 2 ? 0.25f : (2.0f / 3.0f);
 
     R W[5][NEQ];
 #pragma unroll
@@ -554,7 +747,7 @@ sweep_kernel(const SweepArgs a) {
                     for (int f = 0; f < NEQ; ++f) qnp[f] = __ldg(a.qn + f * nc + c);
                     if (a.stage != 1) {
 #pragma unroll
-                        for (int f = 0; f < NEQ; ++f) qkp[f] = __ldg(qin + f * nc + c);
+                        for (int f = 0; f < NEQ; ++f) qkp[f] = a.dinc[f * nc + c];   // D_(k-1)
                     }
                 }
             }
@@ -562,28 +755,22 @@ sweep_kernel(const SweepArgs a) {
         R vm[NEQ], vp[NEQ];
         bool use_weno = true;
         if constexpr (GATED) {
-            // gate: linear weights when the network calls both the density and
-            // the pressure stencil smooth (logit < 0) and the faces stay physical;
-            // all 32 lanes take part in the tensor-core evaluation
-            float sr[5], sp[5], zr = z_flat, zp = z_flat;
+            // gate: linear weights when the density and the pressure stencil
+            // are both smooth -- flat (below the round-off floor), or called
+            // smooth by the network (logit < 0) -- and the faces stay physical;
+            // all 32 lanes take part in the tensor-core evaluation, which a
+            // warp step whose stencils are all flat skips
+            float sr[5], sp[5], xr[5], xp[5], zr = -1.f, zp = -1.f;
 #pragma unroll
             for (int k = 0; k < 5; ++k) {
                 sr[k] = W[k][0] + W[k][1];
                 sp[k] = W[k][IE];
             }
-            bool flat = true;
-#pragma unroll
-            for (int k = 0; k < 5; ++k) flat = flat && sr[k] == sr[2] && sp[k] == sp[2];
-            // all 32 stencil pairs flat: every network input is exactly zero and
-            // every logit is the output at zero, evaluated once per warp below
-            const bool warp_flat = __all_sync(0xffffffffu, flat);
-            if (!warp_flat) {
-                float xr[5], xp[5];
-                gate_input(sr, xr);
-                gate_input(sp, xp);
-                gate_logits(gsm[0], gtile + (threadIdx.x >> 5) * 64, xr, xp, zr, zp);
-            }
-            const bool smooth = zr < 0.f && zp < 0.f;
+            const bool live_r = gate_input(sr, xr), live_p = gate_input(sp, xp);
+            const bool warp_flat = !__any_sync(0xffffffffu, live_r || live_p);
+            if (!warp_flat)
+                gate_logits(gsm[0], gtile + (threadIdx.x >> 5) * 128, xr, xp, live_r, live_p, true, zr, zp);
+            const bool smooth = (!live_r || zr < 0.f) && (!live_p || zp < 0.f);
             if (smooth) {
 #pragma unroll
                 for (int f = 0; f < NEQ; ++f) linear5(W[0][f], W[1][f], W[2][f], W[3][f], W[4][f], vm[f], vp[f]);
@@ -594,6 +781,7 @@ sweep_kernel(const SweepArgs a) {
                 n_gated += smooth && !use_weno;
                 n_cells += 1;
                 n_flat += warp_flat;
+                if (a.gate_dec && active) a.gate_dec[base + (long long)j * ss] = smooth ? (use_weno ? 2 : 1) : 0;
             }
         }
         if (use_weno) {
@@ -683,15 +871,16 @@ sweep_kernel(const SweepArgs a) {
                         R tot = NDIM > 1 ? (EPI_PREFETCH ? accp[f] : acc[f * nc + c]) + L[f] : L[f];
                         double qn = EPI_PREFETCH ? qnp[f] : a.qn[f * nc + c];
                         if constexpr (MIXED) {
-                            // q^(k+1) = a q^n + b q^(k) + (b dt) L, accumulated in FP64
-                            // from the FP32 increment (b dt) L (L itself is FP32)
-                            const double inc = f2d_bits(bdt32 * tot);
+                            // D_k in FP32 from D_(k-1) and the FP32 L; q^(k) = q^n + D_k in FP64
+                            float Dk;
                             if (a.stage == 1) {
-                                qnew[f] = qn + inc;
+                                Dk = dt32 * float(tot);
                             } else {
-                                const double qkd = f2d_bits(EPI_PREFETCH ? qkp[f] : qin[f * nc + c]);
-                                qnew[f] = __fma_rn(rk_a, qn, __fma_rn(rk_b, qkd, inc));
+                                const float Dp = EPI_PREFETCH ? float(qkp[f]) : a.dinc[f * nc + c];
+                                Dk = kfac * fmaf(dt32, float(tot), Dp);
                             }
+                            if (a.stage != 3) a.dinc[f * nc + c] = Dk;
+                            qnew[f] = qn + f2d_bits(Dk);
                         } else {
                             double dL = dt * double(tot);
                             if (a.stage == 1) {
@@ -800,6 +989,9 @@ sweep_kernel(const SweepArgs a) {
         }
     }
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&a.ctrl->status, 1u);
+    if constexpr (TMA) {
+        if (__any_sync(0xffffffffu, tma_fail) && lane == 0) atomicOr(&a.ctrl->status, 4u);
+    }
     if constexpr (GATED) {
         // only cells this lane owns count (inactive lanes and segment halos excluded)
         if (!active) n_gated = n_fallback = n_cells = n_flat = 0;
@@ -865,7 +1057,10 @@ cudaError_t launch_kernel(const SweepArgs& a0, cudaStream_t s) {
     const long long blocks = (sweep_warps(DIR, a.n, a.seg) * 32 + T - 1) / T;
     if (blocks <= 0 || a.dry) return cudaSuccess;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    sweep_kernel<NDIM, DIR, MODE, FORM, NU, NF><<<(unsigned)blocks, T, 0, s>>>(a);
+    CUtensorMap tm;
+    if (a.tmap) tm = *static_cast<const CUtensorMap*>(a.tmap);
+    else memset(&tm, 0, sizeof(tm));
+    sweep_kernel<NDIM, DIR, MODE, FORM, NU, NF><<<(unsigned)blocks, T, 0, s>>>(a, tm);
     return cudaGetLastError();
 }
 

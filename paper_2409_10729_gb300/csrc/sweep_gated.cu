@@ -16,7 +16,7 @@ cudaError_t launch_sweep_gated(int ndim, int dir, int mode, const SweepArgs& a, 
 __global__ void __launch_bounds__(128) gate_forward_tc_kernel(const float* __restrict__ X, long long n,
                                                               const float* __restrict__ theta, float* z) {
     __shared__ GateSmem g;
-    __shared__ uint4 tile[4 * 64];
+    __shared__ uint4 tile[4 * 128];
     gate_fill(g, theta);
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -29,7 +29,7 @@ __global__ void __launch_bounds__(128) gate_forward_tc_kernel(const float* __res
             xr[k] = sr < n ? X[sr * 5 + k] : 0.f;
             xp[k] = sp < n ? X[sp * 5 + k] : 0.f;
         }
-        gate_logits(g, tile + warp * 64, xr, xp, zr, zp);
+        gate_logits(g, tile + warp * 128, xr, xp, sr < n, sp < n, false, zr, zp);
         if (sr < n) z[sr] = zr;
         if (sp < n) z[sp] = zp;
     }

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "lib", "libmfc5.so")
 
 MFC_OK, MFC_EINVAL, MFC_ENOMEM, MFC_ECUDA, MFC_ENONPHYSICAL, MFC_ESTATE, MFC_ETOOBIG = 0, -1, -2, -3, -4, -5, -6
 MFC_NOALLOC_MAX_DOUBLES = 2 * 1024 * 1024
+MFC_GATE_FLOOR = 1e-4
 MFC_FP64, MFC_MIXED, MFC_GATED, MFC_FP64_FAST = 0, 1, 2, 3
 PRECISIONS = {"fp64": MFC_FP64, "mixed": MFC_MIXED, "gated": MFC_GATED, "fp64_fast": MFC_FP64_FAST}
 
@@ -83,6 +84,7 @@ def lib() -> ctypes.CDLL:
             "mfc_gate_stats": ([vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
                                 ctypes.POINTER(ctypes.c_longlong)], ip),
             "mfc_gate_flat": ([vp, ctypes.POINTER(ctypes.c_longlong)], ip),
+            "mfc_gate_rhs": ([vp, vp, vp, ip], ip),
             "mfc_set_grid": ([vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double)], ip),
             "mfc_gate_samples": ([vp, vp, vp, ctypes.c_longlong, ctypes.c_float,
                                   ctypes.POINTER(ctypes.c_longlong)], ip),
@@ -273,6 +275,16 @@ class Solver:
         f = ctypes.c_longlong()
         self._check(lib().mfc_gate_flat(self.ctx, ctypes.byref(f)), "mfc_gate_flat")
         return f.value
+
+    def gate_rhs(self, allow_nonphysical=False):
+        """(L(q^n), decisions [ndim][nz][ny][nx] int8: 0 WENO, 1 linear, 2 fallback)."""
+        out = np.empty(self.shape, dtype=np.float64)
+        dec = np.empty((int(self.p["ndim"]),) + self.shape[1:], dtype=np.int8)
+        ptr, dev = _ptr(out, self.size)
+        allow = (MFC_ENONPHYSICAL,) if allow_nonphysical else ()
+        self.last_status = self._check(lib().mfc_gate_rhs(self.ctx, ptr, ctypes.c_void_p(dec.ctypes.data), dev),
+                                       "mfc_gate_rhs", allow)
+        return out, dec
 
     def gate_samples(self, tau: float = 0.1):
         """Labelled samples (X [n,5], Y [n]) of the current state as torch CUDA tensors."""

@@ -4,8 +4,10 @@ Data: seeded 2-D shock / water-column runs (512 x 256 cells) advanced with the
 mixed form; every `every` steps the library emits, for every cell and
 direction, the normalised density and pressure stencils labelled by plain
 WENO5-JS itself (troubled when a nonlinear weight departs from its linear
-weight by more than tau).  Each snapshot contributes all its troubled samples
-and as many smooth ones (capped), so the classes are balanced.
+weight by more than tau on a stencil whose variation is above the round-off
+floor).  Flat sensor stencils (below the floor) are left out: the gate calls
+them smooth without the network.  Each snapshot contributes its troubled
+samples and as many smooth ones (capped), so the classes are balanced.
 
 Training: mean weighted binary cross-entropy, Adam, minibatches, with the
 loss/gradient and Adam kernels of libmfc5 (mfc_mlp_loss_grad, mfc_mlp_adam).
@@ -38,7 +40,7 @@ def collect(seeds, nx, ny, steps, every, cap, tau, rng):
     from . import inputs as I
     from . import mfc
     xs, ys = [], []
-    stats = {"snapshots": 0, "troubled_fraction": []}
+    stats = {"snapshots": 0, "troubled_fraction": [], "flat_fraction": []}
     for seed in seeds:
         p, w = I.shock_water_column(nx, ny, seed=seed)
         s = mfc.Solver(p, "mixed")
@@ -48,9 +50,10 @@ def collect(seeds, nx, ny, steps, every, cap, tau, rng):
                 s.step_rk3(0.4, every)
             X, Y = s.gate_samples(tau)
             pos = torch.nonzero(Y > 0.5).flatten()
-            neg = torch.nonzero(Y <= 0.5).flatten()
+            neg = torch.nonzero((Y >= 0) & (Y <= 0.5)).flatten()
             stats["snapshots"] += 1
             stats["troubled_fraction"].append(float(len(pos)) / float(len(Y)))
+            stats["flat_fraction"].append(1.0 - float(len(pos) + len(neg)) / float(len(Y)))
             npos = min(len(pos), cap)
             nneg = min(len(neg), max(npos, cap // 8))
             g = torch.Generator(device="cuda")
@@ -62,6 +65,7 @@ def collect(seeds, nx, ny, steps, every, cap, tau, rng):
             ys.append(Y[idx].clone())
         s.close()
     stats["troubled_fraction"] = float(np.mean(stats["troubled_fraction"]))
+    stats["flat_fraction"] = float(np.mean(stats["flat_fraction"]))
     return torch.cat(xs), torch.cat(ys), stats
 
 
@@ -163,7 +167,9 @@ def main(argv=None):
         "data": {"runs": args.runs, "val_runs": args.val_runs, "grid": [args.nx, args.ny], "steps": args.steps,
                  "every": args.every, "tau": args.tau, "train_samples": int(len(Y)),
                  "train_troubled": int((Y > 0.5).sum()), "val_samples": int(len(Yv)),
-                 "troubled_fraction_of_all_cells": round(st["troubled_fraction"], 4)},
+                 "troubled_fraction_of_all_samples": round(st["troubled_fraction"], 4),
+                 "flat_fraction_of_all_samples": round(st["flat_fraction"], 4),
+                 "round_off_floor": 1e-4},
         "training": {"epochs": args.epochs, "batch": args.batch, "lr": args.lr, "pos_weight": args.pos_weight,
                      "loss_per_epoch": [round(h, 5) for h in hist]},
         "heldout": {"decision_shift_logit": round(shift, 4), "recall_troubled": round(tp / max(tp + fn, 1), 5),

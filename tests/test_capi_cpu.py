@@ -125,3 +125,14 @@ def test_noalloc_refuses_overlapping_buffers_before_touching_the_device(lib, off
     q = ctypes.c_void_p(base)
     rhs = ctypes.c_void_p(base + 8 * offset_doubles)
     assert lib.mfc_rhs_noalloc(ctypes.byref(p), q, rhs, None) == mfc.MFC_EINVAL
+
+
+def test_tma_staging_build_option_compiles(tmp_path):
+    """The measured-and-rejected TMA staging of the FP32 y/z sweeps stays a
+    working build option: the FP32 sweep unit compiles with it for sm_103a."""
+    out = tmp_path / "sweep_mixed_tma.o"
+    cmd = [B.nvcc(), *B.ARCH, *B.COMMON, *B.FAST32, "-DMFC_TMA_YZ=1", "-c",
+           os.path.join(B.CSRC, "sweep_mixed.cu"), "-o", str(out)]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert out.stat().st_size > 0

@@ -4,14 +4,19 @@
   (gradients to 1e-5 relative, Adam to 1e-6, logits to 1e-5).
 * Training samples: normalised stencils and WENO-weight labels against the
   oracle's weights, cell by cell.
-* The gated sweep: a gate that never fires reproduces the mixed form (to
-  FP32 round-off; the same WENO code in another kernel); a gate that always fires gives the linear-weight WENO5 RHS (the
-  oracle with a huge epsilon) on smooth data; on a sharp interface the
-  non-physical linear faces fall back to WENO.
-* Training on the GPU lowers the loss; and the trained network's gain: the
-  fraction of cell reconstructions it gates, its time against the mixed form
-  without the gate, and its error against the FP64 path (the plain-WENO
-  judge), stated per field.
+* The gated sweep: a gate that never fires reproduces the mixed form on a
+  state without flat stencils (to FP32 round-off; the same WENO code in
+  another kernel); a gate that always fires gives the linear-weight WENO5
+  RHS (the oracle with a huge epsilon) on smooth data; on a sharp interface
+  the non-physical linear faces fall back to WENO; stencils below the
+  round-off floor are smooth without the network.
+* The fused network (split-f16 tensor-core operands) against the FP64
+  oracle network: logits to 1e-5, decisions equal away from 0.
+* Parity of the whole gate: decisions and RHS of the fused gate against the
+  oracle's gated RHS on an oracle-advanced 96^3 shock/droplet state.
+* Training on the GPU lowers the loss; and the trained network's gain over
+  the trivial (floor-only) gate: fraction of reconstructions gated, time,
+  and per-field error against the FP64 path (the plain-WENO judge).
 """
 import json
 import os
@@ -100,37 +105,45 @@ def test_forward_matches_oracle():
 
 def test_samples_match_oracle_labels():
     """Normalised stencils and labels of every cell and direction of a 2-D
-    state (diffuse interface + shock), recomputed with the oracle's weights."""
+    state (diffuse interface + shock) advanced by the oracle, recomputed with
+    the oracle's normalisation, weights and round-off floor."""
     from paper_2409_10729_gb300 import mfc
     p, w = I.shock_water_column(48, 24)
+    q, _ = O.run_cfl(p, O.prim_to_cons(p, w), 0.4, 20)
     s = mfc.Solver(p, "fp64")
-    s.set_state_prim(w)
-    s.step_rk3(0.4, 20)
-    q = s.get_state()
+    s.set_state(q)
     X, Y = s.gate_samples(0.1)
     X, Y = X.cpu().numpy(), Y.cpu().numpy()
     W = O.cons_to_prim(p, q)[:, 0]            # [6, ny, nx]
     ny, nx = W.shape[1:]
-    checked = 0
+    checked = flat = 0
     for d in range(2):
         for c in range(nx * ny):
             y0, x0 = divmod(c, nx)
             idx = [min(max((x0 if d == 0 else y0) + k, 0), (nx if d == 0 else ny) - 1) for k in range(-2, 3)]
             st = W[:, y0, idx] if d == 0 else W[:, idx, x0]
-            # skip labels within round-off of the threshold
-            dev = 0.0
+            # labels: departures of the non-flat fields; skip labels within
+            # round-off of the threshold or of the floor
+            dev, near = 0.0, False
             for v in st:
+                m = np.max(np.abs(v - v[2]))
+                near |= abs(m - mfc.MFC_GATE_FLOOR * abs(v[2])) <= 1e-9 * abs(v[2])
+                if O.is_flat(v):
+                    continue
                 wm, wp = O.weno5_weights(v)
                 dev = max(dev, np.max(np.abs(wm - [0.1, 0.6, 0.3]) / [0.1, 0.6, 0.3]),
                           np.max(np.abs(wp - [0.3, 0.6, 0.1]) / [0.3, 0.6, 0.1]))
             k = (d * nx * ny + c) * 2
-            np.testing.assert_allclose(X[k], O.mlp_normalise(st[0] + st[1]), atol=2e-6)
-            np.testing.assert_allclose(X[k + 1], O.mlp_normalise(st[4]), atol=2e-6)
-            if abs(dev - 0.1) > 1e-6:
-                assert Y[k] == Y[k + 1] == float(dev > 0.1)
-                checked += 1
-    assert checked > 0.99 * 2 * nx * ny
-    assert 0 < Y.sum() < len(Y)
+            for sensor, v in ((0, st[0] + st[1]), (1, st[4])):
+                np.testing.assert_allclose(X[k + sensor], O.mlp_normalise(v), atol=2e-6)
+                if O.is_flat(v):
+                    flat += 1
+                    assert Y[k + sensor] == -1.0 and np.all(X[k + sensor] == 0.0)
+                elif abs(dev - 0.1) > 1e-6 and not near:
+                    assert Y[k + sensor] == float(dev > 0.1)
+                    checked += 1
+    assert checked + flat > 0.99 * 2 * 2 * nx * ny
+    assert 0 < (Y > 0.5).sum() and 0 < (Y == 0).sum() and 0 < flat
 
 
 def _gated(p, weights):
@@ -147,8 +160,10 @@ def _bias_only(b3):
 
 
 def test_gate_that_never_fires_is_the_mixed_form():
+    """A random periodic state has no flat stencil, so a gate whose network
+    never fires reconstructs every cell with WENO5-JS: the mixed form."""
     from paper_2409_10729_gb300 import mfc
-    p, w = I.shock_droplets(40)
+    p, w = I.random_periodic(3, [24, 20, 18], seed=9)
     g = _gated(p, _bias_only(10.0))
     m = mfc.Solver(p, "mixed")
     for s in (g, m):
@@ -160,7 +175,7 @@ def test_gate_that_never_fires_is_the_mixed_form():
     scale[2:5] = scale[2:5].max()
     assert (np.abs(a - b).max(1) / scale).max() <= 1e-6
     gated, fb, cells = g.gate_stats()
-    assert gated == 0 and fb == 0 and cells == 4 * 3 * 3 * 40 ** 3   # steps x stages x directions x cells
+    assert gated == 0 and fb == 0 and cells == 4 * 3 * 3 * 24 * 20 * 18   # steps x stages x directions x cells
 
 
 def test_gate_that_always_fires_is_linear_weno():
@@ -200,18 +215,37 @@ def test_gate_falls_back_to_weno_on_sharp_interface():
     assert np.all(np.isfinite(q)) and np.all(q[4] >= -1e-6) and np.all(q[0] + q[1] > 0)
 
 
-def test_tensor_core_logits_match_fp32_network():
-    """The gated sweep's network (hidden layers on the tensor cores, fp16
-    operands, FP32 accumulation) against the FP32 network and the FP64
-    oracle on the same inputs: real solver stencils and random ones, with the
-    trained weights and with random weights; ragged sample count."""
+def _oracle_stencils(p, q, limit=None):
+    """Normalised density and pressure stencils (oracle normalisation, with
+    the round-off floor) of every cell and direction of an oracle state,
+    flat ones left out."""
+    W = O.cons_to_prim(p, q)[:, 0]
+    ny, nx = W.shape[1:]
+    out = []
+    for d in range(2):
+        for y0 in range(ny):
+            for x0 in range(nx):
+                idx = [min(max((x0 if d == 0 else y0) + k, 0), (nx if d == 0 else ny) - 1) for k in range(-2, 3)]
+                st = W[:, y0, idx] if d == 0 else W[:, idx, x0]
+                for v in (st[0] + st[1], st[4]):
+                    if not O.is_flat(v):
+                        out.append(O.mlp_normalise(v))
+    return np.array(out)
+
+
+def test_tensor_core_logits_match_the_fp32_network():
+    """The gated sweep's network (every layer on the tensor cores, operands
+    split into two f16 halves) against the FP64 oracle network on the same
+    FP32 inputs, to FP32 accuracy (1e-5 of the logit scale, the bar of the
+    CUDA-core FP32 forward): real solver stencils of an oracle-advanced
+    water-column state and random ones, with the trained weights and with
+    random weights; ragged sample count.  The decisions (logit < 0) agree
+    wherever the oracle logit is more than 1e-4 from 0."""
     import torch
     from paper_2409_10729_gb300 import mfc
     p, w = I.shock_water_column(96, 48)
-    s = mfc.Solver(p, "fp64")
-    s.set_state_prim(w)
-    s.step_rk3(0.4, 100)
-    Xs, _ = s.gate_samples(0.1)
+    q, _ = O.run_cfl(p, O.prim_to_cons(p, w), 0.4, 100)
+    Xs = _cuda(_oracle_stencils(p, q))
     rng = np.random.default_rng(11)
     Xr = _cuda(rng.uniform(-1, 1, (4099, 5)))
     wpath = os.path.join(ROOT, "paper_2409_10729_gb300", "gate_weights.npy")
@@ -228,10 +262,11 @@ def test_tensor_core_logits_match_fp32_network():
             mfc.mlp_forward_tc(X, T, ztc)
             z64 = O.mlp_forward(th.astype(np.float64), X.cpu().numpy().astype(np.float64))
             a, b = ztc.cpu().numpy(), z32.cpu().numpy()
-            assert np.max(np.abs(b - z64)) <= 1e-4 * max(1.0, np.max(np.abs(z64)))
-            # fp16 operands: a few 1e-3 of the logit scale
-            assert np.max(np.abs(a - z64)) <= 2e-2 * max(1.0, np.max(np.abs(z64)))
-            assert np.mean((a < 0) == (z64 < 0)) > 0.99
+            sc = max(1.0, np.max(np.abs(z64)))
+            assert np.max(np.abs(b - z64)) <= 1e-5 * sc
+            assert np.max(np.abs(a - z64)) <= 1e-5 * sc
+            far = np.abs(z64) > 1e-4
+            assert np.array_equal(a[far] < 0, z64[far] < 0)
 
 
 def test_training_on_gpu_lowers_the_loss():
@@ -246,10 +281,18 @@ def test_training_on_gpu_lowers_the_loss():
 
 
 def test_trained_gate_gain():
-    """The committed trained network on the 3-D shock/droplet case (96^3,
-    30 steps): fraction of cell reconstructions gated linear, time per step
-    against the ungated mixed form, and per-field error against the FP64
-    (plain WENO, oracle-exact) result, next to the mixed form's own error."""
+    """What the trained network gains over the trivial gate.  On the 3-D
+    shock/droplet case (96^3, 30 steps) four runs: FP64 (plain WENO, equal to
+    the oracle bit for bit: the judge), mixed (plain WENO in FP32), the gate
+    with the trained network, and the trivial gate -- the same rule with a
+    network that never fires, so only stencils below the round-off floor go
+    linear.  Reported: fraction of cell reconstructions done with linear
+    weights, time per step, and per-field error against FP64.  The network
+    must gate more reconstructions than the trivial gate, at an error within
+    a small factor of it and of the mixed form.  (On this state about three
+    quarters of the reconstructions are below the round-off floor, and the
+    network, held to a recall of 0.995 on troubled samples, adds a fraction
+    of a percent: it must add something, and it must not cost accuracy.)"""
     import torch
     from paper_2409_10729_gb300 import mfc
     wpath = os.path.join(ROOT, "paper_2409_10729_gb300", "gate_weights.npy")
@@ -259,10 +302,11 @@ def test_trained_gate_gain():
     p, w = I.shock_droplets(96)
     steps = 30
     res = {}
-    for form in ("fp64", "mixed", "gated"):
+    for name, form, wts in (("fp64", "fp64", None), ("mixed", "mixed", None), ("network", "gated", weights),
+                            ("trivial", "gated", _bias_only(10.0))):
         s = mfc.Solver(p, form)
-        if form == "gated":
-            s.set_mlp_weights(weights)
+        if wts is not None:
+            s.set_mlp_weights(wts)
         s.set_state_prim(w)
         s.step_rk3(0.4, 2)                          # warm-up (graph capture)
         s.set_state_prim(w)
@@ -270,64 +314,134 @@ def test_trained_gate_gain():
         t0 = time.perf_counter()
         s.step_rk3(0.4, steps)
         torch.cuda.synchronize()
-        res[form] = {"ms_per_step": (time.perf_counter() - t0) * 1e3 / steps, "q": s.get_state()}
+        res[name] = {"ms_per_step": (time.perf_counter() - t0) * 1e3 / steps, "q": s.get_state()}
         if form == "gated":
-            res[form]["gate"] = s.gate_stats()
+            res[name]["gate"] = s.gate_stats() + (s.gate_flat(),)
         s.close()
     ref = res["fp64"]["q"].reshape(7, -1)
     out = {}
-    for form in ("mixed", "gated"):
-        d = np.abs(res[form]["q"].reshape(7, -1) - ref)
+    for name in ("mixed", "network", "trivial"):
+        d = np.abs(res[name]["q"].reshape(7, -1) - ref)
         scale = np.abs(ref).max(1)
         scale[2:5] = scale[2:5].max()
-        out[form] = {"ms_per_step": round(res[form]["ms_per_step"], 3),
+        out[name] = {"ms_per_step": round(res[name]["ms_per_step"], 3),
                      "rel_linf": (d.max(1) / scale).tolist(),
                      "rel_l1": (d.sum(1) / np.abs(ref).sum(1)).tolist()}
-    gated, fb, cells = res["gated"]["gate"]
-    out["gated"]["fraction_gated"] = gated / cells
-    out["gated"]["fraction_fallback"] = fb / cells
+        if "gate" in res[name]:
+            gated, fb, cells, flat = res[name]["gate"]
+            out[name].update(fraction_gated=gated / cells, fraction_fallback=fb / cells,
+                             fraction_flat_warp_steps=flat / cells)
     print("GATE_GAIN " + json.dumps(out))
-    assert out["gated"]["fraction_gated"] > 0.5
-    mix_l1 = np.array(out["mixed"]["rel_l1"])
-    gat_l1 = np.array(out["gated"]["rel_l1"])
-    assert np.all(gat_l1 <= 20 * mix_l1 + 1e-6)
-    assert np.all(np.isfinite(res["gated"]["q"]))
+    for name in ("network", "trivial"):
+        assert np.all(np.isfinite(res[name]["q"]))
+    net, triv, mix = out["network"], out["trivial"], out["mixed"]
+    # the network gates more than the floor alone (reconstructions above the floor)
+    assert net["fraction_gated"] > triv["fraction_gated"] + 1e-3
+    # at an error within a small factor of the trivial gate's and the mixed form's
+    l1n, l1t, l1m = (np.array(x["rel_l1"]) for x in (net, triv, mix))
+    assert np.all(l1n <= 3.0 * np.maximum(l1t, l1m) + 1e-7)
 
 
-def test_flat_warps_take_the_logit_at_zero_input():
-    """Warp steps whose 32 density and pressure stencils are all exactly flat
-    take the network's output at zero input (their exact input) from one
-    evaluation: on a uniform state every reconstruction is such a step, the
-    trained network calls them smooth, and the RHS is exactly zero; on the
-    shock/droplet case only part of them are."""
-    import torch
+def test_flat_stencils_are_smooth_without_the_network():
+    """Stencils below the round-off floor count as smooth whatever the
+    network says: on a uniform state every reconstruction is such a warp
+    step, a network that calls everything troubled still gates them all, and
+    the RHS is exactly zero; on the shock/droplet case only part of them are,
+    the same part for any network (flatness is a property of the state)."""
     from paper_2409_10729_gb300 import mfc
-    wpath = os.path.join(ROOT, "paper_2409_10729_gb300", "gate_weights.npy")
-    if not os.path.exists(wpath):
-        pytest.skip("no trained gate weights (python -m paper_2409_10729_gb300.train_gate)")
-    weights = np.load(wpath)
-    z0 = torch.empty(64, device="cuda")
-    mfc.mlp_forward_tc(torch.zeros(64, 5, device="cuda"), torch.from_numpy(weights).cuda(), z0)
     p, w = I.shock_droplets(40)
     wu = np.empty_like(w)
     for f in range(w.shape[0]):
         wu[f] = w[f].reshape(-1)[0]                 # the pre-shock air state everywhere
-    g = _gated(p, weights)
+    g = _gated(p, _bias_only(10.0))
     g.set_state_prim(wu)
     L = g.rhs()
     gated, fb, cells = g.gate_stats()
-    assert g.gate_flat() == cells == 3 * 40 ** 3
-    if float(z0[0]) < 0:
-        assert gated == cells and fb == 0
+    assert g.gate_flat() == cells == gated == 3 * 40 ** 3 and fb == 0
     assert np.all(L == 0.0)
     g.set_state_prim(w)
     g.rhs()
     gated, fb, cells = g.gate_stats()
     flat = g.gate_flat()
-    assert 0 < flat < cells
-    # flatness is a property of the state: a never-firing gate sees the same
-    # flat steps on the same state, and still never fires
-    n = _gated(p, _bias_only(10.0))
-    n.set_state_prim(w)
-    n.rhs()
-    assert n.gate_stats()[0] == 0 and n.gate_flat() == flat
+    assert 0 < flat < cells and gated >= flat - fb
+    wpath = os.path.join(ROOT, "paper_2409_10729_gb300", "gate_weights.npy")
+    if os.path.exists(wpath):
+        n = _gated(p, np.load(wpath))
+        n.set_state_prim(w)
+        n.rhs()
+        assert n.gate_flat() == flat and n.gate_stats()[0] >= gated
+
+
+def _lipschitz(th):
+    """Upper bound of |z(x) - z(x')| / max_k |x_k - x'_k| of the network."""
+    th = np.asarray(th, dtype=np.float64)
+    W1 = np.abs(th[0:160].reshape(32, 5))
+    W2 = np.abs(th[192:1216].reshape(32, 32))
+    w3 = np.abs(th[1248:1280])
+    return float(w3 @ W2 @ W1 @ np.ones(5))
+
+
+def test_gated_rhs_matches_the_oracle_gate():
+    """The fused gate on the tensor cores against the oracle's gated RHS
+    (FP64 primitives, FP64 network, the same rule) on a 96^3 shock/droplet
+    state advanced 30 steps by the oracle, with the trained weights.
+
+    Decisions are compared cell by cell and direction by direction.  The two
+    sides read the stencils in different precisions (the gated form's FP32
+    state against FP64), so a decision may legitimately differ only near one
+    of its thresholds: a flat ratio within 1e-3 of 1, a logit within the
+    bound of what the FP32 input rounding can move it (network Lipschitz
+    bound x 2^-18 (1 + 1/(floor x ratio)), plus 1e-4), or a linear face
+    within FP32 rounding of admissibility (relative 1e-5 for rho and c^2,
+    absolute 2^-21 for alpha1 and 1 - alpha1).  Elsewhere they must be
+    equal, and the near-threshold cells must be rare.  Where a cell's decision and its
+    neighbours' along every direction agree, its RHS must equal the oracle's
+    to the mixed form's FP32 accuracy (1e-5 of the flux scale)."""
+    from paper_2409_10729_gb300 import mfc
+    wpath = os.path.join(ROOT, "paper_2409_10729_gb300", "gate_weights.npy")
+    if not os.path.exists(wpath):
+        pytest.skip("no trained gate weights (python -m paper_2409_10729_gb300.train_gate)")
+    weights = np.load(wpath)
+    p, w = I.shock_droplets(96)
+    q, _ = O.run_cfl(p, O.prim_to_cons(p, w), 0.4, 30)
+    Lo, deco, info = O.rhs_gated(p, q, weights.astype(np.float64), mfc.MFC_GATE_FLOOR)
+    g = _gated(p, weights)
+    g.set_state(q)
+    L, dec = g.gate_rhs()
+    g.close()
+
+    Lnet = _lipschitz(weights)
+    ratio = info[..., 2:4]
+    zo = info[..., 0:2]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        margin = Lnet * 2.0 ** -18 * (1.0 + 1.0 / (mfc.MFC_GATE_FLOOR * ratio)) + 1e-4
+        near = (np.abs(ratio - 1.0) <= 1e-3).any(-1)
+        near |= (~np.isnan(zo) & (np.abs(zo) <= margin)).any(-1)
+        adm = info[..., 4:8]
+        near |= (np.abs(adm[..., 0]) <= 1e-5) | (np.abs(adm[..., 3]) <= 1e-5)
+        near |= (np.abs(adm[..., 1]) <= 2.0 ** -21) | (np.abs(adm[..., 2]) <= 2.0 ** -21)
+    mismatch = dec != deco
+    assert not np.any(mismatch & ~near), f"{int((mismatch & ~near).sum())} decisions differ away from thresholds"
+    # the logit bound is wide for stencils just above the floor (their FP32
+    # inputs carry up to 2^-19 / floor of rounding): a few percent of cells
+    assert near.mean() < 0.05
+    assert np.all(np.isin(dec, [0, 1, 2])) and (dec == 1).any() and (dec == 0).any()
+
+    # cells whose reconstructions (own, and both neighbours along each
+    # direction) were decided alike on both sides
+    agree = ~mismatch                                 # [3, z, y, x]
+    ok = np.ones(agree.shape[1:], dtype=bool)
+    for d in range(3):
+        a = agree[d]
+        ax = 2 - d                                    # array axis of direction d
+        ok &= a & np.roll(a, 1, axis=ax) & np.roll(a, -1, axis=ax)
+    S = O.max_wavespeed(p, q)
+    scale = np.maximum(np.abs(Lo).reshape(7, -1).max(1), np.abs(q).reshape(7, -1).max(1) * S)
+    err = np.abs(L - Lo).reshape(7, -1)[:, ok.reshape(-1)].max(1) / scale
+    assert ok.mean() > 0.99
+    assert err.max() <= 1e-5, err
+    assert np.all(np.isfinite(L))
+    print("GATE_PARITY " + json.dumps({"cells": int(dec[0].size), "near_threshold": float(near.mean()),
+                                       "mismatch": int(mismatch.sum()), "compared_rhs": float(ok.mean()),
+                                       "rhs_err": err.tolist(),
+                                       "fractions": [float((dec == k).mean()) for k in (0, 1, 2)]}))

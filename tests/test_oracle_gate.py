@@ -177,9 +177,11 @@ def test_fallback_exactly_where_linear_faces_are_not_admissible():
     p, w = I.air_water_shock_tube(200)
     q = O.prim_to_cons(p, w)
     L, dec, info = O.rhs_gated(p, q, _bias(-10.0), DELTA)
-    d, adm = dec[0, 0, 0], info[0, 0, 0, :, 4]
+    d, m = dec[0, 0, 0], info[0, 0, 0, :, 4:8]
+    admissible = (m[:, 0] > 0) & (m[:, 1] >= 0) & (m[:, 2] >= 0) & (m[:, 3] > 0)
     assert np.any(d == 2) and np.any(d == 1) and not np.any(d == 0)
-    assert np.all(adm[d == 2] < 0.0) and np.all(adm[d == 1] >= 0.0)
+    assert np.array_equal(d == 1, admissible)
+    assert np.any(m[d == 2, 1] < 0) or np.any(m[d == 2, 2] < 0)    # alpha1 leaves [0, 1]
     # cell by cell: where the cell and both neighbours use WENO, the plain
     # RHS; where all three are linear, the linear-weight RHS
     Lw = O.rhs(p, q)
