@@ -96,7 +96,9 @@ __device__ __forceinline__ void mixture(const EosR<R, NF>& e, const R* a, R& G, 
 //   left:  (5 d2 - 2 d1)/6, (d2 + 2 d3)/6, (4 d3 - d4)/6
 //   right: (d1 - 4 d2)/6, -(2 d2 + d3)/6, (2 d4 - 5 d3)/6
 // (the same polynomials as the textbook forms), so uniform data reconstructs
-// exactly and both faces share one reciprocal.
+// exactly.  FP64: product-form weights and one reciprocal for both faces.
+// FP32: weights relative to the smoothest stencil, the linear weights and
+// the 1/6 folded into the corrections, one fast reciprocal per face.
 template <typename R>
 __device__ __forceinline__ void weno5(R v0, R v1, R v2, R v3, R v4, R eps, R& vm, R& vp) {
     const R c13 = R(13.0 / 12.0);
@@ -122,6 +124,24 @@ __device__ __forceinline__ void weno5(R v0, R v1, R v2, R v3, R v4, R eps, R& vm
         m0 = __fdividef(smin, s0);
         m1 = __fdividef(smin, s1);
         m2 = __fdividef(smin, s2);
+        // face values v_i + sum_k d_k m_k c_k / sum_k d_k m_k with the linear
+        // weights d_k and the 1/6 of the candidates folded into the
+        // corrections c_k, and one reciprocal per face
+        const R t1 = R(0.6) * m1;
+        const R Dm = fmaf(R(0.1), m0, fmaf(R(0.3), m2, t1));
+        const R Dp = fmaf(R(0.3), m0, fmaf(R(0.1), m2, t1));
+        const R d2x02 = R(0.2) * d2, d3x02 = R(0.2) * d3;
+        const R cm0 = fmaf(R(0.5 / 6.0), d2, R(-0.2 / 6.0) * d1);   // 0.1 (5 d2 - 2 d1)/6
+        const R cm1 = fmaf(R(0.1), d2, d3x02);                      // 0.6 (d2 + 2 d3)/6
+        const R cm2 = fmaf(R(-0.05), d4, d3x02);                    // 0.3 (4 d3 - d4)/6
+        const R cp0 = fmaf(R(0.05), d1, -d2x02);                    // 0.3 (d1 - 4 d2)/6
+        const R cp1 = fmaf(R(-0.1), d3, -d2x02);                    // -0.6 (2 d2 + d3)/6
+        const R cp2 = fmaf(R(0.2 / 6.0), d4, R(-0.5 / 6.0) * d3);   // 0.1 (2 d4 - 5 d3)/6
+        const R Nm = fmaf(m0, cm0, fmaf(m1, cm1, m2 * cm2));
+        const R Np = fmaf(m0, cp0, fmaf(m1, cp1, m2 * cp2));
+        vm = fmaf(Nm, __fdividef(R(1), Dm), v2);
+        vp = fmaf(Np, __fdividef(R(1), Dp), v2);
+        return;
     }
     R am0 = R(0.1) * m0, am1 = R(0.6) * m1, am2 = R(0.3) * m2;
     R ap0 = R(0.3) * m0, ap1 = R(0.6) * m1, ap2 = R(0.1) * m2;
