@@ -87,6 +87,8 @@ struct SweepArgs {
     int order;            // WENO order, 3 or 5
     int periodic;         // along the sweep direction
     int seg;              // cells per thread along the sweep direction (set at launch)
+    long long nwarps;     // > 0: balanced mapping, the launch's warps split the
+                          // pencil cells evenly (set at launch); 0: seg mapping
     int dry;              // 1: only pick the launch shape (fills the occupancy caches), launch nothing
     int stage;            // 1, 2, 3
     DevCtrl* ctrl;
@@ -178,6 +180,32 @@ __host__ __device__ constexpr int sweep_threads(int dir) { return dir == 0 ? 32 
 #ifndef MFC_MIN_WAVES
 #define MFC_MIN_WAVES 6
 #endif
+// Balanced work split (default): the launch has exactly MFC_BAL_WAVES times
+// the device's resident warps, and warp w takes cells [w T / W, (w + 1) T / W)
+// of the T = (pencil groups x cells per pencil) cells in pencil-group order --
+// one or more pieces of consecutive pencil groups -- so every warp does the
+// same work and no partial last wave is left.  Warps take at least
+// MFC_BAL_MIN_CELLS cells (small grids launch fewer warps).  Used by the
+// forms where it measured faster: FP64 (256^3: 0.956 -> 0.913 ns), FP64-fast
+// (0.552 -> 0.523) and the mixed form with more than two fluids (0.0179 ->
+// 0.0171).  The two-fluid mixed form keeps the seg mapping: its sweeps are
+// register-capped, and the piece loop cost more than the balance gained
+// (512^3: 0.0149 -> 0.0170); so does the gated form, whose cost per warp
+// depends on the data (warp steps with all stencils flat skip the network),
+// where many short blocks let the block scheduler even it out.  0: the seg
+// mapping everywhere (and always for MFC_TMA_YZ sweeps).
+#ifndef MFC_BALANCE
+#define MFC_BALANCE 1
+#endif
+#ifndef MFC_BAL_WAVES
+#define MFC_BAL_WAVES 1
+#endif
+#ifndef MFC_BAL_MIN_CELLS
+#define MFC_BAL_MIN_CELLS 32
+#endif
+__host__ __device__ constexpr bool sweep_balanced(int form, int nf) {
+    return MFC_BALANCE && (form == FORM_FP64_EXACT || form == FORM_FP64_FAST || (form == FORM_MIXED && nf > 2));
+}
 #ifndef MFC_MIN_BLOCKS_FP64
 #define MFC_MIN_BLOCKS_FP64 1
 #endif
@@ -202,6 +230,14 @@ __host__ __device__ constexpr int sweep_threads(int dir) { return dir == 0 ? 32 
 #ifndef MFC_PREFETCH
 #define MFC_PREFETCH 1
 #endif
+
+// Cells of a sweep counted in warp units: pencil groups (32 adjacent pencils)
+// times cells per pencil.
+__host__ __device__ inline long long sweep_group_cells(int dir, const int* n) {
+    int na = dir == 0 ? n[1] : n[0];
+    int nb = dir == 2 ? n[1] : n[2];
+    return (long long)((na + 31) / 32) * nb * n[dir];
+}
 
 __host__ __device__ inline long long sweep_warps(int dir, const int* n, int seg) {
     int na = dir == 0 ? n[1] : n[0];

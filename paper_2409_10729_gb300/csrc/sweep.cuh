@@ -10,7 +10,9 @@
 // third stage, reduces the CFL wave speed of the new state.
 //
 // Thread mapping.  A warp owns 32 adjacent pencils along d and a segment of
-// `seg` cells of each.  For d = y, z the 32 lanes run along x, so every load
+// `seg` cells of each -- or, in the balanced split, an even share of all the
+// sweep's cells, one or more such segments of consecutive pencil groups
+// (sweep_balanced).  For d = y, z the 32 lanes run along x, so every load
 // is one coalesced row.  For d = x the lanes run along y: each lane loads
 // its own row, whose 32-byte sector stays in L1 for the lane's next cells,
 // and the RHS goes out through a shared-memory tile as whole sectors.  Each
@@ -544,147 +546,45 @@ sweep_kernel(const SweepArgs a, const __grid_constant__ CUtensorMap tmap) {
     const long long sa = DIR == 0 ? (long long)n0 : 1LL;
     const long long sb = DIR == 2 ? (long long)n0 : (long long)n0 * n1;
     const long long ss = DIR == 0 ? 1LL : (DIR == 1 ? (long long)n0 : (long long)n0 * n1);
-    const int seg = a.seg;
     const long long nchunk = (na + 31) >> 5;
-    const long long nseg = (ns + seg - 1) / seg;
     const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (warp >= nchunk * nseg * nb) return;  // uniform over the warp
-    const int chunk = (int)(warp % nchunk);
-    const long long rest = warp / nchunk;
-    const int segi = (int)(rest % nseg);
-    const int b = (int)(rest / nseg);
-    const int ia = chunk * 32 + lane;
-    const bool active = ia < na;
-    const int s0 = segi * seg;
-    const int s1 = min(s0 + seg, ns);
-    // inactive lanes follow a valid pencil so that every address is in bounds;
-    // their results are discarded
-    const long long base = (long long)(active ? ia : na - 1) * sa + (long long)b * sb;
+    // This warp's cells in pencil-group order: group g = chunk + nchunk b
+    // (32 adjacent pencils), cell j along the pencil at index g ns + j.
+    // Balanced mapping: an even share of all of them, which may span the end
+    // of one group and the start of the next (one piece each).  Seg mapping:
+    // one segment of `seg` cells of one group.
+    // (Forms on the seg mapping only, sweep_balanced false, run the piece loop
+    // once on gseg, sseg0, sseg1.)
+    constexpr bool BAL = sweep_balanced(FORM, NF);
+    long long r0, r1, gseg = 0;
+    int sseg0 = 0, sseg1 = 0;
+    if (BAL && a.nwarps > 0) {
+        if (warp >= a.nwarps) return;  // uniform over the warp
+        const long long T = nchunk * nb * ns;
+        r0 = warp * T / a.nwarps;
+        r1 = (warp + 1) * T / a.nwarps;
+    } else {
+        const int seg = a.seg;
+        const long long nseg = (ns + seg - 1) / seg;
+        if (warp >= nchunk * nseg * nb) return;  // uniform over the warp
+        const long long rest = warp / nchunk;
+        gseg = warp % nchunk + nchunk * (rest / nseg);
+        sseg0 = (int)(rest % nseg) * seg;
+        sseg1 = min(sseg0 + seg, ns);
+        r0 = gseg * ns + sseg0;
+        r1 = gseg * ns + sseg1;
+    }
     const long long nc = a.ncell;
     const R inv_dx = R(a.inv_dx[DIR]);
     const R eps = R(a.eps);
     const EosR<R, NF> er(a.eos);
     const R* __restrict__ qin = static_cast<const R*>(a.qin);
-
-    // Values of loaded cell k (index s0 - 3 + k along the pencil) -> v[].
-    // Along y and z the warp's 32 loads form one coalesced row per field;
-    // along x each lane reads its own row, and the 32-byte sector it brings
-    // into L1 serves the lane's next CH - 1 cells.
-    // TMA staging: interior segments (no ghost cell) of launches given a
-    // tensor map read their cells from the warp's shared-memory slots; chunk
-    // ck (cells s0 - 3 + ck TC ..) lands in slot ck & 1, and starting to read
-    // chunk ck refills the other slot with chunk ck + 1.  Waits are bounded:
-    // a box that never lands sets status bit 2 instead of hanging.
     const int wib = threadIdx.x >> 5;
-    const int kcells = s1 - s0 + 6;
-    const bool use_tma = TMA && a.tmap && s0 >= 3 && s1 + 3 <= ns;
-    bool tma_fail = false;
-    auto tma_issue = [&](int ck) {   // one lane
-        if constexpr (TMA) {
-            uint64_t* bar = tbar + wib * 2 + (ck & 1);
-            float* dst = tbuf + (wib * 2 + (ck & 1)) * TSLOT;
-            mbar_expect_tx(bar, (unsigned)(TSLOT * sizeof(float)));
-            const int jc = s0 - 3 + ck * TC;
-#pragma unroll
-            for (int f = 0; f < NL; ++f) {
-                if constexpr (DIR == 1) tma_load_4d(dst + f * TC * 32, &tmap, chunk * 32, jc, b, LS::field(f), bar);
-                else tma_load_4d(dst + f * TC * 32, &tmap, chunk * 32, b, jc, LS::field(f), bar);
-            }
-        }
-    };
-    if constexpr (TMA) {
-        if (use_tma) {
-            if (lane == 0) {
-                mbar_init(tbar + wib * 2, 1);
-                mbar_init(tbar + wib * 2 + 1, 1);
-                asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-            }
-            __syncwarp();
-            if (lane == 0) tma_issue(0);
-        }
-    }
-
-    // FP32 x sweep with rows of a multiple of 4 cells: 16-byte aligned rows,
-    // loaded four cells at a time (cells are fetched in order along the row)
-    constexpr bool XVEC = MIXED && DIR == 0 && MFC_XVEC;
-    const bool xvec_ok = XVEC && (n0 & 3) == 0;
-    float xq[XVEC ? NL : 1][3];
-    int xpend = 0;
-
-    // A ghost cell beyond a side that borders another block (block
-    // decomposition) comes from that side's halo buffer; any other from the
-    // BC index map.  j is the same for the whole warp.
-    auto fetch = [&](int k, R* v) {
-        if constexpr (TMA) {
-            if (use_tma) {
-                const int ck = k / TC, cc = k - ck * TC;
-                if (cc == 0) {
-                    bool ok = false;
-                    for (int it = 0; it < (1 << 22) && !ok; ++it) ok = mbar_try_wait(tbar + wib * 2 + (ck & 1), (ck >> 1) & 1);
-                    tma_fail |= !ok;
-                    if ((ck + 1) * TC < kcells) {
-                        // every lane's reads of the slot being refilled (chunk
-                        // ck - 1) are ordered before the copy that overwrites it
-                        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-                        __syncwarp();
-                        if (lane == 0) tma_issue(ck + 1);
-                    }
-                }
-                const float* src = tbuf + (wib * 2 + (ck & 1)) * TSLOT + cc * 32 + lane;
-#pragma unroll
-                for (int f = 0; f < NL; ++f) v[f] = src[f * TC * 32];
-                return;
-            }
-        }
-        const int j = s0 - 3 + k;
-        if constexpr (XVEC) {
-            // FP32 x sweep: four cells of the lane's row per 16-byte load, the
-            // three not yet used kept in registers for the next steps
-            if (xpend > 0) {
-#pragma unroll
-                for (int f = 0; f < NL; ++f) {
-                    v[f] = xq[f][0];
-                    xq[f][0] = xq[f][1];
-                    xq[f][1] = xq[f][2];
-                }
-                --xpend;
-                return;
-            }
-            if (xvec_ok && (j & 3) == 0 && j >= 0 && j + 3 < ns) {
-#pragma unroll
-                for (int f = 0; f < NL; ++f) {
-                    const float4 t = __ldg(reinterpret_cast<const float4*>(qin + LS::field(f) * nc + base + j));
-                    v[f] = t.x;
-                    xq[f][0] = t.y;
-                    xq[f][1] = t.z;
-                    xq[f][2] = t.w;
-                }
-                xpend = 3;
-                return;
-            }
-        }
-        const R* h = j < 0 ? static_cast<const R*>(a.hlo) : (j >= ns ? static_cast<const R*>(a.hhi) : nullptr);
-        if (h) {
-            // the pencil's position in the plane normal to DIR, from its first
-            // cell `base` (x fastest): y + n1 z along x, x + n0 z along y, x + n0 y along z
-            long long p;
-            if constexpr (DIR == 0) p = base / n0;
-            else if constexpr (DIR == 1) p = base % n0 + (long long)n0 * (base / ((long long)n0 * n1));
-            else p = base;
-            const long long hc = (long long)(j < 0 ? j + 3 : j - ns) * a.hplane + p;
-#pragma unroll
-            for (int f = 0; f < NL; ++f) v[f] = __ldg(h + (long long)LS::field(f) * 3 * a.hplane + hc);
-        } else {
-            const long long c = base + (long long)bc_index(j, ns, a.periodic) * ss;
-#pragma unroll
-            for (int f = 0; f < NL; ++f) v[f] = __ldg(qin + LS::field(f) * nc + c);
-        }
-    };
 
     constexpr bool PREFETCH = MFC_PREFETCH != 0;
     constexpr bool EPI_PREFETCH = PREFETCH && MIXED;
-    bool bad = false;
+    bool bad_any = false, tma_fail = false;
     R smax = R(0);
     unsigned n_gated = 0, n_fallback = 0, n_cells = 0, n_flat = 0;
     double dt = 0.0;
@@ -697,289 +597,430 @@ sweep_kernel(const SweepArgs a, const __grid_constant__ CUtensorMap tmap) {
     const float dt32 = float(dt);
     const float kfac = a.stage == 2 ? 0.25f : (2.0f / 3.0f);
 
-    R W[5][NEQ];
-#pragma unroll
-    for (int k = 0; k < 5; ++k) {
-        R v[NL];
-        fetch(k, v);
-        if constexpr (EXACT) exact::cons_to_prim<NDIM, NF>(a.eos, v, W[k]);
-        else to_prim<NDIM, NF>(er, v, W[k]);
-        bad |= !(mix_rho<NF>(W[k]) > R(0));
-    }
-    // FP64 reference-order form: the smoothness indicators' curvature terms
-    // of the window's stencils {i-2..i}, {i-1..i+1} (cell i = window centre),
-    // carried along the pencil so that each is formed once (exact::curv)
-    constexpr bool TCARRY = EXACT && !GATED && !NU && NF == 2;
-    double Tm[TCARRY ? NEQ : 1], T0[TCARRY ? NEQ : 1];
-    if constexpr (TCARRY) {
-#pragma unroll
-        for (int f = 0; f < NEQ; ++f) {
-            Tm[f] = exact::curv(W[0][f], W[1][f], W[2][f]);
-            T0[f] = exact::curv(W[1][f], W[2][f], W[3][f]);
+    for (long long r = r0; r < r1;) {
+        long long g = gseg;
+        int s0 = sseg0, s1 = sseg1;
+        if constexpr (BAL) {
+            g = r / ns;
+            s0 = (int)(r - g * ns);
+            s1 = (int)min((long long)ns, r1 - g * ns);
         }
-    }
-    R vmPrev[NEQ], Fprev[NEQ];
-    R ufPrev = R(0), alphaCell[NA];
-#pragma unroll
-    for (int i = 0; i < NA; ++i) alphaCell[i] = R(0);
-#pragma unroll
-    for (int f = 0; f < NEQ; ++f) vmPrev[f] = Fprev[f] = R(0);
+        r = g * ns + s1;
+        const int chunk = (int)(g % nchunk);
+        const int b = (int)(g / nchunk);
+        const int ia = chunk * 32 + lane;
+        const bool active = ia < na;
+        // inactive lanes follow a valid pencil so that every address is in bounds;
+        // their results are discarded
+        const long long base = (long long)(active ? ia : na - 1) * sa + (long long)b * sb;
+        bool bad = false;
+        unsigned p_gated = 0, p_fallback = 0, p_cells = 0, p_flat = 0;
 
-    for (int j = s0 - 1; j <= s1; ++j) {
-        // the cell that enters the window at the end of this iteration: its
-        // loads are issued now and complete under this iteration's arithmetic
-        R vnext[NL];
-        if (PREFETCH && j < s1) fetch(j + 3 - (s0 - 3), vnext);
-        // the FP32 forms also issue the stage-update operands of the cell
-        // this iteration completes (cell j - 1) here, ahead of the stencil work
-        R accp[NEQ], qkp[NEQ];
-        double qnp[NEQ];
-        if constexpr (EPI_PREFETCH) {
-            if (j > s0) {
-                const long long c = base + (long long)(j - 1) * ss;
-                if constexpr (NDIM > 1 && MODE != SW_FIRST) {
-                    const R* acc = static_cast<const R*>(a.acc);
+        // Values of loaded cell k (index s0 - 3 + k along the pencil) -> v[].
+        // Along y and z the warp's 32 loads form one coalesced row per field;
+        // along x each lane reads its own row, and the 32-byte sector it brings
+        // into L1 serves the lane's next CH - 1 cells.
+        // TMA staging: interior segments (no ghost cell) of launches given a
+        // tensor map read their cells from the warp's shared-memory slots; chunk
+        // ck (cells s0 - 3 + ck TC ..) lands in slot ck & 1, and starting to read
+        // chunk ck refills the other slot with chunk ck + 1.  Waits are bounded:
+        // a box that never lands sets status bit 2 instead of hanging.
+        const int kcells = s1 - s0 + 6;
+        const bool use_tma = TMA && a.tmap && a.nwarps == 0 && s0 >= 3 && s1 + 3 <= ns;
+        auto tma_issue = [&](int ck) {   // one lane
+            if constexpr (TMA) {
+                uint64_t* bar = tbar + wib * 2 + (ck & 1);
+                float* dst = tbuf + (wib * 2 + (ck & 1)) * TSLOT;
+                mbar_expect_tx(bar, (unsigned)(TSLOT * sizeof(float)));
+                const int jc = s0 - 3 + ck * TC;
 #pragma unroll
-                    for (int f = 0; f < NEQ; ++f) accp[f] = acc[f * nc + c];
+                for (int f = 0; f < NL; ++f) {
+                    if constexpr (DIR == 1) tma_load_4d(dst + f * TC * 32, &tmap, chunk * 32, jc, b, LS::field(f), bar);
+                    else tma_load_4d(dst + f * TC * 32, &tmap, chunk * 32, b, jc, LS::field(f), bar);
                 }
-                if constexpr (MODE == SW_LAST_RK) {
-#pragma unroll
-                    for (int f = 0; f < NEQ; ++f) qnp[f] = __ldg(a.qn + f * nc + c);
-                    if (a.stage != 1) {
-#pragma unroll
-                        for (int f = 0; f < NEQ; ++f) qkp[f] = a.dinc[f * nc + c];   // D_(k-1)
-                    }
+            }
+        };
+        if constexpr (TMA) {
+            if (use_tma) {
+                if (lane == 0) {
+                    mbar_init(tbar + wib * 2, 1);
+                    mbar_init(tbar + wib * 2 + 1, 1);
+                    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
                 }
+                __syncwarp();
+                if (lane == 0) tma_issue(0);
             }
         }
-        R vm[NEQ], vp[NEQ];
-        bool use_weno = true;
-        if constexpr (GATED) {
-            // gate: linear weights when the density and the pressure stencil
-            // are both smooth -- flat (below the round-off floor), or called
-            // smooth by the network (logit < 0) -- and the faces stay physical;
-            // all 32 lanes take part in the tensor-core evaluation, which a
-            // warp step whose stencils are all flat skips
-            float sr[5], sp[5], xr[5], xp[5], zr = -1.f, zp = -1.f;
-#pragma unroll
-            for (int k = 0; k < 5; ++k) {
-                sr[k] = W[k][0] + W[k][1];
-                sp[k] = W[k][IE];
-            }
-            const bool live_r = gate_input(sr, xr), live_p = gate_input(sp, xp);
-            const bool warp_flat = !__any_sync(0xffffffffu, live_r || live_p);
-            if (!warp_flat)
-                gate_logits(gsm[0], gtile + (threadIdx.x >> 5) * 128, xr, xp, live_r, live_p, true, zr, zp);
-            const bool smooth = (!live_r || zr < 0.f) && (!live_p || zp < 0.f);
-            if (smooth) {
-#pragma unroll
-                for (int f = 0; f < NEQ; ++f) linear5(W[0][f], W[1][f], W[2][f], W[3][f], W[4][f], vm[f], vp[f]);
-                use_weno = !(face_ok<NDIM>(er, vm) && face_ok<NDIM>(er, vp));
-            }
-            if (j >= s0 && j < s1) {   // count each cell once (not the segment halos)
-                n_fallback += smooth && use_weno;
-                n_gated += smooth && !use_weno;
-                n_cells += 1;
-                n_flat += warp_flat;
-                if (a.gate_dec && active) a.gate_dec[base + (long long)j * ss] = smooth ? (use_weno ? 2 : 1) : 0;
-            }
-        }
-        if (use_weno) {
-            if (NU && a.tab) {   // non-uniform direction: this cell's table (uniform over the warp)
-                const R* T = static_cast<const R*>(a.tab) + (long long)(j + 1) * kTabDoubles;
-#pragma unroll
-                for (int f = 0; f < NEQ; ++f) weno5_tab<R>(T, W[0][f], W[1][f], W[2][f], W[3][f], W[4][f], eps, vm[f], vp[f]);
-            } else if (GATED || a.order == 5) {
-#pragma unroll
-                for (int f = 0; f < NEQ; ++f) {
-                    if constexpr (TCARRY) {
-                        const double Tp = exact::curv(W[2][f], W[3][f], W[4][f]);
-                        exact::weno5_t(a.eps, W[0][f], W[1][f], W[2][f], W[3][f], W[4][f], Tm[f], T0[f], Tp,
-                                       vm[f], vp[f]);
-                        Tm[f] = T0[f];
-                        T0[f] = Tp;
-                    } else if constexpr (EXACT) {
-                        exact::weno5(a.eps, W[0][f], W[1][f], W[2][f], W[3][f], W[4][f], vm[f], vp[f]);
-                    } else {
-                        weno5(W[0][f], W[1][f], W[2][f], W[3][f], W[4][f], eps, vm[f], vp[f]);
-                    }
-                }
-            } else {   // WENO3 (uniform over the launch): cells i-1 .. i+1 of the window
-#pragma unroll
-                for (int f = 0; f < NEQ; ++f) {
-                    if constexpr (EXACT) exact::weno3(a.eps, W[1][f], W[2][f], W[3][f], vm[f], vp[f]);
-                    else weno3(W[1][f], W[2][f], W[3][f], eps, vm[f], vp[f]);
-                }
-            }
-        }
-        if (j >= s0) {
-            R F[NEQ], uf;
-            if constexpr (EXACT) bad |= exact::hllc<NDIM, DIR, NF>(a.eos, vmPrev, vp, F, uf);
-            else bad |= hllc<NDIM, DIR, R, NF>(er, vmPrev, vp, F, uf);
-            if (j > s0 && (active || OSTAGE_ON)) {
-                // cell i = j - 1 is complete: faces i-1/2 (Fprev) and i+1/2 (F)
-                R L[NEQ];
-                if constexpr (EXACT) {
-                    // (F_{i-1/2} - F_{i+1/2})/dx, then + alpha1 (u_f+ - u_f-)/dx
-                    double dx = a.dx[DIR], rdx = a.rdx[DIR];
-                    if (NU && a.cw[DIR]) {   // non-uniform: the cell's own width
-                        dx = __ldg(a.cw[DIR] + (j - 1));
-                        rdx = __ldg(a.crw[DIR] + (j - 1));
-                    }
-#pragma unroll
-                    for (int f = 0; f < NEQ; ++f) L[f] = exact::div_rcp(Fprev[f] - F[f], dx, rdx);
-#pragma unroll
-                    for (int i = 0; i < NA; ++i)
-                        L[IA + i] = L[IA + i] + exact::div_rcp(alphaCell[i] * (uf - ufPrev), dx, rdx);
-                } else {
-                    R idx = inv_dx;
-                    if (NU && a.cw[DIR]) {
-                        if constexpr (sizeof(R) == 8) idx = __ldg(a.crw[DIR] + (j - 1));
-                        else idx = __ldg(a.crw32[DIR] + (j - 1));
-                    }
-#pragma unroll
-                    for (int f = 0; f < NEQ; ++f) L[f] = (Fprev[f] - F[f]) * idx;
-#pragma unroll
-                    for (int i = 0; i < NA; ++i) L[IA + i] += alphaCell[i] * (uf - ufPrev) * idx;
-                }
-                const long long c = base + (long long)(j - 1) * ss;
-                if constexpr (OSTAGE_ON) {
-                    R* o = ostage + (threadIdx.x >> 5) * OSTAGE + lane * PITCH + ((j - 1) & (CH - 1));
-#pragma unroll
-                    for (int f = 0; f < NEQ; ++f) o[f * 32 * PITCH] = L[f];
-                } else if constexpr (MODE == SW_FIRST) {
-                    R* acc = static_cast<R*>(a.acc);
-#pragma unroll
-                    for (int f = 0; f < NEQ; ++f) acc[f * nc + c] = L[f];
-                } else if constexpr (MODE == SW_MID) {
-                    R* acc = static_cast<R*>(a.acc);
-#pragma unroll
-                    for (int f = 0; f < NEQ; ++f) acc[f * nc + c] = (EPI_PREFETCH ? accp[f] : acc[f * nc + c]) + L[f];
-                } else if constexpr (MODE == SW_LAST_RHS) {
-                    const R* acc = static_cast<const R*>(a.acc);
-                    double* out = static_cast<double*>(a.qout);
-#pragma unroll
-                    for (int f = 0; f < NEQ; ++f) {
-                        R tot = NDIM > 1 ? (EPI_PREFETCH ? accp[f] : acc[f * nc + c]) + L[f] : L[f];
-                        out[f * nc + c] = double(tot);
-                    }
-                } else {  // SW_LAST_RK
-                    const R* acc = static_cast<const R*>(a.acc);
-                    double qnew[NEQ];
-#pragma unroll
-                    for (int f = 0; f < NEQ; ++f) {
-                        R tot = NDIM > 1 ? (EPI_PREFETCH ? accp[f] : acc[f * nc + c]) + L[f] : L[f];
-                        double qn = EPI_PREFETCH ? qnp[f] : a.qn[f * nc + c];
-                        if constexpr (MIXED) {
-                            // D_k in FP32 from D_(k-1) and the FP32 L; q^(k) = q^n + D_k in FP64
-                            float Dk;
-                            if (a.stage == 1) {
-                                Dk = dt32 * float(tot);
-                            } else {
-                                const float Dp = EPI_PREFETCH ? float(qkp[f]) : a.dinc[f * nc + c];
-                                Dk = kfac * fmaf(dt32, float(tot), Dp);
-                            }
-                            if (a.stage != 3) a.dinc[f * nc + c] = Dk;
-                            qnew[f] = qn + f2d_bits(Dk);
-                        } else {
-                            double dL = dt * double(tot);
-                            if (a.stage == 1) {
-                                qnew[f] = qn + dL;
-                            } else {
-                                double qkd = double(qin[f * nc + c]);
-                                if (a.stage == 2)
-                                    qnew[f] = 0.75 * qn + 0.25 * (qkd + dL);
-                                else
-                                    qnew[f] = (1.0 / 3.0) * qn + (2.0 / 3.0) * (qkd + dL);
-                            }
+
+        // FP32 x sweep with rows of a multiple of 4 cells: 16-byte aligned rows,
+        // loaded four cells at a time (cells are fetched in order along the row)
+        constexpr bool XVEC = MIXED && DIR == 0 && MFC_XVEC;
+        const bool xvec_ok = XVEC && (n0 & 3) == 0;
+        float xq[XVEC ? NL : 1][3];
+        int xpend = 0;
+
+        // A ghost cell beyond a side that borders another block (block
+        // decomposition) comes from that side's halo buffer; any other from the
+        // BC index map.  j is the same for the whole warp.
+        auto fetch = [&](int k, R* v) {
+            if constexpr (TMA) {
+                if (use_tma) {
+                    const int ck = k / TC, cc = k - ck * TC;
+                    if (cc == 0) {
+                        bool ok = false;
+                        for (int it = 0; it < (1 << 22) && !ok; ++it) ok = mbar_try_wait(tbar + wib * 2 + (ck & 1), (ck >> 1) & 1);
+                        tma_fail |= !ok;
+                        if ((ck + 1) * TC < kcells) {
+                            // every lane's reads of the slot being refilled (chunk
+                            // ck - 1) are ordered before the copy that overwrites it
+                            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                            __syncwarp();
+                            if (lane == 0) tma_issue(ck + 1);
                         }
                     }
-                    if constexpr (!MIXED) {
+                    const float* src = tbuf + (wib * 2 + (ck & 1)) * TSLOT + cc * 32 + lane;
+#pragma unroll
+                    for (int f = 0; f < NL; ++f) v[f] = src[f * TC * 32];
+                    return;
+                }
+            }
+            const int j = s0 - 3 + k;
+            if constexpr (XVEC) {
+                // FP32 x sweep: four cells of the lane's row per 16-byte load, the
+                // three not yet used kept in registers for the next steps
+                if (xpend > 0) {
+#pragma unroll
+                    for (int f = 0; f < NL; ++f) {
+                        v[f] = xq[f][0];
+                        xq[f][0] = xq[f][1];
+                        xq[f][1] = xq[f][2];
+                    }
+                    --xpend;
+                    return;
+                }
+                if (xvec_ok && (j & 3) == 0 && j >= 0 && j + 3 < ns) {
+#pragma unroll
+                    for (int f = 0; f < NL; ++f) {
+                        const float4 t = __ldg(reinterpret_cast<const float4*>(qin + LS::field(f) * nc + base + j));
+                        v[f] = t.x;
+                        xq[f][0] = t.y;
+                        xq[f][1] = t.z;
+                        xq[f][2] = t.w;
+                    }
+                    xpend = 3;
+                    return;
+                }
+            }
+            const R* h = j < 0 ? static_cast<const R*>(a.hlo) : (j >= ns ? static_cast<const R*>(a.hhi) : nullptr);
+            if (h) {
+                // the pencil's position in the plane normal to DIR, from its first
+                // cell `base` (x fastest): y + n1 z along x, x + n0 z along y, x + n0 y along z
+                long long p;
+                if constexpr (DIR == 0) p = base / n0;
+                else if constexpr (DIR == 1) p = base % n0 + (long long)n0 * (base / ((long long)n0 * n1));
+                else p = base;
+                const long long hc = (long long)(j < 0 ? j + 3 : j - ns) * a.hplane + p;
+#pragma unroll
+                for (int f = 0; f < NL; ++f) v[f] = __ldg(h + (long long)LS::field(f) * 3 * a.hplane + hc);
+            } else {
+                const long long c = base + (long long)bc_index(j, ns, a.periodic) * ss;
+#pragma unroll
+                for (int f = 0; f < NL; ++f) v[f] = __ldg(qin + LS::field(f) * nc + c);
+            }
+        };
+
+        R W[5][NEQ];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            R v[NL];
+            fetch(k, v);
+            if constexpr (EXACT) exact::cons_to_prim<NDIM, NF>(a.eos, v, W[k]);
+            else to_prim<NDIM, NF>(er, v, W[k]);
+            bad |= !(mix_rho<NF>(W[k]) > R(0));
+        }
+        // FP64 reference-order form: the smoothness indicators' curvature terms
+        // of the window's stencils {i-2..i}, {i-1..i+1} (cell i = window centre),
+        // carried along the pencil so that each is formed once (exact::curv)
+        constexpr bool TCARRY = EXACT && !GATED && !NU && NF == 2;
+        double Tm[TCARRY ? NEQ : 1], T0[TCARRY ? NEQ : 1];
+        if constexpr (TCARRY) {
+#pragma unroll
+            for (int f = 0; f < NEQ; ++f) {
+                Tm[f] = exact::curv(W[0][f], W[1][f], W[2][f]);
+                T0[f] = exact::curv(W[1][f], W[2][f], W[3][f]);
+            }
+        }
+        R vmPrev[NEQ], Fprev[NEQ];
+        R ufPrev = R(0), alphaCell[NA];
+#pragma unroll
+        for (int i = 0; i < NA; ++i) alphaCell[i] = R(0);
+#pragma unroll
+        for (int f = 0; f < NEQ; ++f) vmPrev[f] = Fprev[f] = R(0);
+
+        for (int j = s0 - 1; j <= s1; ++j) {
+            // the cell that enters the window at the end of this iteration: its
+            // loads are issued now and complete under this iteration's arithmetic
+            R vnext[NL];
+            if (PREFETCH && j < s1) fetch(j + 3 - (s0 - 3), vnext);
+            // the FP32 forms also issue the stage-update operands of the cell
+            // this iteration completes (cell j - 1) here, ahead of the stencil work
+            R accp[NEQ], qkp[NEQ];
+            double qnp[NEQ];
+            if constexpr (EPI_PREFETCH) {
+                if (j > s0) {
+                    const long long c = base + (long long)(j - 1) * ss;
+                    if constexpr (NDIM > 1 && MODE != SW_FIRST) {
+                        const R* acc = static_cast<const R*>(a.acc);
+#pragma unroll
+                        for (int f = 0; f < NEQ; ++f) accp[f] = acc[f * nc + c];
+                    }
+                    if constexpr (MODE == SW_LAST_RK) {
+#pragma unroll
+                        for (int f = 0; f < NEQ; ++f) qnp[f] = __ldg(a.qn + f * nc + c);
+                        if (a.stage != 1) {
+#pragma unroll
+                            for (int f = 0; f < NEQ; ++f) qkp[f] = a.dinc[f * nc + c];   // D_(k-1)
+                        }
+                    }
+                }
+            }
+            R vm[NEQ], vp[NEQ];
+            bool use_weno = true;
+            if constexpr (GATED) {
+                // gate: linear weights when the density and the pressure stencil
+                // are both smooth -- flat (below the round-off floor), or called
+                // smooth by the network (logit < 0) -- and the faces stay physical;
+                // all 32 lanes take part in the tensor-core evaluation, which a
+                // warp step whose stencils are all flat skips
+                float sr[5], sp[5], xr[5], xp[5], zr = -1.f, zp = -1.f;
+#pragma unroll
+                for (int k = 0; k < 5; ++k) {
+                    sr[k] = W[k][0] + W[k][1];
+                    sp[k] = W[k][IE];
+                }
+                const bool live_r = gate_input(sr, xr), live_p = gate_input(sp, xp);
+                const bool warp_flat = !__any_sync(0xffffffffu, live_r || live_p);
+                if (!warp_flat)
+                    gate_logits(gsm[0], gtile + (threadIdx.x >> 5) * 128, xr, xp, live_r, live_p, true, zr, zp);
+                const bool smooth = (!live_r || zr < 0.f) && (!live_p || zp < 0.f);
+                if (smooth) {
+#pragma unroll
+                    for (int f = 0; f < NEQ; ++f) linear5(W[0][f], W[1][f], W[2][f], W[3][f], W[4][f], vm[f], vp[f]);
+                    use_weno = !(face_ok<NDIM>(er, vm) && face_ok<NDIM>(er, vp));
+                }
+                if (j >= s0 && j < s1) {   // count each cell once (not the segment halos)
+                    p_fallback += smooth && use_weno;
+                    p_gated += smooth && !use_weno;
+                    p_cells += 1;
+                    p_flat += warp_flat;
+                    if (a.gate_dec && active) a.gate_dec[base + (long long)j * ss] = smooth ? (use_weno ? 2 : 1) : 0;
+                }
+            }
+            if (use_weno) {
+                if (NU && a.tab) {   // non-uniform direction: this cell's table (uniform over the warp)
+                    const R* T = static_cast<const R*>(a.tab) + (long long)(j + 1) * kTabDoubles;
+#pragma unroll
+                    for (int f = 0; f < NEQ; ++f) weno5_tab<R>(T, W[0][f], W[1][f], W[2][f], W[3][f], W[4][f], eps, vm[f], vp[f]);
+                } else if (GATED || a.order == 5) {
+#pragma unroll
+                    for (int f = 0; f < NEQ; ++f) {
+                        if constexpr (TCARRY) {
+                            const double Tp = exact::curv(W[2][f], W[3][f], W[4][f]);
+                            exact::weno5_t(a.eps, W[0][f], W[1][f], W[2][f], W[3][f], W[4][f], Tm[f], T0[f], Tp,
+                                           vm[f], vp[f]);
+                            Tm[f] = T0[f];
+                            T0[f] = Tp;
+                        } else if constexpr (EXACT) {
+                            exact::weno5(a.eps, W[0][f], W[1][f], W[2][f], W[3][f], W[4][f], vm[f], vp[f]);
+                        } else {
+                            weno5(W[0][f], W[1][f], W[2][f], W[3][f], W[4][f], eps, vm[f], vp[f]);
+                        }
+                    }
+                } else {   // WENO3 (uniform over the launch): cells i-1 .. i+1 of the window
+#pragma unroll
+                    for (int f = 0; f < NEQ; ++f) {
+                        if constexpr (EXACT) exact::weno3(a.eps, W[1][f], W[2][f], W[3][f], vm[f], vp[f]);
+                        else weno3(W[1][f], W[2][f], W[3][f], eps, vm[f], vp[f]);
+                    }
+                }
+            }
+            if (j >= s0) {
+                R F[NEQ], uf;
+                if constexpr (EXACT) bad |= exact::hllc<NDIM, DIR, NF>(a.eos, vmPrev, vp, F, uf);
+                else bad |= hllc<NDIM, DIR, R, NF>(er, vmPrev, vp, F, uf);
+                if (j > s0 && (active || OSTAGE_ON)) {
+                    // cell i = j - 1 is complete: faces i-1/2 (Fprev) and i+1/2 (F)
+                    R L[NEQ];
+                    if constexpr (EXACT) {
+                        // (F_{i-1/2} - F_{i+1/2})/dx, then + alpha1 (u_f+ - u_f-)/dx
+                        double dx = a.dx[DIR], rdx = a.rdx[DIR];
+                        if (NU && a.cw[DIR]) {   // non-uniform: the cell's own width
+                            dx = __ldg(a.cw[DIR] + (j - 1));
+                            rdx = __ldg(a.crw[DIR] + (j - 1));
+                        }
+#pragma unroll
+                        for (int f = 0; f < NEQ; ++f) L[f] = exact::div_rcp(Fprev[f] - F[f], dx, rdx);
+#pragma unroll
+                        for (int i = 0; i < NA; ++i)
+                            L[IA + i] = L[IA + i] + exact::div_rcp(alphaCell[i] * (uf - ufPrev), dx, rdx);
+                    } else {
+                        R idx = inv_dx;
+                        if (NU && a.cw[DIR]) {
+                            if constexpr (sizeof(R) == 8) idx = __ldg(a.crw[DIR] + (j - 1));
+                            else idx = __ldg(a.crw32[DIR] + (j - 1));
+                        }
+#pragma unroll
+                        for (int f = 0; f < NEQ; ++f) L[f] = (Fprev[f] - F[f]) * idx;
+#pragma unroll
+                        for (int i = 0; i < NA; ++i) L[IA + i] += alphaCell[i] * (uf - ufPrev) * idx;
+                    }
+                    const long long c = base + (long long)(j - 1) * ss;
+                    if constexpr (OSTAGE_ON) {
+                        R* o = ostage + (threadIdx.x >> 5) * OSTAGE + lane * PITCH + ((j - 1) & (CH - 1));
+#pragma unroll
+                        for (int f = 0; f < NEQ; ++f) o[f * 32 * PITCH] = L[f];
+                    } else if constexpr (MODE == SW_FIRST) {
+                        R* acc = static_cast<R*>(a.acc);
+#pragma unroll
+                        for (int f = 0; f < NEQ; ++f) acc[f * nc + c] = L[f];
+                    } else if constexpr (MODE == SW_MID) {
+                        R* acc = static_cast<R*>(a.acc);
+#pragma unroll
+                        for (int f = 0; f < NEQ; ++f) acc[f * nc + c] = (EPI_PREFETCH ? accp[f] : acc[f * nc + c]) + L[f];
+                    } else if constexpr (MODE == SW_LAST_RHS) {
+                        const R* acc = static_cast<const R*>(a.acc);
                         double* out = static_cast<double*>(a.qout);
 #pragma unroll
-                        for (int f = 0; f < NEQ; ++f) out[f * nc + c] = qnew[f];
-                        if (a.stage == 3) {
-                            R s;
-                            double dx3[3], rdx3[3], idx3[3];
-                            cell_geometry<DIR, NU>(a, j - 1, active ? ia : na - 1, b, dx3, rdx3, idx3);
-                            if constexpr (EXACT) {
-                                s = exact::cell_wavespeed<NDIM, NF>(a.eos, qnew, dx3, rdx3, bad);
+                        for (int f = 0; f < NEQ; ++f) {
+                            R tot = NDIM > 1 ? (EPI_PREFETCH ? accp[f] : acc[f * nc + c]) + L[f] : L[f];
+                            out[f * nc + c] = double(tot);
+                        }
+                    } else {  // SW_LAST_RK
+                        const R* acc = static_cast<const R*>(a.acc);
+                        double qnew[NEQ];
+#pragma unroll
+                        for (int f = 0; f < NEQ; ++f) {
+                            R tot = NDIM > 1 ? (EPI_PREFETCH ? accp[f] : acc[f * nc + c]) + L[f] : L[f];
+                            double qn = EPI_PREFETCH ? qnp[f] : a.qn[f * nc + c];
+                            if constexpr (MIXED) {
+                                // D_k in FP32 from D_(k-1) and the FP32 L; q^(k) = q^n + D_k in FP64
+                                float Dk;
+                                if (a.stage == 1) {
+                                    Dk = dt32 * float(tot);
+                                } else {
+                                    const float Dp = EPI_PREFETCH ? float(qkp[f]) : a.dinc[f * nc + c];
+                                    Dk = kfac * fmaf(dt32, float(tot), Dp);
+                                }
+                                if (a.stage != 3) a.dinc[f * nc + c] = Dk;
+                                qnew[f] = qn + f2d_bits(Dk);
                             } else {
-                                double wn[NEQ];
-                                to_prim<NDIM, NF>(er, qnew, wn);
-                                s = cell_wavespeed<NDIM, double, NF>(er, wn, idx3, bad);
+                                double dL = dt * double(tot);
+                                if (a.stage == 1) {
+                                    qnew[f] = qn + dL;
+                                } else {
+                                    double qkd = double(qin[f * nc + c]);
+                                    if (a.stage == 2)
+                                        qnew[f] = 0.75 * qn + 0.25 * (qkd + dL);
+                                    else
+                                        qnew[f] = (1.0 / 3.0) * qn + (2.0 / 3.0) * (qkd + dL);
+                                }
                             }
-                            smax = s > smax ? s : smax;
                         }
-                    } else {
-                        float q32[NEQ];
+                        if constexpr (!MIXED) {
+                            double* out = static_cast<double*>(a.qout);
 #pragma unroll
-                        for (int f = 0; f < NEQ; ++f) q32[f] = d2f_bits(qnew[f]);
-                        float pnew = mixed_pressure<NDIM, NF>(a.eos, qnew, q32);
-                        float* o32 = static_cast<float*>(a.stage == 3 ? a.qout2 : a.qout);
+                            for (int f = 0; f < NEQ; ++f) out[f * nc + c] = qnew[f];
+                            if (a.stage == 3) {
+                                R s;
+                                double dx3[3], rdx3[3], idx3[3];
+                                cell_geometry<DIR, NU>(a, j - 1, active ? ia : na - 1, b, dx3, rdx3, idx3);
+                                if constexpr (EXACT) {
+                                    s = exact::cell_wavespeed<NDIM, NF>(a.eos, qnew, dx3, rdx3, bad);
+                                } else {
+                                    double wn[NEQ];
+                                    to_prim<NDIM, NF>(er, qnew, wn);
+                                    s = cell_wavespeed<NDIM, double, NF>(er, wn, idx3, bad);
+                                }
+                                smax = s > smax ? s : smax;
+                            }
+                        } else {
+                            float q32[NEQ];
 #pragma unroll
-                        for (int f = 0; f < NEQ; ++f) o32[f * nc + c] = q32[f];
-                        o32[NEQ * nc + c] = pnew;
-                        if (a.stage == 3) {
-                            double* o64 = static_cast<double*>(a.qout);
+                            for (int f = 0; f < NEQ; ++f) q32[f] = d2f_bits(qnew[f]);
+                            float pnew = mixed_pressure<NDIM, NF>(a.eos, qnew, q32);
+                            float* o32 = static_cast<float*>(a.stage == 3 ? a.qout2 : a.qout);
 #pragma unroll
-                            for (int f = 0; f < NEQ; ++f) o64[f * nc + c] = qnew[f];
-                            float v[NEQ], wn[NEQ];
+                            for (int f = 0; f < NEQ; ++f) o32[f * nc + c] = q32[f];
+                            o32[NEQ * nc + c] = pnew;
+                            if (a.stage == 3) {
+                                double* o64 = static_cast<double*>(a.qout);
 #pragma unroll
-                            for (int f = 0; f < NEQ; ++f) v[f] = q32[f];
-                            v[IE] = pnew;
-                            to_prim<NDIM, NF>(er, v, wn);
-                            double dx3[3], rdx3[3], idx3[3];
-                            cell_geometry<DIR, NU>(a, j - 1, active ? ia : na - 1, b, dx3, rdx3, idx3);
-                            R s = cell_wavespeed<NDIM, float, NF>(er, wn, idx3, bad);
-                            smax = s > smax ? s : smax;
+                                for (int f = 0; f < NEQ; ++f) o64[f * nc + c] = qnew[f];
+                                float v[NEQ], wn[NEQ];
+#pragma unroll
+                                for (int f = 0; f < NEQ; ++f) v[f] = q32[f];
+                                v[IE] = pnew;
+                                to_prim<NDIM, NF>(er, v, wn);
+                                double dx3[3], rdx3[3], idx3[3];
+                                cell_geometry<DIR, NU>(a, j - 1, active ? ia : na - 1, b, dx3, rdx3, idx3);
+                                R s = cell_wavespeed<NDIM, float, NF>(er, wn, idx3, bad);
+                                smax = s > smax ? s : smax;
+                            }
                         }
+                    }
+                }
+#pragma unroll
+                for (int f = 0; f < NEQ; ++f) Fprev[f] = F[f];
+                ufPrev = uf;
+                if constexpr (OSTAGE_ON) {
+                    // cell i = j - 1 closes a sector (or the segment): the warp writes
+                    // cells max(x0, s0) .. i of its rows, whole sectors per row
+                    const int i = j - 1;
+                    if (j > s0 && ((i & (CH - 1)) == CH - 1 || j == s1)) {
+                        __syncwarp();
+                        const int x0 = i & ~(CH - 1), lo = max(x0, s0);
+                        const int t = lane % CH, x = x0 + t;
+                        const R* o = ostage + (threadIdx.x >> 5) * OSTAGE;
+                        R* acc = static_cast<R*>(a.acc);
+#pragma unroll
+                        for (int k = 0; k < CH; ++k) {
+                            const int r = lane / CH + (32 / CH) * k;
+                            const int row = chunk * 32 + r;
+                            if (x >= lo && x <= i && row < na) {
+                                const long long cc = (long long)row * sa + (long long)b * sb + x;
+#pragma unroll
+                                for (int f = 0; f < NEQ; ++f) acc[f * nc + cc] = o[(f * 32 + r) * PITCH + t];
+                            }
+                        }
+                        __syncwarp();
                     }
                 }
             }
 #pragma unroll
-            for (int f = 0; f < NEQ; ++f) Fprev[f] = F[f];
-            ufPrev = uf;
-            if constexpr (OSTAGE_ON) {
-                // cell i = j - 1 closes a sector (or the segment): the warp writes
-                // cells max(x0, s0) .. i of its rows, whole sectors per row
-                const int i = j - 1;
-                if (j > s0 && ((i & (CH - 1)) == CH - 1 || j == s1)) {
-                    __syncwarp();
-                    const int x0 = i & ~(CH - 1), lo = max(x0, s0);
-                    const int t = lane % CH, x = x0 + t;
-                    const R* o = ostage + (threadIdx.x >> 5) * OSTAGE;
-                    R* acc = static_cast<R*>(a.acc);
+            for (int f = 0; f < NEQ; ++f) vmPrev[f] = vm[f];
 #pragma unroll
-                    for (int k = 0; k < CH; ++k) {
-                        const int r = lane / CH + (32 / CH) * k;
-                        const int row = chunk * 32 + r;
-                        if (x >= lo && x <= i && row < na) {
-                            const long long cc = (long long)row * sa + (long long)b * sb + x;
+            for (int i = 0; i < NA; ++i) alphaCell[i] = W[2][IA + i];
+            if (j < s1) {
 #pragma unroll
-                            for (int f = 0; f < NEQ; ++f) acc[f * nc + cc] = o[(f * 32 + r) * PITCH + t];
-                        }
-                    }
-                    __syncwarp();
-                }
+                for (int k = 0; k < 4; ++k)
+#pragma unroll
+                    for (int f = 0; f < NEQ; ++f) W[k][f] = W[k + 1][f];
+                if (!PREFETCH) fetch(j + 3 - (s0 - 3), vnext);
+                if constexpr (EXACT) exact::cons_to_prim<NDIM, NF>(a.eos, vnext, W[4]);
+                else to_prim<NDIM, NF>(er, vnext, W[4]);
+                bad |= !(mix_rho<NF>(W[4]) > R(0));
             }
         }
-#pragma unroll
-        for (int f = 0; f < NEQ; ++f) vmPrev[f] = vm[f];
-#pragma unroll
-        for (int i = 0; i < NA; ++i) alphaCell[i] = W[2][IA + i];
-        if (j < s1) {
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-#pragma unroll
-                for (int f = 0; f < NEQ; ++f) W[k][f] = W[k + 1][f];
-            if (!PREFETCH) fetch(j + 3 - (s0 - 3), vnext);
-            if constexpr (EXACT) exact::cons_to_prim<NDIM, NF>(a.eos, vnext, W[4]);
-            else to_prim<NDIM, NF>(er, vnext, W[4]);
-            bad |= !(mix_rho<NF>(W[4]) > R(0));
+        // only cells this lane owns count (inactive lanes and segment halos excluded)
+        bad_any |= bad && active;
+        if (active) {
+            n_gated += p_gated;
+            n_fallback += p_fallback;
+            n_cells += p_cells;
+            n_flat += p_flat;
         }
+        if constexpr (!BAL) break;   // the seg mapping gives one piece
     }
-    bad = bad && active;
 
     if constexpr (MODE == SW_LAST_RK) {
         if (a.stage == 3) {
@@ -988,13 +1029,11 @@ sweep_kernel(const SweepArgs a, const __grid_constant__ CUtensorMap tmap) {
                 atomicMax(&a.ctrl->S_bits, (unsigned long long)__double_as_longlong(double(m)));
         }
     }
-    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&a.ctrl->status, 1u);
+    if (__any_sync(0xffffffffu, bad_any) && lane == 0) atomicOr(&a.ctrl->status, 1u);
     if constexpr (TMA) {
         if (__any_sync(0xffffffffu, tma_fail) && lane == 0) atomicOr(&a.ctrl->status, 4u);
     }
     if constexpr (GATED) {
-        // only cells this lane owns count (inactive lanes and segment halos excluded)
-        if (!active) n_gated = n_fallback = n_cells = n_flat = 0;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             n_gated += __shfl_xor_sync(0xffffffffu, n_gated, o);
@@ -1052,9 +1091,26 @@ inline int pick_seg(int dir, const int* n, int threads, long long slots) {
 template <int NDIM, int DIR, int MODE, int FORM, bool NU, int NF>
 cudaError_t launch_kernel(const SweepArgs& a0, cudaStream_t s) {
     constexpr int T = sweep_threads(DIR);
+    constexpr bool TMA = MFC_TMA_YZ && (FORM == FORM_MIXED || FORM == FORM_GATED) && (DIR == 1 || DIR == 2) && !NU;
     SweepArgs a = a0;
-    a.seg = pick_seg(DIR, a.n, T, sweep_slots<NDIM, DIR, MODE, FORM, NU, NF>());
-    const long long blocks = (sweep_warps(DIR, a.n, a.seg) * 32 + T - 1) / T;
+    const long long slots = sweep_slots<NDIM, DIR, MODE, FORM, NU, NF>();
+    constexpr bool BAL = sweep_balanced(FORM, NF);
+    long long blocks;
+    if (BAL && !(TMA && a.tmap)) {
+        // balanced mapping: MFC_BAL_WAVES x the resident warps, each taking at
+        // least MFC_BAL_MIN_CELLS cells
+        const long long cells = sweep_group_cells(DIR, a.n);
+        long long w = slots * (T / 32) * MFC_BAL_WAVES;
+        const long long wmax = (cells + MFC_BAL_MIN_CELLS - 1) / MFC_BAL_MIN_CELLS;
+        if (w > wmax) w = wmax;
+        a.nwarps = w;
+        a.seg = 0;
+        blocks = (w * 32 + T - 1) / T;
+    } else {
+        a.nwarps = 0;
+        a.seg = pick_seg(DIR, a.n, T, slots);
+        blocks = (sweep_warps(DIR, a.n, a.seg) * 32 + T - 1) / T;
+    }
     if (blocks <= 0 || a.dry) return cudaSuccess;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     CUtensorMap tm;

@@ -97,9 +97,16 @@ def test_planted_mistake_is_caught(name, tmp_path):
     subprocess.run(["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o",
                     str(so), str(csrc), other, "-lm"], check=True)
     env = dict(os.environ, MFC5_ORACLE_LIB=str(so))
-    suites = [os.path.join(ROOT, "tests", f) for f in
-              ("test_oracle_elements.py", "test_oracle_physics.py", "test_oracle_stretched.py",
-               "test_oracle_nfluids.py", "test_oracle_gate.py", "test_oracle_mlp.py")]
+    suites = ["test_oracle_elements.py", "test_oracle_physics.py", "test_oracle_stretched.py",
+              "test_oracle_nfluids.py", "test_oracle_gate.py", "test_oracle_mlp.py"]
+    # the suite that pins the mutated part runs first (-x stops at the first
+    # failing pin); every suite still runs for a mutant it does not catch
+    first = {"gate": "test_oracle_gate.py", "nu": "test_oracle_stretched.py", "nf": "test_oracle_nfluids.py"}
+    lead = first.get(name.split("_")[0])
+    if lead:
+        suites.remove(lead)
+        suites.insert(0, lead)
+    suites = [os.path.join(ROOT, "tests", f) for f in suites]
     r = subprocess.run([sys.executable, "-m", "pytest", *suites, "-x", "-q", "-p", "no:cacheprovider",
                         "-m", "not gpu"], cwd=ROOT, env=env, capture_output=True, text=True,
                        timeout=600)
