@@ -541,7 +541,9 @@ def run_ours(args):
         "roofline": roof,
         "forms": out_forms,
         "e2e": {"value": round(e2e_grind, 5), "unit": UNIT, "h2d_bytes_per_step": ncell * neq * 8,
-                "d2h_bytes_per_step": ncell * neq * 8, "steps": e2e_steps},
+                "d2h_bytes_per_step": ncell * neq * 8, "steps": e2e_steps,
+                "copies": "mfc_set_state / mfc_get_state from page-locked host buffers, copied by the SMs "
+                          "through the buffers' device mapping"},
         "gpu_launches": sum(r["launches"] for r in forms.values()),
         "clocks": res["clocks"],
         "cpu_baseline": base,

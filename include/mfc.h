@@ -17,7 +17,12 @@
  *   - Pointers flagged on_device = 1 are device pointers on the device the
  *     context was created on; on_device = 0 means host memory.  Copies are
  *     ordered on the context's stream; calls that return host data
- *     synchronise that stream before returning.
+ *     synchronise that stream before returning.  A host array in page-locked
+ *     memory mapped into the device's address space (cudaHostAlloc, or
+ *     memory pinned by PyTorch, under unified addressing), with its address
+ *     and size multiples of 16 bytes, is copied by the GPU's SMs through that
+ *     mapping; it must lie within one page-locked allocation.  Other host
+ *     memory goes through cudaMemcpyAsync.
  *   - The context owns all device memory it allocates; the caller owns every
  *     pointer it passes in and keeps it valid until the call returns.
  *   - Every call returns an mfc_status.  Nothing aborts, traps or prints.

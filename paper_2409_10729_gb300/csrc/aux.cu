@@ -3,6 +3,8 @@
 // wave-speed reduction, and the per-step control kernel.  Built with
 // -fmad=false: the conversion and the wave speed follow the reference
 // operation order bit for bit, so every form starts from the same state.
+#include <stdint.h>
+
 #include <type_traits>
 
 #include "sweep.cuh"
@@ -175,6 +177,43 @@ cudaError_t launch_step_begin(DevCtrl* ctrl, cudaStream_t s) {
 cudaError_t launch_f32_to_f64(const float* src, double* dst, long long n, cudaStream_t s) {
     f32_to_f64_kernel<<<aux_blocks(n), kAuxThreads, 0, s>>>(src, dst, n);
     return cudaGetLastError();
+}
+
+// 16-byte grid-stride copy; one side is page-locked host memory read or
+// written through its device mapping.
+__global__ void copy16_kernel(const uint4* __restrict__ src, uint4* __restrict__ dst, long long n16) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n16;
+         i += (long long)gridDim.x * blockDim.x)
+        dst[i] = src[i];
+}
+
+// True when [p, p + bytes) starts and ends in page-locked host memory that
+// the current device reaches at the same address (unified addressing).
+static bool host_mapped(const void* p, size_t bytes) {
+    const void* ends[2] = {p, static_cast<const char*>(p) + (bytes - 1)};
+    for (const void* e : ends) {
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, e) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        if (at.type != cudaMemoryTypeHost || at.devicePointer != e) return false;
+    }
+    return true;
+}
+
+cudaError_t host_copy(void* dst, const void* src, size_t bytes, bool to_device, cudaStream_t s) {
+    if (bytes == 0) return cudaSuccess;
+    const void* host = to_device ? src : dst;
+    const bool aligned = (((uintptr_t)dst | (uintptr_t)src | bytes) & 15u) == 0;
+    if (aligned && host_mapped(host, bytes)) {
+        const long long n16 = (long long)(bytes / 16);
+        long long blocks = (n16 + 511) / 512;
+        if (blocks > kHostCopyBlocks) blocks = kHostCopyBlocks;
+        copy16_kernel<<<(unsigned)blocks, 512, 0, s>>>(static_cast<const uint4*>(src), static_cast<uint4*>(dst), n16);
+        return cudaGetLastError();
+    }
+    return cudaMemcpyAsync(dst, src, bytes, to_device ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost, s);
 }
 
 }  // namespace mfc5

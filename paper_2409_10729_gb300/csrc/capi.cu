@@ -392,13 +392,12 @@ static int after_state_change(mfc_ctx* ctx) {
     return MFC_OK;
 }
 
-static cudaMemcpyKind kind_in(int on_device) { return on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice; }
-static cudaMemcpyKind kind_out(int on_device) { return on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost; }
 
 extern "C" int mfc_set_state(mfc_ctx* ctx, const double* q, int on_device) {
     if (!ctx || !q) return MFC_EINVAL;
     size_t bytes = (size_t)ctx->ncell * ctx->neq * sizeof(double);
-    CK(cudaMemcpyAsync(ctx->qn, q, bytes, kind_in(on_device), ctx->stream));
+    CK(on_device ? cudaMemcpyAsync(ctx->qn, q, bytes, cudaMemcpyDeviceToDevice, ctx->stream)
+                 : host_copy(ctx->qn, q, bytes, true, ctx->stream));
     int st = after_state_change(ctx);
     if (st) return st;
     if (!on_device) CK(cudaStreamSynchronize(ctx->stream));
@@ -408,7 +407,8 @@ extern "C" int mfc_set_state(mfc_ctx* ctx, const double* q, int on_device) {
 extern "C" int mfc_set_state_prim(mfc_ctx* ctx, const double* w, int on_device) {
     if (!ctx || !w) return MFC_EINVAL;
     size_t bytes = (size_t)ctx->ncell * ctx->neq * sizeof(double);
-    CK(cudaMemcpyAsync(ctx->qn, w, bytes, kind_in(on_device), ctx->stream));
+    CK(on_device ? cudaMemcpyAsync(ctx->qn, w, bytes, cudaMemcpyDeviceToDevice, ctx->stream)
+                 : host_copy(ctx->qn, w, bytes, true, ctx->stream));
     CK(launch_prim_to_cons(ctx->ndim, ctx->qn, ctx->ncell, ctx->eos, ctx->stream));
     int st = after_state_change(ctx);
     if (st) return st;
@@ -420,7 +420,8 @@ extern "C" int mfc_get_state(mfc_ctx* ctx, double* q, int on_device) {
     if (!ctx || !q) return MFC_EINVAL;
     if (!ctx->have_state) return MFC_ESTATE;
     size_t bytes = (size_t)ctx->ncell * ctx->neq * sizeof(double);
-    CK(cudaMemcpyAsync(q, ctx->qn, bytes, kind_out(on_device), ctx->stream));
+    CK(on_device ? cudaMemcpyAsync(q, ctx->qn, bytes, cudaMemcpyDeviceToDevice, ctx->stream)
+                 : host_copy(q, ctx->qn, bytes, false, ctx->stream));
     if (!on_device) CK(cudaStreamSynchronize(ctx->stream));
     return MFC_OK;
 }
@@ -476,8 +477,7 @@ static int rhs_impl(mfc_ctx* ctx, double* rhs, int on_device) {
         CK(launch_sweep(ctx, d, mode, a, ctx->stream));
     }
     if (!on_device)
-        CK(cudaMemcpyAsync(rhs, out, (size_t)ctx->ncell * ctx->neq * sizeof(double), cudaMemcpyDeviceToHost,
-                           ctx->stream));
+        CK(host_copy(rhs, out, (size_t)ctx->ncell * ctx->neq * sizeof(double), false, ctx->stream));
     st = read_ctrl(ctx);
     if (st) return st;
     return ctx->ctrl_h->status ? MFC_ENONPHYSICAL : MFC_OK;
@@ -502,8 +502,8 @@ extern "C" int mfc_gate_rhs(mfc_ctx* ctx, double* rhs, signed char* decisions, i
     int st = rhs_impl(ctx, rhs, on_device);
     ctx->dec_on = false;
     if (st != MFC_OK && st != MFC_ENONPHYSICAL) return st;
-    CK(cudaMemcpyAsync(decisions, ctx->dec_dev, nb, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                       ctx->stream));
+    CK(on_device ? cudaMemcpyAsync(decisions, ctx->dec_dev, nb, cudaMemcpyDeviceToDevice, ctx->stream)
+                 : host_copy(decisions, ctx->dec_dev, nb, false, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     return st;
 }
