@@ -121,7 +121,8 @@ __device__ __forceinline__ double fma2(double k, double v, double x) { return __
 // Two correctly rounded operations of WENO5 computed from the IEEE 754
 // binary64 fields on the integer pipes (GB300's FP64 pipe retires two
 // operations per SM and clock): the product of v by a small odd integer K and
-// the quotient x/6.  Same bits as the FP64 operation for every input: zeros
+// the quotient x/6, both on 32-bit words (32-bit multiplies, multiply-highs,
+// shifts and adds; no floating-point or 64-bit integer instruction).  Same bits as the FP64 operation for every input: zeros
 // are returned directly, and subnormal, infinite or NaN operands and results
 // near the exponent limits take the FP64 instruction.
 //
@@ -133,16 +134,24 @@ __device__ __forceinline__ double fma2(double k, double v, double x) { return __
 template <unsigned K>
 __device__ __forceinline__ double mul_small(double v) {
     static_assert(K % 2 == 1 && K >= 3 && K <= 15, "odd factor 3..15");
-    constexpr int S0 = K < 4 ? 1 : (K < 8 ? 2 : 3);   // M K in [2^(52+S0), 2^(54+S0))
-    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
-    const unsigned e = (unsigned)(b >> 52) & 0x7ffu;
-    if (__builtin_expect(e > 2041u || (e == 0u && (b << 1) != 0ull), 0)) return (double)K * v;
-    const unsigned long long m = (b & 0x000fffffffffffffull) | 0x0010000000000000ull;
-    const unsigned long long P = m * K;
-    const unsigned s = S0 + (P >= (1ull << (53 + S0)) ? 1u : 0u);
-    const unsigned long long R = (P + ((1ull << (s - 1)) - 1ull) + ((P >> s) & 1ull)) >> s;
-    const unsigned long long out = (b & 0x8000000000000000ull) + ((unsigned long long)(e + s - 1u) << 52) + R;
-    return e == 0u ? v : __longlong_as_double((long long)out);
+    constexpr unsigned S0 = K < 4 ? 1 : (K < 8 ? 2 : 3);   // M K in [2^(52+S0), 2^(54+S0))
+    const unsigned hi = (unsigned)__double2hiint(v), lo = (unsigned)__double2loint(v);
+    const unsigned e = (hi >> 20) & 0x7ffu;
+    // subnormals, |v| >= 2^1019, infinities and NaNs
+    if (__builtin_expect(e > 2041u || (e == 0u && ((hi << 1) | lo) != 0u), 0)) return (double)K * v;
+    // P = M K in two 32-bit words (M = mh:lo): no 64-bit integer instruction
+    const unsigned mh = (hi & 0x000fffffu) | 0x00100000u;
+    const unsigned pl = lo * K;
+    const unsigned ph = mh * K + __umulhi(lo, K);
+    const unsigned s = S0 + ((ph >> (21 + S0)) & 1u);   // P >= 2^(53+S0): one more bit to drop
+    const unsigned add = ((1u << (s - 1u)) - 1u) + ((pl >> s) & 1u);
+    const unsigned nl = pl + add;
+    const unsigned nh = ph + (nl < pl ? 1u : 0u);
+    const unsigned rl = __funnelshift_r(nl, nh, s), rh = nh >> s;
+    const bool zero = e == 0u;   // +-0: K 0 = 0 with the sign kept
+    const unsigned oh = zero ? hi : (hi & 0x80000000u) + ((e + s - 1u) << 20) + rh;
+    const unsigned ol = zero ? lo : rl;
+    return __hiloint2double((int)oh, (int)ol);
 }
 
 // x/6: with x = +-M 2^(e-1075), x/6 = +-(M 2^k / 3) 2^(e-1076-k), where k = 2
@@ -150,14 +159,22 @@ __device__ __forceinline__ double mul_small(double v) {
 // of an integer is never halfway between two integers, so the round-to-nearest
 // significand is floor((M 2^k + 1) / 3) and never reaches 2^53.
 __device__ __forceinline__ double div6(double x) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const unsigned e = (unsigned)(b >> 52) & 0x7ffu;
-    if (__builtin_expect(e == 2047u || (e < 4u && (b << 1) != 0ull), 0)) return x / 6.0;
-    const unsigned long long m = (b & 0x000fffffffffffffull) | 0x0010000000000000ull;
-    const unsigned k = m < 0x0018000000000000ull ? 2u : 1u;
-    const unsigned long long Q = ((m << k) + 1ull) / 3ull;
-    const unsigned long long out = (b & 0x8000000000000000ull) + ((unsigned long long)(e - 2u - k) << 52) + Q;
-    return e == 0u ? x : __longlong_as_double((long long)out);
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const unsigned e = (hi >> 20) & 0x7ffu;
+    if (__builtin_expect(e == 2047u || (e < 4u && ((hi << 1) | lo) != 0u), 0)) return x / 6.0;
+    // N = M 2^k + 1 in two 32-bit words (M = mh:lo), then N / 3 word by word:
+    // H = 3 q1 + r1, L = 3 qL + rL and 2^32 = 3 * 1431655765 + 1 give
+    // N / 3 = q1 2^32 + r1 * 1431655765 + qL + (r1 + rL >= 3), whose low word never carries
+    const unsigned mh = (hi & 0x000fffffu) | 0x00100000u;
+    const unsigned k = mh < 0x00180000u ? 2u : 1u;
+    const unsigned L = (lo << k) | 1u, H = __funnelshift_l(lo, mh, k);
+    const unsigned q1 = __umulhi(H, 0xAAAAAAABu) >> 1, r1 = H - 3u * q1;
+    const unsigned qL = __umulhi(L, 0xAAAAAAABu) >> 1, rL = L - 3u * qL;
+    const unsigned q0 = r1 * 1431655765u + qL + (r1 + rL >= 3u ? 1u : 0u);
+    const bool zero = e == 0u;   // +-0 (subnormals took the division)
+    const unsigned oh = zero ? hi : (hi & 0x80000000u) + ((e - 2u - k) << 20) + q1;
+    const unsigned ol = zero ? lo : q0;
+    return __hiloint2double((int)oh, (int)ol);
 }
 
 // The curvature term of a Jiang-Shu smoothness indicator on the three cells
