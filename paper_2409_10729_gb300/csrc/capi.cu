@@ -278,6 +278,7 @@ static SweepArgs base_args(mfc_ctx* ctx) {
         a.inv_dx[d] = ctx->inv_dx[d];
         a.dx[d] = ctx->dx[d];
         a.rdx[d] = ctx->rdx[d];
+        a.inv_dx32[d] = (float)ctx->inv_dx[d];
     }
     a.ncell = ctx->ncell;
     a.eos = ctx->eos;

@@ -30,6 +30,14 @@ inline Eos make_eos(const double* gamma, const double* pi_inf, int nf) {
         e.dg[i] = e.g[i] - e.g[nf - 1];
         e.dP[i] = e.P[i] - e.P[nf - 1];
     }
+    for (int i = 0; i < nf; ++i) {
+        e.g32[i] = (float)e.g[i];
+        e.P32[i] = (float)e.P[i];
+    }
+    for (int i = 0; i < nf - 1; ++i) {
+        e.dg32[i] = (float)e.dg[i];
+        e.dP32[i] = (float)e.dP[i];
+    }
     return e;
 }
 
@@ -82,6 +90,7 @@ struct SweepArgs {
     double inv_dx[3];     // n/(hi - lo) per direction (reformulated forms)
     double dx[3];         // (hi - lo)/n per direction
     double rdx[3];        // RN(1/dx) per direction (reference-order form)
+    float inv_dx32[3];    // inv_dx rounded to FP32 (FP32 forms)
     Eos eos;
     double eps;
     int order;            // WENO order, 3 or 5

@@ -27,6 +27,10 @@ constexpr int kMaxFluids = 4;
 struct Eos {
     double g[kMaxFluids], P[kMaxFluids];
     double dg[kMaxFluids - 1], dP[kMaxFluids - 1];
+    // the same constants rounded to FP32 (on the host), so that the FP32 forms
+    // read them without a conversion on GB300's narrow FP64 pipe
+    float g32[kMaxFluids], P32[kMaxFluids];
+    float dg32[kMaxFluids - 1], dP32[kMaxFluids - 1];
     int nf;
 };
 
@@ -62,11 +66,23 @@ __device__ __forceinline__ R sqrt_pos(R x) { return sqrt(x); }
 template <typename R, int NF = 2>
 struct EosR {
     R dg[NF - 1], gN, dP[NF - 1], PN;
-    __device__ __forceinline__ explicit EosR(const Eos& e) : gN(R(e.g[NF - 1])), PN(R(e.P[NF - 1])) {
+    __device__ __forceinline__ explicit EosR(const Eos& e) {
+        if constexpr (sizeof(R) == 4) {
+            gN = e.g32[NF - 1];
+            PN = e.P32[NF - 1];
+        } else {
+            gN = R(e.g[NF - 1]);
+            PN = R(e.P[NF - 1]);
+        }
 #pragma unroll
         for (int i = 0; i < NF - 1; ++i) {
-            dg[i] = R(e.dg[i]);
-            dP[i] = R(e.dP[i]);
+            if constexpr (sizeof(R) == 4) {
+                dg[i] = e.dg32[i];
+                dP[i] = e.dP32[i];
+            } else {
+                dg[i] = R(e.dg[i]);
+                dP[i] = R(e.dP[i]);
+            }
         }
     }
 };

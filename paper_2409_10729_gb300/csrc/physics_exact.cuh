@@ -54,11 +54,13 @@ __device__ __forceinline__ double mix_rho(const double* q) {
     return rho;
 }
 
+// 0.5 rho |u|^2 in the oracle's order, whose sum starts from 0.0: 0.0 + u_0^2
+// is u_0^2 itself (a square is never -0), so the sum starts there.
 template <int NDIM>
 __device__ __forceinline__ double kinetic(double rho, const double* u) {
-    double s = 0.0;
+    double s = u[0] * u[0];
 #pragma unroll
-    for (int k = 0; k < NDIM; ++k) s = s + u[k] * u[k];
+    for (int k = 1; k < NDIM; ++k) s = s + u[k] * u[k];
     return 0.5 * rho * s;
 }
 

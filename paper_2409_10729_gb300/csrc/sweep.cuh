@@ -132,9 +132,9 @@ __device__ __forceinline__ float mixed_pressure(const Eos& e, const double* q, c
 #pragma unroll
     for (int i = 1; i < FL::NA; ++i) Pi = Pi + q[FL::IA + i] * e.dP[i];
     double num = (q[FL::IE] - Pi) - f2d_bits(0.5f * ke2);
-    float G = q32[FL::IA] * float(e.dg[0]) + float(e.g[NF - 1]);
+    float G = q32[FL::IA] * e.dg32[0] + e.g32[NF - 1];
 #pragma unroll
-    for (int i = 1; i < FL::NA; ++i) G = G + q32[FL::IA + i] * float(e.dg[i]);
+    for (int i = 1; i < FL::NA; ++i) G = G + q32[FL::IA + i] * e.dg32[i];
     return __fdividef(d2f_bits(num), G);
 }
 
@@ -149,8 +149,8 @@ __device__ __forceinline__ R warp_max(R v) {
 }
 
 // Per-cell wave speed sum_d (|u_d| + c) / dx_d from primitives.
-template <int NDIM, typename R, int NF = 2>
-__device__ __forceinline__ R cell_wavespeed(const EosR<R, NF>& e, const R* w, const double* inv_dx, bool& bad) {
+template <int NDIM, typename R, int NF = 2, typename T = double>
+__device__ __forceinline__ R cell_wavespeed(const EosR<R, NF>& e, const R* w, const T* inv_dx, bool& bad) {
     using FL = Fields<NDIM, NF>;
     R rho = mix_rho<NF>(w);
     R G, Pi;
@@ -576,8 +576,12 @@ sweep_kernel(const SweepArgs a, const __grid_constant__ CUtensorMap tmap) {
         r1 = gseg * ns + sseg1;
     }
     const long long nc = a.ncell;
-    const R inv_dx = R(a.inv_dx[DIR]);
+    const R inv_dx = sizeof(R) == 4 ? R(a.inv_dx32[DIR]) : R(a.inv_dx[DIR]);
     const R eps = R(a.eps);
+    // FP64 reference-order form: a uniform width along DIR that is a power of two
+    // (zero fraction bits) with a normal reciprocal, which a.rdx then holds exactly
+    const unsigned dxh = (unsigned)__double2hiint(a.dx[DIR]), dxe = (dxh >> 20) & 0x7ffu;
+    const bool pow2_dx = EXACT && (dxh & 0x800fffffu) == 0u && __double2loint(a.dx[DIR]) == 0 && dxe - 2u < 2043u;
     const EosR<R, NF> er(a.eos);
     const R* __restrict__ qin = static_cast<const R*>(a.qin);
     const int wib = threadIdx.x >> 5;
@@ -858,11 +862,20 @@ sweep_kernel(const SweepArgs a, const __grid_constant__ CUtensorMap tmap) {
                             dx = __ldg(a.cw[DIR] + (j - 1));
                             rdx = __ldg(a.crw[DIR] + (j - 1));
                         }
+                        if (pow2_dx && !(NU && a.cw[DIR])) {
+                            // a power-of-two width: x / dx and x * (1/dx) are the same real
+                            // number, so one multiplication gives the quotient's bits
 #pragma unroll
-                        for (int f = 0; f < NEQ; ++f) L[f] = exact::div_rcp(Fprev[f] - F[f], dx, rdx);
+                            for (int f = 0; f < NEQ; ++f) L[f] = (Fprev[f] - F[f]) * rdx;
 #pragma unroll
-                        for (int i = 0; i < NA; ++i)
-                            L[IA + i] = L[IA + i] + exact::div_rcp(alphaCell[i] * (uf - ufPrev), dx, rdx);
+                            for (int i = 0; i < NA; ++i) L[IA + i] = L[IA + i] + alphaCell[i] * (uf - ufPrev) * rdx;
+                        } else {
+#pragma unroll
+                            for (int f = 0; f < NEQ; ++f) L[f] = exact::div_rcp(Fprev[f] - F[f], dx, rdx);
+#pragma unroll
+                            for (int i = 0; i < NA; ++i)
+                                L[IA + i] = L[IA + i] + exact::div_rcp(alphaCell[i] * (uf - ufPrev), dx, rdx);
+                        }
                     } else {
                         R idx = inv_dx;
                         if (NU && a.cw[DIR]) {
@@ -961,9 +974,14 @@ sweep_kernel(const SweepArgs a, const __grid_constant__ CUtensorMap tmap) {
                                 for (int f = 0; f < NEQ; ++f) v[f] = q32[f];
                                 v[IE] = pnew;
                                 to_prim<NDIM, NF>(er, v, wn);
-                                double dx3[3], rdx3[3], idx3[3];
-                                cell_geometry<DIR, NU>(a, j - 1, active ? ia : na - 1, b, dx3, rdx3, idx3);
-                                R s = cell_wavespeed<NDIM, float, NF>(er, wn, idx3, bad);
+                                float idx32[3] = {a.inv_dx32[0], a.inv_dx32[1], a.inv_dx32[2]};
+                                if constexpr (NU) {
+                                    double dx3[3], rdx3[3], idx3[3];
+                                    cell_geometry<DIR, NU>(a, j - 1, active ? ia : na - 1, b, dx3, rdx3, idx3);
+#pragma unroll
+                                    for (int d = 0; d < 3; ++d) idx32[d] = float(idx3[d]);
+                                }
+                                R s = cell_wavespeed<NDIM, float, NF>(er, wn, idx32, bad);
                                 smax = s > smax ? s : smax;
                             }
                         }
