@@ -246,6 +246,11 @@ __host__ __device__ constexpr bool sweep_balanced(int form, int nf) {
 // 1: the sweeps issue the loads of the cell entering the stencil window at the
 // top of each step along the pencil (they complete under that step's
 // arithmetic); 0: at the bottom, just before they are used.
+// FP64 reference-order sweeps: carry two WENO5 candidate values per field
+// from cell to cell (1) or form them in every cell (0)
+#ifndef MFC_CAND_CARRY
+#define MFC_CAND_CARRY 1
+#endif
 #ifndef MFC_PREFETCH
 #define MFC_PREFETCH 1
 #endif

@@ -223,6 +223,48 @@ __device__ __forceinline__ void weno5_t(double eps, double v0, double v1, double
     vp = div_rcp(a0, s, ys) * p0 + div_rcp(a1, s, ys) * p1 + div_rcp(a2, s, ys) * p2;
 }
 
+// The right-face candidates of cell i, (-v_{i-2} + 5 v_{i-1} + 2 v_i)/6 and
+// (2 v_{i-1} + 5 v_i - v_{i+1})/6, are the left-face candidates p1 and p2 of
+// cell i-1, formed from the same values in the same order (the same bits):
+// weno5_tc takes them as r0, r1 and returns this cell's p1, p2 for the next.
+__device__ __forceinline__ void weno5_tc(double eps, double v0, double v1, double v2, double v3, double v4,
+                                         double t0, double t1, double t2, double& r0, double& r1, double& vm,
+                                         double& vp) {
+    const double v2x3 = mul_small<3>(v2);
+    double b0 = fma2(0.25, sq(fma2(-4.0, v1, v0) + v2x3), t0);
+    double b1 = fma2(0.25, sq(v1 - v3), t1);
+    double b2 = fma2(0.25, sq(fma2(-4.0, v3, v2x3) + v4), t2);
+    double s0 = sq(eps + b0), s1 = sq(eps + b1), s2 = sq(eps + b2);
+    double y0 = rcp(s0), y1 = rcp(s1), y2 = rcp(s2);
+
+    double a0 = div_rcp(0.1, s0, y0);
+    double a1 = div_rcp(0.6, s1, y1);
+    double a2 = div_rcp(0.3, s2, y2);
+    double s = a0 + a1 + a2;
+    double ys = rcp(s);
+    const double v2x5 = mul_small<5>(v2), v2x11 = mul_small<11>(v2);
+    double p0 = div6(fma2(2.0, v0, -mul_small<7>(v1)) + v2x11);     // (2 v0 - 7 v1 + 11 v2)/6
+    double p1 = div6(fma2(2.0, v3, -v1 + v2x5));                    // (-v1 + 5 v2 + 2 v3)/6
+    double p2 = div6(fma2(2.0, v2, mul_small<5>(v3)) - v4);         // (2 v2 + 5 v3 - v4)/6
+    vm = div_rcp(a0, s, ys) * p0 + div_rcp(a1, s, ys) * p1 + div_rcp(a2, s, ys) * p2;
+
+    a0 = div_rcp(0.3, s0, y0);
+    a1 = div_rcp(0.6, s1, y1);
+    a2 = div_rcp(0.1, s2, y2);
+    s = a0 + a1 + a2;
+    ys = rcp(s);
+    p0 = div6(fma2(2.0, v4, v2x11 - mul_small<7>(v3)));             // (11 v2 - 7 v3 + 2 v4)/6
+    vp = div_rcp(a0, s, ys) * r0 + div_rcp(a1, s, ys) * r1 + div_rcp(a2, s, ys) * p0;
+    r0 = p1;
+    r1 = p2;
+}
+
+// The right-face candidates r0, r1 of the cell whose window is v0..v3 (as in weno5_t).
+__device__ __forceinline__ void weno5_right01(double v0, double v1, double v2, double v3, double& r0, double& r1) {
+    r0 = div6(fma2(2.0, v2, -v0 + mul_small<5>(v1)));
+    r1 = div6(fma2(2.0, v1, mul_small<5>(v2)) - v3);
+}
+
 __device__ __forceinline__ void weno5(double eps, double v0, double v1, double v2, double v3, double v4,
                                       double& vm, double& vp) {
     weno5_t(eps, v0, v1, v2, v3, v4, curv(v0, v1, v2), curv(v1, v2, v3), curv(v2, v3, v4), vm, vp);

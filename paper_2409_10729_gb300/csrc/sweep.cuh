@@ -586,7 +586,10 @@ sweep_kernel(const SweepArgs a, const __grid_constant__ CUtensorMap tmap) {
     const R* __restrict__ qin = static_cast<const R*>(a.qin);
     const int wib = threadIdx.x >> 5;
 
-    constexpr bool PREFETCH = MFC_PREFETCH != 0;
+    // the FP64 reference-order kernels are FP64-pipe bound with latency to spare:
+    // the registers of a prefetched cell go to the carried candidates instead
+    constexpr bool PCARRY = EXACT && !GATED && !NU && NF == 2 && MFC_CAND_CARRY;
+    constexpr bool PREFETCH = MFC_PREFETCH != 0 && !PCARRY;
     constexpr bool EPI_PREFETCH = PREFETCH && MIXED;
     bool bad_any = false, tma_fail = false;
     R smax = R(0);
@@ -754,6 +757,13 @@ sweep_kernel(const SweepArgs a, const __grid_constant__ CUtensorMap tmap) {
                 T0[f] = exact::curv(W[1][f], W[2][f], W[3][f]);
             }
         }
+        // and the right-face candidates of the window's centre cell, carried as
+        // the left-face candidates of the cell before it (exact::weno5_tc)
+        double Pr0[PCARRY ? NEQ : 1], Pr1[PCARRY ? NEQ : 1];
+        if constexpr (PCARRY) {
+#pragma unroll
+            for (int f = 0; f < NEQ; ++f) exact::weno5_right01(W[0][f], W[1][f], W[2][f], W[3][f], Pr0[f], Pr1[f]);
+        }
         R vmPrev[NEQ], Fprev[NEQ];
         R ufPrev = R(0), alphaCell[NA];
 #pragma unroll
@@ -828,7 +838,13 @@ sweep_kernel(const SweepArgs a, const __grid_constant__ CUtensorMap tmap) {
                 } else if (GATED || a.order == 5) {
 #pragma unroll
                     for (int f = 0; f < NEQ; ++f) {
-                        if constexpr (TCARRY) {
+                        if constexpr (PCARRY) {
+                            const double Tp = exact::curv(W[2][f], W[3][f], W[4][f]);
+                            exact::weno5_tc(a.eps, W[0][f], W[1][f], W[2][f], W[3][f], W[4][f], Tm[f], T0[f], Tp,
+                                            Pr0[f], Pr1[f], vm[f], vp[f]);
+                            Tm[f] = T0[f];
+                            T0[f] = Tp;
+                        } else if constexpr (TCARRY) {
                             const double Tp = exact::curv(W[2][f], W[3][f], W[4][f]);
                             exact::weno5_t(a.eps, W[0][f], W[1][f], W[2][f], W[3][f], W[4][f], Tm[f], T0[f], Tp,
                                            vm[f], vp[f]);
