@@ -248,6 +248,11 @@ __host__ __device__ constexpr bool sweep_balanced(int form, int nf) {
 // arithmetic); 0: at the bottom, just before they are used.
 // FP64 reference-order sweeps: carry two WENO5 candidate values per field
 // from cell to cell (1) or form them in every cell (0)
+// mixed form, uniform grids, x sweep: carry WENO5 first differences and
+// curvature parts from cell to cell (1) or form them in every cell (0)
+#ifndef MFC_DIFF_CARRY
+#define MFC_DIFF_CARRY 1
+#endif
 #ifndef MFC_CAND_CARRY
 #define MFC_CAND_CARRY 1
 #endif

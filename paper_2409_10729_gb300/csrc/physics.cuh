@@ -115,6 +115,53 @@ __device__ __forceinline__ void mixture(const EosR<R, NF>& e, const R* a, R& G, 
 // exactly.  FP64: product-form weights and one reciprocal for both faces.
 // FP32: weights relative to the smoothest stencil, the linear weights and
 // the 1/6 folded into the corrections, one fast reciprocal per face.
+// FP32 WENO5 from the smoothness indicators: weights relative to the smoothest
+// stencil, the linear weights and the 1/6 of the candidates folded into the
+// corrections, one reciprocal per face.
+__device__ __forceinline__ void weno5_tail32(float v2, float d1, float d2, float d3, float d4, float b0, float b1,
+                                             float b2, float eps, float& vm, float& vp) {
+    float s0 = eps + b0, s1 = eps + b1, s2 = eps + b2;
+    s0 = s0 * s0;
+    s1 = s1 * s1;
+    s2 = s2 * s2;
+    // weights relative to the smoothest stencil, all in (0, 1]
+    const float smin = fminf(s0, fminf(s1, s2));
+    const float m0 = __fdividef(smin, s0);
+    const float m1 = __fdividef(smin, s1);
+    const float m2 = __fdividef(smin, s2);
+    // face values v_i + sum_k d_k m_k c_k / sum_k d_k m_k with the linear
+    // weights d_k and the 1/6 of the candidates folded into the
+    // corrections c_k, and one reciprocal per face
+    const float t1 = float(0.6) * m1;
+    const float Dm = fmaf(float(0.1), m0, fmaf(float(0.3), m2, t1));
+    const float Dp = fmaf(float(0.3), m0, fmaf(float(0.1), m2, t1));
+    const float d2x02 = float(0.2) * d2, d3x02 = float(0.2) * d3;
+    const float cm0 = fmaf(float(0.5 / 6.0), d2, float(-0.2 / 6.0) * d1);  // 0.1 (5 d2 - 2 d1)/6
+    const float cm1 = fmaf(float(0.1), d2, d3x02);  // 0.6 (d2 + 2 d3)/6
+    const float cm2 = fmaf(-float(0.05), d4, d3x02);  // 0.3 (4 d3 - d4)/6
+    const float cp0 = fmaf(float(0.05), d1, -d2x02);  // 0.3 (d1 - 4 d2)/6
+    const float cp1 = fmaf(-float(0.1), d3, -d2x02);  // -0.6 (2 d2 + d3)/6
+    const float cp2 = fmaf(float(0.2 / 6.0), d4, float(-0.5 / 6.0) * d3);  // 0.1 (2 d4 - 5 d3)/6
+    const float Nm = fmaf(m0, cm0, fmaf(m1, cm1, m2 * cm2));
+    const float Np = fmaf(m0, cp0, fmaf(m1, cp1, m2 * cp2));
+    vm = fmaf(Nm, __fdividef(1.0f, Dm), v2);
+    vp = fmaf(Np, __fdividef(1.0f, Dp), v2);
+}
+
+// FP32 WENO5 of cell i from values carried along the pencil: the first
+// differences d1..d4 of v_{i-2}..v_{i+2} and the curvature parts
+// C_k = 13/12 (d_{k+2} - d_{k+1})^2 of the three indicators.  d1..d3 and C0, C1
+// are d2..d4 and C1, C2 of cell i-1, so a sweep forms one difference and one
+// curvature part per cell and field.
+__device__ __forceinline__ void weno5_dc(float v2, float d1, float d2, float d3, float d4, float C0, float C1,
+                                         float C2, float eps, float& vm, float& vp) {
+    const float Q0 = 3.0f * d2 - d1, Q1 = d2 + d3, Q2 = 3.0f * d3 - d4;
+    const float b0 = fmaf(0.25f * Q0, Q0, C0);
+    const float b1 = fmaf(0.25f * Q1, Q1, C1);
+    const float b2 = fmaf(0.25f * Q2, Q2, C2);
+    weno5_tail32(v2, d1, d2, d3, d4, b0, b1, b2, eps, vm, vp);
+}
+
 template <typename R>
 __device__ __forceinline__ void weno5(R v0, R v1, R v2, R v3, R v4, R eps, R& vm, R& vp) {
     const R c13 = R(13.0 / 12.0);
@@ -124,41 +171,16 @@ __device__ __forceinline__ void weno5(R v0, R v1, R v2, R v3, R v4, R eps, R& vm
     R b0 = c13 * D0 * D0 + R(0.25) * Q0 * Q0;
     R b1 = c13 * D1 * D1 + R(0.25) * Q1 * Q1;
     R b2 = c13 * D2 * D2 + R(0.25) * Q2 * Q2;
+    if constexpr (sizeof(R) == 4) {
+        weno5_tail32(v2, d1, d2, d3, d4, b0, b1, b2, eps, vm, vp);
+        return;
+    }
     R s0 = eps + b0, s1 = eps + b1, s2 = eps + b2;
     s0 = s0 * s0;
     s1 = s1 * s1;
     s2 = s2 * s2;
-    R m0, m1, m2;
-    if constexpr (sizeof(R) == 8) {
-        // product form: weight of stencil k is proportional to d_k * s_j * s_l
-        m0 = s1 * s2;
-        m1 = s0 * s2;
-        m2 = s0 * s1;
-    } else {
-        // FP32: weights relative to the smoothest stencil, all in (0, 1]
-        R smin = fminf(s0, fminf(s1, s2));
-        m0 = __fdividef(smin, s0);
-        m1 = __fdividef(smin, s1);
-        m2 = __fdividef(smin, s2);
-        // face values v_i + sum_k d_k m_k c_k / sum_k d_k m_k with the linear
-        // weights d_k and the 1/6 of the candidates folded into the
-        // corrections c_k, and one reciprocal per face
-        const R t1 = R(0.6) * m1;
-        const R Dm = fmaf(R(0.1), m0, fmaf(R(0.3), m2, t1));
-        const R Dp = fmaf(R(0.3), m0, fmaf(R(0.1), m2, t1));
-        const R d2x02 = R(0.2) * d2, d3x02 = R(0.2) * d3;
-        const R cm0 = fmaf(R(0.5 / 6.0), d2, R(-0.2 / 6.0) * d1);   // 0.1 (5 d2 - 2 d1)/6
-        const R cm1 = fmaf(R(0.1), d2, d3x02);                      // 0.6 (d2 + 2 d3)/6
-        const R cm2 = fmaf(R(-0.05), d4, d3x02);                    // 0.3 (4 d3 - d4)/6
-        const R cp0 = fmaf(R(0.05), d1, -d2x02);                    // 0.3 (d1 - 4 d2)/6
-        const R cp1 = fmaf(R(-0.1), d3, -d2x02);                    // -0.6 (2 d2 + d3)/6
-        const R cp2 = fmaf(R(0.2 / 6.0), d4, R(-0.5 / 6.0) * d3);   // 0.1 (2 d4 - 5 d3)/6
-        const R Nm = fmaf(m0, cm0, fmaf(m1, cm1, m2 * cm2));
-        const R Np = fmaf(m0, cp0, fmaf(m1, cp1, m2 * cp2));
-        vm = fmaf(Nm, __fdividef(R(1), Dm), v2);
-        vp = fmaf(Np, __fdividef(R(1), Dp), v2);
-        return;
-    }
+    // product form: weight of stencil k is proportional to d_k * s_j * s_l
+    R m0 = s1 * s2, m1 = s0 * s2, m2 = s0 * s1;
     R am0 = R(0.1) * m0, am1 = R(0.6) * m1, am2 = R(0.3) * m2;
     R ap0 = R(0.3) * m0, ap1 = R(0.6) * m1, ap2 = R(0.1) * m2;
     R Nm = am0 * (R(5) * d2 - R(2) * d1) + am1 * (d2 + R(2) * d3) + am2 * (R(4) * d3 - d4);

@@ -764,6 +764,24 @@ sweep_kernel(const SweepArgs a, const __grid_constant__ CUtensorMap tmap) {
 #pragma unroll
             for (int f = 0; f < NEQ; ++f) exact::weno5_right01(W[0][f], W[1][f], W[2][f], W[3][f], Pr0[f], Pr1[f]);
         }
+        // mixed form, x sweep: the first differences d1..d3 and curvature parts C0, C1
+        // of the window's centre cell, carried along the pencil (weno5_dc); the y and
+        // z sweeps, register-capped for occupancy, lose more to spills than it saves
+        constexpr bool DCARRY = FORM == FORM_MIXED && !NU && DIR == 0 && MFC_DIFF_CARRY;
+        float Dd1[DCARRY ? NEQ : 1], Dd2[DCARRY ? NEQ : 1], Dd3[DCARRY ? NEQ : 1];
+        float Cc0[DCARRY ? NEQ : 1], Cc1[DCARRY ? NEQ : 1];
+        const float c13f = float(13.0 / 12.0);
+        if constexpr (DCARRY) {
+#pragma unroll
+            for (int f = 0; f < NEQ; ++f) {
+                Dd1[f] = float(W[1][f] - W[0][f]);
+                Dd2[f] = float(W[2][f] - W[1][f]);
+                Dd3[f] = float(W[3][f] - W[2][f]);
+                const float D0 = Dd2[f] - Dd1[f], D1 = Dd3[f] - Dd2[f];
+                Cc0[f] = c13f * D0 * D0;
+                Cc1[f] = c13f * D1 * D1;
+            }
+        }
         R vmPrev[NEQ], Fprev[NEQ];
         R ufPrev = R(0), alphaCell[NA];
 #pragma unroll
@@ -852,6 +870,19 @@ sweep_kernel(const SweepArgs a, const __grid_constant__ CUtensorMap tmap) {
                             T0[f] = Tp;
                         } else if constexpr (EXACT) {
                             exact::weno5(a.eps, W[0][f], W[1][f], W[2][f], W[3][f], W[4][f], vm[f], vp[f]);
+                        } else if constexpr (DCARRY) {
+                            const float d4 = float(W[4][f] - W[3][f]);
+                            const float D2 = d4 - Dd3[f];
+                            const float C2 = c13f * D2 * D2;
+                            float fm, fp;
+                            weno5_dc(float(W[2][f]), Dd1[f], Dd2[f], Dd3[f], d4, Cc0[f], Cc1[f], C2, float(eps), fm, fp);
+                            vm[f] = R(fm);
+                            vp[f] = R(fp);
+                            Dd1[f] = Dd2[f];
+                            Dd2[f] = Dd3[f];
+                            Dd3[f] = d4;
+                            Cc0[f] = Cc1[f];
+                            Cc1[f] = C2;
                         } else {
                             weno5(W[0][f], W[1][f], W[2][f], W[3][f], W[4][f], eps, vm[f], vp[f]);
                         }
