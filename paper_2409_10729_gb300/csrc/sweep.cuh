@@ -743,7 +743,8 @@ sweep_kernel(const SweepArgs a, const __grid_constant__ CUtensorMap tmap) {
             fetch(k, v);
             if constexpr (EXACT) exact::cons_to_prim<NDIM, NF>(a.eos, v, W[k]);
             else to_prim<NDIM, NF>(er, v, W[k]);
-            bad |= !(mix_rho<NF>(W[k]) > R(0));
+            if constexpr (EXACT) bad |= !exact::gt0(mix_rho<NF>(W[k]));
+            else bad |= !(mix_rho<NF>(W[k]) > R(0));
         }
         // FP64 reference-order form: the smoothness indicators' curvature terms
         // of the window's stencils {i-2..i}, {i-1..i+1} (cell i = window centre),
@@ -1073,7 +1074,8 @@ sweep_kernel(const SweepArgs a, const __grid_constant__ CUtensorMap tmap) {
                 if (!PREFETCH) fetch(j + 3 - (s0 - 3), vnext);
                 if constexpr (EXACT) exact::cons_to_prim<NDIM, NF>(a.eos, vnext, W[4]);
                 else to_prim<NDIM, NF>(er, vnext, W[4]);
-                bad |= !(mix_rho<NF>(W[4]) > R(0));
+                if constexpr (EXACT) bad |= !exact::gt0(mix_rho<NF>(W[4]));
+                else bad |= !(mix_rho<NF>(W[4]) > R(0));
             }
         }
         // only cells this lane owns count (inactive lanes and segment halos excluded)
