@@ -46,6 +46,56 @@ struct Fields {
     static constexpr int NA = NF - 1;         // carried volume fractions
 };
 
+// Comparisons of FP64 values on the integer pipes, from the two 32-bit words
+// of each operand (GB300's narrow FP64 pipe also executes the FP64 compare
+// instruction).  The answers are the IEEE compares': false when an operand
+// is a NaN, and -0 equal to +0.
+__device__ __forceinline__ bool is_nan_w(unsigned h, unsigned l) {
+    const unsigned m = h & 0x7fffffffu;
+    return m > 0x7ff00000u || (m == 0x7ff00000u && l != 0u);
+}
+
+// x > 0
+__device__ __forceinline__ bool gt0(double x) {
+    const unsigned h = (unsigned)__double2hiint(x), l = (unsigned)__double2loint(x);
+    return (h >> 31) == 0u && (h | l) != 0u && !is_nan_w(h, l);
+}
+
+// 0 <= x
+__device__ __forceinline__ bool ge0(double x) {
+    const unsigned h = (unsigned)__double2hiint(x), l = (unsigned)__double2loint(x);
+    return ((h >> 31) == 0u && !is_nan_w(h, l)) || (h == 0x80000000u && l == 0u);
+}
+
+// a < b
+__device__ __forceinline__ bool less(double a, double b) {
+    const unsigned ha = (unsigned)__double2hiint(a), la = (unsigned)__double2loint(a);
+    const unsigned hb = (unsigned)__double2hiint(b), lb = (unsigned)__double2loint(b);
+    const unsigned ma = ha & 0x7fffffffu, mb = hb & 0x7fffffffu;
+    const bool lt_mag = ma < mb || (ma == mb && la < lb);   // |a| < |b|
+    const bool gt_mag = mb < ma || (ma == mb && lb < la);   // |a| > |b|
+    const bool zeros = (ma | la | mb | lb) == 0u;
+    const unsigned sa = ha >> 31, sb = hb >> 31;
+    const bool r = sa == 0u ? (sb == 0u && lt_mag) : (sb == 0u ? !zeros : gt_mag);
+    return r && !is_nan_w(ha, la) && !is_nan_w(hb, lb);
+}
+
+template <typename R>
+__device__ __forceinline__ bool pos(R x) {
+    if constexpr (sizeof(R) == 8) return gt0(x);
+    else return x > R(0);
+}
+template <typename R>
+__device__ __forceinline__ bool nonneg(R x) {
+    if constexpr (sizeof(R) == 8) return ge0(x);
+    else return R(0) <= x;
+}
+template <typename R>
+__device__ __forceinline__ bool lt(R a, R b) {
+    if constexpr (sizeof(R) == 8) return less(a, b);
+    else return a < b;
+}
+
 // Mixture density of the partial densities w[0..NF-1].
 template <int NF, typename R>
 __device__ __forceinline__ R mix_rho(const R* w) {
@@ -284,15 +334,16 @@ __device__ __forceinline__ bool hllc(const EosR<R, NF>& e, const R* wL, const R*
     R pL = wL[IE], pR = wR[IE];
     R c2L = rdiv((GL + R(1)) * pL + PiL, GL * rhoL);
     R c2R = rdiv((GR + R(1)) * pR + PiR, GR * rhoR);
-    bool bad = !(rhoL > R(0)) || !(rhoR > R(0)) || !(c2L > R(0)) || !(c2R > R(0));
+    bool bad = !pos(rhoL) || !pos(rhoR) || !pos(c2L) || !pos(c2R);
     R cL = sqrt_pos(c2L), cR = sqrt_pos(c2R);
     R uL = wL[IU + DIR], uR = wR[IU + DIR];
-    R SL = (uL - cL < uR - cR) ? uL - cL : uR - cR;
-    R SR = (uL + cL > uR + cR) ? uL + cL : uR + cR;
+    const R aL = uL - cL, aR = uR - cR, bL = uL + cL, bR = uR + cR;
+    R SL = lt(aL, aR) ? aL : aR;
+    R SR = lt(bR, bL) ? bL : bR;
     R mL = rhoL * (SL - uL), mR = rhoR * (SR - uR);
     R Ss = rdiv(pR - pL + uL * mL - uR * mR, mL - mR);
-    const bool left = (R(0) <= SL) || (R(0) <= Ss);
-    const bool star = left ? !(R(0) <= SL) : (R(0) <= SR);
+    const bool left = nonneg(SL) || nonneg(Ss);
+    const bool star = left ? !nonneg(SL) : nonneg(SR);
     // selected side K (element-wise select keeps both states in registers)
     R w[FL::NEQ];
 #pragma unroll

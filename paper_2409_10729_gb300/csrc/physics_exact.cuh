@@ -28,40 +28,6 @@ __device__ __forceinline__ double rcp(double b) { return __drcp_rn(b); }
 
 __device__ __forceinline__ double sq(double x) { return x * x; }
 
-// Comparisons of FP64 values on the integer pipes, from the two 32-bit words
-// of each operand (GB300's narrow FP64 pipe also executes the FP64 compare
-// instruction).  The answers are the IEEE compares': false when an operand
-// is a NaN, and -0 equal to +0.
-__device__ __forceinline__ bool is_nan_w(unsigned h, unsigned l) {
-    const unsigned m = h & 0x7fffffffu;
-    return m > 0x7ff00000u || (m == 0x7ff00000u && l != 0u);
-}
-
-// x > 0
-__device__ __forceinline__ bool gt0(double x) {
-    const unsigned h = (unsigned)__double2hiint(x), l = (unsigned)__double2loint(x);
-    return (h >> 31) == 0u && (h | l) != 0u && !is_nan_w(h, l);
-}
-
-// 0 <= x
-__device__ __forceinline__ bool ge0(double x) {
-    const unsigned h = (unsigned)__double2hiint(x), l = (unsigned)__double2loint(x);
-    return ((h >> 31) == 0u && !is_nan_w(h, l)) || (h == 0x80000000u && l == 0u);
-}
-
-// a < b
-__device__ __forceinline__ bool less(double a, double b) {
-    const unsigned ha = (unsigned)__double2hiint(a), la = (unsigned)__double2loint(a);
-    const unsigned hb = (unsigned)__double2hiint(b), lb = (unsigned)__double2loint(b);
-    const unsigned ma = ha & 0x7fffffffu, mb = hb & 0x7fffffffu;
-    const bool lt_mag = ma < mb || (ma == mb && la < lb);   // |a| < |b|
-    const bool gt_mag = mb < ma || (ma == mb && lb < la);   // |a| > |b|
-    const bool zeros = (ma | la | mb | lb) == 0u;
-    const unsigned sa = ha >> 31, sb = hb >> 31;
-    const bool r = sa == 0u ? (sb == 0u && lt_mag) : (sb == 0u ? !zeros : gt_mag);
-    return r && !is_nan_w(ha, la) && !is_nan_w(hb, lb);
-}
-
 // Gamma = sum_i alpha_i g_i, Pi = sum_i alpha_i P_i over the NF fluids, the
 // carried fractions a[0..NF-2] first and alpha_N = 1 - a[0] - ... - a[NF-2]
 // last (two fluids: a1 g1 + (1 - a1) g2).

@@ -156,12 +156,12 @@ __device__ __forceinline__ R cell_wavespeed(const EosR<R, NF>& e, const R* w, co
     R G, Pi;
     mixture(e, w + FL::IA, G, Pi);
     R c2 = rdiv((G + R(1)) * w[FL::IE] + Pi, G * rho);
-    bad |= !(rho > R(0)) || !(c2 > R(0));
+    bad |= !pos(rho) || !pos(c2);
     R c = sqrt_pos(c2);
     R s = R(0);
 #pragma unroll
     for (int d = 0; d < NDIM; ++d) s += (fabs(w[FL::IU + d]) + c) * R(inv_dx[d]);
-    bad |= !(s < R(INFINITY));
+    bad |= !lt(s, R(INFINITY));
     return s;
 }
 
@@ -743,8 +743,7 @@ sweep_kernel(const SweepArgs a, const __grid_constant__ CUtensorMap tmap) {
             fetch(k, v);
             if constexpr (EXACT) exact::cons_to_prim<NDIM, NF>(a.eos, v, W[k]);
             else to_prim<NDIM, NF>(er, v, W[k]);
-            if constexpr (EXACT) bad |= !exact::gt0(mix_rho<NF>(W[k]));
-            else bad |= !(mix_rho<NF>(W[k]) > R(0));
+            bad |= !pos(mix_rho<NF>(W[k]));
         }
         // FP64 reference-order form: the smoothness indicators' curvature terms
         // of the window's stencils {i-2..i}, {i-1..i+1} (cell i = window centre),
@@ -1074,8 +1073,7 @@ sweep_kernel(const SweepArgs a, const __grid_constant__ CUtensorMap tmap) {
                 if (!PREFETCH) fetch(j + 3 - (s0 - 3), vnext);
                 if constexpr (EXACT) exact::cons_to_prim<NDIM, NF>(a.eos, vnext, W[4]);
                 else to_prim<NDIM, NF>(er, vnext, W[4]);
-                if constexpr (EXACT) bad |= !exact::gt0(mix_rho<NF>(W[4]));
-                else bad |= !(mix_rho<NF>(W[4]) > R(0));
+                bad |= !pos(mix_rho<NF>(W[4]));
             }
         }
         // only cells this lane owns count (inactive lanes and segment halos excluded)
