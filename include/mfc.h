@@ -354,8 +354,9 @@ int mfc_selfcheck_conversions(long long n, unsigned long long seed, long long* m
 
 /* Instrumentation, no counterpart in the paper: checks the FP64 form's
  * integer-pipe WENO5 operations (products by 3, 5, 7 and 11, quotients by 6)
- * against the FP64 instructions on n pseudo-random patterns (all exponents,
- * zeros, subnormals, infinities, NaNs); *mismatches receives the number of
+ * against the FP64 instructions, and its integer-word compares (x > 0, 0 <= x,
+ * x < y) against the FP64 compares, on n pseudo-random patterns (all
+ * exponents, zeros, subnormals, infinities, NaNs); *mismatches receives the number of
  * differing results (0 expected).  Allocates 4 bytes of device memory and
  * synchronises the legacy default stream. */
 int mfc_selfcheck_exact_ops(long long n, unsigned long long seed, long long* mismatches);

@@ -301,9 +301,12 @@ __global__ void conversion_check_kernel(long long n, unsigned long long seed, un
 }
 
 // Self-check of the FP64 form's integer-pipe products K v and quotients x/6
-// against the FP64 instructions: pseudo-random patterns over every exponent,
-// with a share of zeros, subnormals, infinities, NaNs and exponents at the
-// ends of the range where the integer path hands over to the FP64 one.
+// against the FP64 instructions, and of its integer-word compares (x > 0,
+// 0 <= x, x < y) against the FP64 compares: pseudo-random patterns over every
+// exponent, with a share of zeros, subnormals, infinities, NaNs and exponents
+// at the ends of the range where the integer path hands over to the FP64 one;
+// the second compare operand is another such pattern, x itself or x with its
+// lowest bit or its sign flipped.
 __global__ void exact_ops_check_kernel(long long n, unsigned long long seed, unsigned* mismatches) {
     unsigned bad = 0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
@@ -328,6 +331,15 @@ __global__ void exact_ops_check_kernel(long long n, unsigned long long seed, uns
         for (int k = 0; k < 5; ++k)
             if (__double_as_longlong(r[k]) != __double_as_longlong(h[k]) && !(r[k] != r[k] && h[k] != h[k]))
                 ++bad;
+        unsigned long long w = z * 0xd6e8feb86659fd93ULL;
+        w ^= w >> 32;
+        const unsigned pick = (unsigned)(i >> 4) & 3u;
+        if (pick == 0u) w = bits;
+        else if (pick == 1u) w = bits ^ 1ULL;
+        else if (pick == 2u) w = bits ^ 0x8000000000000000ULL;
+        else if ((w & 7u) == 0u) w &= 0x8000000000000000ULL;   // +-0 now and then
+        const double y = __longlong_as_double((long long)w);
+        bad += (gt0(x) != (x > 0.0)) + (ge0(x) != (0.0 <= x)) + (less(x, y) != (x < y)) + (less(y, x) != (y < x));
     }
     if (bad) atomicAdd(mismatches, bad);
 }

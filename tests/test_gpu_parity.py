@@ -335,8 +335,10 @@ def test_integer_conversions_match_hardware():
 
 def test_integer_weno_operations_match_hardware():
     """The FP64 form's integer-pipe products K v (K = 3, 5, 7, 11) and
-    quotients x/6 return the FP64 instructions' bits on 64M patterns, zeros,
-    subnormals, infinities, NaNs and the ends of the exponent range among them."""
+    quotients x/6 return the FP64 instructions' bits, and its integer-word
+    compares (x > 0, 0 <= x, x < y) the FP64 compares' answers, on 64M
+    patterns, zeros, subnormals, infinities, NaNs and the ends of the exponent
+    range among them."""
     import ctypes
     from paper_2409_10729_gb300 import mfc
     bad = ctypes.c_longlong(-1)
