@@ -72,20 +72,24 @@ __global__ void wavespeed_kernel(const double* __restrict__ q, long long nc, Eos
     // every thread of a warp runs the same number of iterations so that the
     // warp reduction below sees all 32 lanes
     long long iters = (nc + stride - 1) / stride;
+    // uniform over the launch: only a non-uniform grid needs the cell's
+    // coordinates (64-bit divisions, kept off the uniform-grid path)
+    const bool nu = g.cw[0] || g.cw[1] || g.cw[2];
     for (long long it = 0; it < iters; ++it) {
         long long c = start + it * stride;
         if (c < nc) {
             double v[FL::NEQ];
 #pragma unroll
             for (int f = 0; f < FL::NEQ; ++f) v[f] = __ldg(q + f * nc + c);
-            // non-uniform directions: the cell's own width
-            const long long ci[3] = {c % n0, (c / n0) % n1, c / ((long long)n0 * n1)};
+            if (nu) {   // non-uniform directions: the cell's own width
+                const long long ci[3] = {c % n0, (c / n0) % n1, c / ((long long)n0 * n1)};
 #pragma unroll
-            for (int d = 0; d < NDIM; ++d)
-                if (g.cw[d]) {
-                    dx[d] = __ldg(g.cw[d] + ci[d]);
-                    rdx[d] = __ldg(g.crw[d] + ci[d]);
-                }
+                for (int d = 0; d < NDIM; ++d)
+                    if (g.cw[d]) {
+                        dx[d] = __ldg(g.cw[d] + ci[d]);
+                        rdx[d] = __ldg(g.crw[d] + ci[d]);
+                    }
+            }
             double s = exact::cell_wavespeed<NDIM, NF>(e, v, dx, rdx, bad);
             smax = s > smax ? s : smax;
         }
